@@ -1,0 +1,185 @@
+"""Pins for the low-rank FP64 oracle (CPU only): SMW, LR-ADI, NLR-ADI, Algorithms 1-2, Framework 1."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import care_inputs as ci
+from oracle import dense as od
+from oracle import lowrank as ol
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def small():
+    p = ci.config_small_fdm()
+    A = p.A.to_dense()
+    X = od.newton_care(A, p.B, p.C)["X"]
+    return p, A, X
+
+
+@pytest.mark.parametrize("shift", [-300.0, complex(-900.0, 1500.0)])
+def test_smw_against_dense_inverse(small, shift):
+    """Section 4 SMW formula: (A_k + p I)^{-T} W equals the dense inverse applied to W."""
+    p, A, X = small
+    s = ci.Stream(ci.SEED, 21)
+    K = X @ p.B
+    W = s.normal(p.n * 3).reshape(p.n, 3)
+    V = ol.smw_solve(ol.ShiftedSolver(p.A.to_scipy()), p.B, K, shift, W)
+    Ak = A - p.B @ K.T
+    V_dense = np.linalg.solve((Ak + shift * np.eye(p.n)).T, W.astype(complex))
+    assert np.linalg.norm(V - V_dense) <= 1e-11 * np.linalg.norm(V_dense)
+
+
+def test_lradi_against_bartels_stewart(small):
+    """LR-ADI (residual form, complex pairs) vs Bartels-Stewart on the nonsymmetric n=400
+    operator, without and with feedback; the +/- split returns the two halves."""
+    p, A, X = small
+    As = p.A.to_scipy()
+    W = p.C.T
+    Z, info = ol.lradi(As, p.B, None, W, 1e-12)
+    assert any(s.imag != 0 for s in info["shifts"]), "complex shifts expected on this operator"
+    X1 = od.lyap_bartels_stewart(A.T, W @ W.T)
+    assert np.linalg.norm(Z @ Z.T - X1) <= 1e-10 * np.linalg.norm(X1)
+    K = X @ p.B
+    s = ci.Stream(ci.SEED, 22)
+    Wp = s.normal(p.n * 2).reshape(p.n, 2)
+    Wm = 0.1 * s.normal(p.n).reshape(p.n, 1)
+    (Zp, Zm), _ = ol.lradi(As, p.B, K, np.hstack([Wp, Wm]), 1e-12, split=2)
+    Ak = A - p.B @ K.T
+    Xp = od.lyap_bartels_stewart(Ak.T, Wp @ Wp.T)
+    Xm = od.lyap_bartels_stewart(Ak.T, Wm @ Wm.T)
+    assert np.linalg.norm(Zp @ Zp.T - Xp) <= 1e-10 * np.linalg.norm(Xp)
+    assert np.linalg.norm(Zm @ Zm.T - Xm) <= 1e-9 * np.linalg.norm(Xm)
+
+
+def test_lradi_closed_form_laplacian_modes():
+    """P4 at larger n: F = Dirichlet Laplacian (symmetric), W in the span of analytic modes:
+    X = V_S [(V_S^T W W^T V_S)_ij / (-(l_i + l_j))] V_S^T."""
+    N = 50
+    A = ci.dirichlet_laplacian(N, 2).to_scipy()
+    modes = [(1, 1), (2, 1), (1, 3), (4, 4)]
+    vs, ls = zip(*[ci.laplacian_mode(N, 2, k) for k in modes])
+    V = np.stack(vs, 1)
+    lam = np.array(ls)
+    s = ci.Stream(ci.SEED, 23)
+    W = V @ s.normal(4 * 2).reshape(4, 2)
+    G = V.T @ W @ W.T @ V
+    core = G / -(lam[:, None] + lam[None, :])
+    Z, _ = ol.lradi(A, np.zeros((N * N, 1)), None, W, 1e-13)
+    w, Q = np.linalg.eigh(core)
+    Zx = V @ (Q * np.sqrt(np.maximum(w, 0.0)))
+    assert od.lowrank_diff_fro(Z, Zx) <= 1e-10 * od.lowrank_fro(Zx)
+
+
+def test_residual_factor_identity(small):
+    """Algorithm 1: F M F^T equals the dense residual R(Z Z^T); with eta_r = 0,
+    C+C+^T - C-C-^T = R and ||H||_F = ||R||_F; with eta_r > 0 the dropped part is
+    bounded by sqrt(#dropped) * eta_r."""
+    p, A, X = small
+    s = ci.Stream(ci.SEED, 24)
+    Z = np.linalg.cholesky(X + 1e-12 * np.eye(p.n))[:, :6] + 1e-3 * s.normal(p.n * 6).reshape(p.n, 6)
+    R = od.riccati_residual(A, p.B, p.C, Z @ Z.T)
+    Cp, Cm, res, info = ol.residual_factor(A, p.B, p.C, Z, eta_r_rel=0.0)
+    assert res == pytest.approx(np.linalg.norm(R), rel=1e-10)
+    assert np.linalg.norm(Cp @ Cp.T - Cm @ Cm.T - R) <= 1e-11 * np.linalg.norm(R)
+    Cp2, Cm2, res2, info2 = ol.residual_factor(A, p.B, p.C, Z, eta_r_rel=1e-4)
+    lam = info2["lam"]
+    eta = 1e-4 * np.max(np.abs(lam))
+    ndrop = int(np.sum(np.abs(lam) < eta))
+    err = np.linalg.norm(Cp2 @ Cp2.T - Cm2 @ Cm2.T - R)
+    assert err <= math.sqrt(max(ndrop, 1)) * eta * 1.0001 + 1e-11 * np.linalg.norm(R)
+    assert res2 == pytest.approx(res, rel=1e-12)
+    # M's sign pattern: flipping the -I_m block gives a different (wrong) residual
+    wrongR = R + 2 * (Z @ Z.T @ p.B) @ (Z @ Z.T @ p.B).T
+    assert abs(res - np.linalg.norm(wrongR)) > 1e-6 * res
+
+
+def test_solution_factor_identity():
+    """Algorithm 2: with eta_s = 0 and Z Z^T + Z+ Z+^T - Z- Z-^T PSD, the new factor
+    reproduces it; an indefinite update is replaced by its positive spectral part."""
+    n = 80
+    s = ci.Stream(ci.SEED, 25)
+    Z = s.normal(n * 5).reshape(n, 5)
+    Zp = 0.1 * s.normal(n * 2).reshape(n, 2)
+    Zm = Z[:, :2] * 0.5
+    Xn = Z @ Z.T + Zp @ Zp.T - Zm @ Zm.T
+    Znew, _ = ol.solution_factor(Z, Zp, Zm, eta_s_mult=0.0)
+    assert np.linalg.norm(Znew @ Znew.T - Xn) <= 1e-12 * np.linalg.norm(Xn)
+    Zm2 = 2.0 * s.normal(n * 1).reshape(n, 1)
+    Xi = Z @ Z.T - Zm2 @ Zm2.T
+    w, V = np.linalg.eigh(Xi)
+    Xpos = (V[:, w > 0] * w[w > 0]) @ V[:, w > 0].T
+    Znew2, _ = ol.solution_factor(Z, np.zeros((n, 0)), Zm2, eta_s_mult=0.0)
+    assert np.linalg.norm(Znew2 @ Znew2.T - Xpos) <= 1e-11 * np.linalg.norm(Xpos)
+
+
+def test_nlradi_matches_newton(small):
+    p, A, X = small
+    Z, info = ol.nlradi(p.A.to_scipy(), p.B, p.C, 1e-12, 1e-12)
+    assert np.linalg.norm(Z @ Z.T - X) <= 1e-9 * np.linalg.norm(X)
+    assert 2 <= info["newton_steps"] <= 20
+
+
+def test_framework1_small_fdm(small):
+    """Framework 1 (FP64) on the n=400 convection-diffusion CARE: residual <= 1e-12 and
+    X within 1e-10 of Newton/Bartels-Stewart."""
+    p, A, X = small
+    Z, info = ol.framework1(p.A.to_scipy(), p.B, p.C, tau_R=1e-12)
+    assert info["status"] == "ok"
+    assert info["rel_res"] <= 1e-12
+    assert np.linalg.norm(Z @ Z.T - X) <= 1e-10 * np.linalg.norm(X)
+
+
+def test_framework1_refines_perturbed_start(small):
+    """Refinement from a perturbed factor: residual falls below 1e-12 within a few outer
+    steps and each step contracts."""
+    p, A, X = small
+    w, V = np.linalg.eigh(X)
+    keep = w > 1e-14 * w.max()
+    Zx = V[:, keep] * np.sqrt(w[keep])
+    s = ci.Stream(ci.SEED, 26)
+    Z1 = Zx * (1 + 1e-4 * s.normal(Zx.size).reshape(Zx.shape))
+    Z, info = ol.framework1(p.A.to_scipy(), p.B, p.C, tau_R=1e-12, Z1=Z1)
+    h = info["res_hist"]
+    assert info["status"] == "ok" and len(h) <= 4
+    assert all(h[i + 1] < 0.1 * h[i] for i in range(len(h) - 1))
+    assert np.linalg.norm(Z @ Z.T - X) <= 1e-10 * np.linalg.norm(X)
+
+
+def test_framework1_eigen_aligned_large():
+    """P3: A = -(Dirichlet Laplacian) on a 60x60 grid with B, C along three analytic modes;
+    the exact X* = sum x_i v_i v_i^T is known at any n."""
+    pr = ci.eigen_aligned_problem(60, 2, [(1, 1), (2, 3), (5, 2)], [0.8, 1.5, 0.3], [2.0, 0.5, 3.0])
+    Z, info = ol.framework1(pr.A.to_scipy(), pr.B, pr.C, tau_R=1e-12)
+    x = od.scalar_care(pr.meta["lams"], pr.meta["beta"], pr.meta["gamma"])
+    Zx = pr.meta["V"] * np.sqrt(x)
+    assert info["rel_res"] <= 1e-12
+    assert od.lowrank_diff_fro(Z, Zx) <= 1e-10 * od.lowrank_fro(Zx)
+
+
+def test_framework1_dense_conditioning_k1():
+    p = ci.config_dense_conditioning(1)
+    A = p.A.to_dense()
+    X = od.newton_care(A, p.B, p.C)["X"]
+    Z, info = ol.framework1(A, p.B, p.C, tau_R=1e-12, dense=True)
+    assert info["rel_res"] <= 1e-12
+    assert np.linalg.norm(Z @ Z.T - X) <= 1e-9 * np.linalg.norm(X)
+
+
+@pytest.mark.slow
+def test_table1_example1_fp64():
+    """Golden (Section 5.1, Table 1, FP64 rows): the oracle reproduces the paper's Res level,
+    and Newton/refinement counts and rank within a small margin (shift-strategy dependent)."""
+    g = json.load(open(os.path.join(GOLD, "table1_example1_fp64.json")))
+    for case in g["cases"][:1]:
+        p = ci.paper_example1(q=case["q"])
+        Z, info = ol.framework1(p.A.to_dense(), p.B, p.C, tau_R=1e-14, dense=True)
+        assert info["status"] == "ok"
+        assert info["res_paper"] <= 10 * case["res"]
+        assert abs(info["iter0"][0] - case["iter0"][0]) <= 3
+        assert abs(info["iter"][0] - case["iter"][0]) <= 1
+        assert abs(info["rank"] - case["rank"]) <= 3
