@@ -1,0 +1,343 @@
+"""Benchmark: time to relative residual 1e-10 for the large sparse CARE, mixed
+precision (FP32 NLR-ADI / LR-ADI inner solves, FP64 residual factorisation and
+update) vs the all-FP64 path of the same code, on one B300; plus the SpMM
+roofline.  Prints one JSON line.
+
+Workload: 2D convection-diffusion -Lap(u) + 10 u_x + 100 u_y on a 500 x 500
+interior grid (n = 250,000, nnz = 1,248,000), A = -L, B n x 5 and C 5 x n with
+U[0,1) entries from the seeded generator.  A step is one complete care_solve
+(NLR-ADI + refinement to ||R||_F / ||C^T C||_F <= 1e-10) with the inputs
+resident in HBM; L2 is flushed (a 256 MB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (the program the GPU results are
+checked against) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel. residual 1e-10, mixed vs all-FP64 on 1 B300; SpMM HBM GB/s vs peak"
+TOL = 1e-10
+GRID = 500
+MP = 5
+R_CAP = 512
+
+
+def workload_config(prob):
+    return {"workload": f"2D convection-diffusion CARE, {GRID}x{GRID} grid (n={prob.n}, nnz={prob.A.nnz}), "
+                        f"m=p={MP}, tol {TOL:g}, mixed FP32-inner/FP64-outer",
+            "n": prob.n, "nnz": prob.A.nnz, "m": MP, "p": MP, "tol": TOL,
+            "l2": "flushed by a 256 MB write before each timed step"}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampler (SM clock and throttle reasons) for the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", "0"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+        if mx:
+            out["sm_max_mhz"] = max(mx)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(sm)
+        return out
+
+
+def run_reference(args):
+    """CPU FP64 oracle on the host cores: a bounded sample of the same workload."""
+    import numpy as np
+    import care_inputs as ci
+    from oracle import lowrank as ol
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = ci.config_fdm2d(GRID, MP, MP)
+    As = prob.A.to_scipy()
+    cores = os.cpu_count()
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        v, sample = oracle_sample(prob, As)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(v)
+    val = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(prob),
+            "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+SHIFTED_SOLVES_PER_SOLVE = None
+
+
+def oracle_sample(prob, As, shifted_solves=None):
+    """Time the oracle's FP64 LR-ADI shifted solve (SuperLU factorisation of
+    M_p = (A + pI)^T and an SMW block solve with p + m right-hand sides) for three
+    shifts, and scale to a full solve by the number of shifted solves a full
+    FP64 Framework-1 run performs (the GPU run's count, or 150 if unknown)."""
+    import numpy as np
+    from oracle import lowrank as ol
+    solver = ol.ShiftedSolver(As)
+    W = np.hstack([prob.C.T, np.zeros((prob.n, MP))])
+    K = 1e-3 * prob.B
+    shifts = [-3000.0, -3.0e4, -3.0e5]
+    t0 = time.perf_counter()
+    for p in shifts:
+        ol.smw_solve(solver, prob.B, K, p, W)
+    per = (time.perf_counter() - t0) / len(shifts)
+    count = shifted_solves or SHIFTED_SOLVES_PER_SOLVE or 150
+    return per * count, (f"3 FP64 SMW shifted solves (SuperLU of (A+pI)^T, {2 * MP} RHS) on the n={prob.n} "
+                         f"operator, {per:.3f} s each, scaled x{count} shifted solves per full solve")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import care_inputs as ci
+    import paper_2607_14742_b300 as pb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    prob = ci.config_fdm2d(GRID, MP, MP)
+    A = pb.CSR.from_arrays(prob.n, prob.A.rowptr, prob.A.colind, prob.A.val, device=dev)
+    B = torch.tensor(prob.B, device=dev)
+    C = torch.tensor(prob.C, device=dev)
+    ws = pb.Workspace()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def solve(prec):
+        return pb.care_solve(A, B, C, tol=TOL, prec=prec, r_cap=R_CAP, workspace=ws)
+
+    for _ in range(args.warmup):
+        Z, info = solve("mixed")
+    stream = torch.cuda.current_stream()
+    ts = []
+    infos = []
+    launches0 = pb.kernel_launches()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
+    barrier()
+    with clocks:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Z, info = solve("mixed")
+            e1.record(stream)
+            barrier()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+            infos.append(info)
+    launches = pb.kernel_launches() - launches0
+    t = max(ts) if False else statistics.mean(ts)
+    if world > 1:
+        tt = torch.tensor([t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    info = infos[-1]
+    # the all-FP64 path of the same code
+    fp64 = None
+    if args.fp64_steps > 0:
+        Z64, i64 = solve("fp64")
+        t64 = []
+        for _ in range(args.fp64_steps):
+            flush.fill_(1.0)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Z64, i64 = solve("fp64")
+            e1.record(stream)
+            barrier()
+            t64.append(e0.elapsed_time(e1) / 1e3)
+        fp64 = {"s_per_solve": statistics.mean(t64), "status": i64["status"], "rank": i64["rank"],
+                "res_rel_CtC": i64["res_rel_CtC"], "iter0": i64["iter0"], "iter": i64["iter"],
+                "speedup_mixed_vs_fp64": statistics.mean(t64) / t}
+    # end to end through the public API: host inputs -> device, Z -> host, every step
+    hA = [torch.from_numpy(prob.A.rowptr).pin_memory(), torch.from_numpy(prob.A.colind).pin_memory(),
+          torch.from_numpy(prob.A.val).pin_memory()]
+    hB = torch.from_numpy(prob.B).pin_memory()
+    hC = torch.from_numpy(prob.C).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in hA + [hB, hC])
+    e2e_t = []
+    d2h = 0
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        barrier()
+        t0 = time.perf_counter()
+        dA = pb.CSR(prob.n, hA[0].to(dev, non_blocking=True), hA[1].to(dev, non_blocking=True),
+                    hA[2].to(dev, non_blocking=True))
+        dB = hB.to(dev, non_blocking=True)
+        dC = hC.to(dev, non_blocking=True)
+        Ze, ie = pb.care_solve(dA, dB, dC, tol=TOL, prec="mixed", r_cap=R_CAP, workspace=ws)
+        Zh = Ze.cpu()
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+        d2h = Zh.numel() * Zh.element_size()
+    # SpMM roofline: the fused BiCGStab SpMM shape (b = 2*(p+m) FP32 columns) and a
+    # cold operator + blocks larger than L2 (the 3D 100^3 operator, 20 columns)
+    spmm = spmm_roofline(pb, torch, prob, dev)
+    pk = peaks()
+    line = {
+        "metric": METRIC, "value": t, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic (seeded; see care_inputs)", "config": workload_config(prob),
+        "status": info["status"], "res_rel_CtC": info["res_rel_CtC"], "res_paper": info["res_paper"],
+        "rank": info["rank"], "iter0": info["iter0"], "iter": info["iter"], "krylov_iters": info["krylov_iters"],
+        "ms_phase": {"nlradi": info["ms_phase"][0], "alg1": info["ms_phase"][1], "inner_lradi": info["ms_phase"][2],
+                     "alg2": info["ms_phase"][3]},
+        "fp64_path": fp64,
+        "e2e": {"value": statistics.mean(e2e_t), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches // max(1, args.steps),
+        "roofline": spmm["roofline"],
+        "spmm": spmm,
+        "clocks": clocks.summary(),
+        "peaks_source": "MEASURED_PEAKS.json" if pk else "fallback 6400 GB/s",
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        global SHIFTED_SOLVES_PER_SOLVE
+        v, sample = oracle_sample(prob, prob.A.to_scipy(), shifted_solves=(info["iter0"][1] + info["iter"][1]))
+        line["cpu_baseline"] = {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def spmm_roofline(pb, torch, prob, dev):
+    """Time the SpMM kernel live with CUDA events on the launching stream."""
+    import care_inputs as ci
+    pk = peaks()
+    peak = float(pk.get("hbm_gbs", 6400.0))
+    out = {}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timeit(op, X, reps=20):
+        Y = None
+        for _ in range(3):
+            Y = pb.spmm(op, X, -1000.0)
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.spmm(op, X, -1000.0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    cases = {}
+    op2 = pb.Operator(pb.CSR.from_arrays(prob.n, prob.A.rowptr, prob.A.colind, prob.A.val, device=dev))
+    X2 = torch.randn(prob.n, 2 * 2 * MP, device=dev, dtype=torch.float32)
+    ms2 = timeit(op2, X2)
+    b2 = X2.shape[1]
+    bytes2 = prob.A.nnz * 8 + 4 * (prob.n + 1) + 2 * prob.n * b2 * 4
+    cases["fdm2d_500_b20_f32"] = {"ms": ms2, "alg_bytes": bytes2, "GBs": bytes2 / ms2 / 1e6}
+    p3 = ci.convection_diffusion(100, (10.0, 50.0, 100.0))
+    op3 = pb.Operator(pb.CSR.from_arrays(p3.n, p3.rowptr, p3.colind, p3.val, device=dev))
+    X3 = torch.randn(p3.n, 20, device=dev, dtype=torch.float32)
+    ms3 = timeit(op3, X3)
+    bytes3 = p3.nnz * 8 + 4 * (p3.n + 1) + 2 * p3.n * 20 * 4
+    cases["fdm3d_100_b20_f32"] = {"ms": ms3, "alg_bytes": bytes3, "GBs": bytes3 / ms3 / 1e6}
+    ach = cases["fdm3d_100_b20_f32"]["GBs"]
+    out["cases"] = cases
+    out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "traffic": None,
+                       "kernel": "k_spmm (CSR A^T, 7-point 100^3 operator, 20 FP32 columns, shift fused)"}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * care_b300.h -- C ABI of the B300 (sm_103a) mixed-precision low-rank CARE solver.
+ *
+ * Problem (paper Section 1, Eq. (1.1)):  A^T X + X A - X B B^T X + C^T C = 0,
+ * A (n x n) sparse and stable, B (n x m), C (p x n), m, p << n; the stabilising
+ * solution is returned as a low-rank factor X ~ Z Z^T.
+ *
+ * Method: Framework 1 of the paper (Section 2) realised with NLR-ADI for the
+ * initial approximation and LR-ADI for the correction Lyapunov equations
+ * (Section 4).  Shifted solves use a block BiCGStab on M_p = (A + p I)^T with the
+ * closed-loop feedback handled by the Sherman-Morrison-Woodbury formula
+ * (Section 4).  The residual factor decomposition (Algorithm 1) and the solution
+ * factor decomposition (Algorithm 2) always run in FP64.
+ *
+ * Conventions (all entry points):
+ *  - Pointers to matrices are DEVICE pointers unless a parameter says "host".
+ *  - Boundary matrices (B, C, K, W, Z, C+, C-) are FP64 COLUMN-MAJOR with the
+ *    given leading dimension, as in LAPACK.  The kernel-level entry points
+ *    (care_spmm, care_gram, care_shifted_solve) take ROW-MAJOR blocks, the
+ *    library's internal layout, with a leading dimension counted in reals.
+ *  - The caller owns every buffer.  The library allocates no device memory:
+ *    each solver entry point takes a device workspace whose size the matching
+ *    *_workspace_size query returns.  Host-side bookkeeping uses ordinary heap
+ *    memory.
+ *  - Work is issued on the given CUDA stream (0 = legacy default stream).  The
+ *    solver entry points synchronise that stream internally (the iteration
+ *    control runs on the host), so outputs are complete when they return.
+ *    care_spmm and care_gram are asynchronous.
+ *  - Errors are reported only through the returned care_status; nothing
+ *    throws across the ABI.  After CARE_ERR_CUDA the stream's state is
+ *    undefined.
+ *  - Not thread-safe per stream: concurrent calls must use distinct streams
+ *    and distinct workspaces.
+ */
+#ifndef CARE_B300_H
+#define CARE_B300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* care_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  CARE_OK = 0,
+  CARE_ERR_INVALID_ARG = 1,   /* bad size, null pointer, leading dimension too small   */
+  CARE_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed            */
+  CARE_ERR_WORKSPACE = 3,     /* work_bytes smaller than the workspace query's result   */
+  CARE_ERR_RANK_CAPACITY = 4, /* a factor would exceed its column capacity              */
+  CARE_NOT_CONVERGED = 5,     /* k_max refinement steps without reaching tol (Z valid)  */
+  CARE_STAGNATED = 6,         /* residual ratio above stag_ratio (Section 5; Z valid)   */
+  CARE_INNER_FAILED = 7,      /* LR-ADI / Krylov made no progress                       */
+  CARE_UNSTABLE = 8,          /* a projected Ritz value of A_k^T has Re >= 0            */
+  CARE_NONFINITE = 9,         /* NaN/Inf met in inputs or iterates                      */
+  CARE_ERR_SMALL_DENSE = 10   /* a small dense host factorisation failed                */
+} care_status;
+
+typedef enum {
+  CARE_PREC_FP64 = 0,       /* u_s = u = u_r = u_c = FP64: the all-FP64 path            */
+  CARE_PREC_MIXED_FP32 = 1  /* u_s = FP32 (NLR-ADI and inner LR-ADI); u, u_r, u_c = FP64 */
+} care_prec;
+
+typedef enum { CARE_KRYLOV_BICGSTAB = 0 } care_krylov;
+typedef enum { CARE_PRECOND_NONE = 0, CARE_PRECOND_JACOBI = 1 } care_precond;
+
+/* A itself (not A^T) in CSR: int32 row pointers (n+1) and column indices (nnz),
+ * FP64 values (nnz); device pointers; column indices need not be sorted. */
+typedef struct {
+  int n;
+  int nnz;
+  const int* rowptr;
+  const int* colind;
+  const double* val;
+} care_csr;
+
+/* Parameters.  care_opts_default() fills in the paper's values (Section 5:
+ * eta_r = 1e-4 max|lambda(H)|, eta_s = 10 u max|lambda(P)|, tau_L = 1e-12 / 1e-5,
+ * k_max = 20, j_max = 50; GMRES tolerances 1e-10 / 1e-5 and iteration limits
+ * 200 / 100 of Section 5.2 reused for the block Krylov solver). */
+typedef struct {
+  int kmax;              /* refinement steps of Framework 1                          */
+  int jmax;              /* LR-ADI shifts per Lyapunov solve                         */
+  int newton_max;        /* NLR-ADI Newton steps                                     */
+  int adi_cap;           /* column capacity of one LR-ADI factor (workspace sizing)  */
+  double eta_r_rel;      /* Algorithm 1 truncation, relative to max|lambda(H)|       */
+  double eta_s_mult;     /* Algorithm 2 truncation: eta_s = eta_s_mult*u*max|sigma|  */
+  double tau_L_lo;       /* LR-ADI tolerance with FP32 inner solves                  */
+  double tau_L_hi;       /* LR-ADI tolerance with FP64 inner solves                  */
+  double tau_N_lo;       /* NLR-ADI Newton tolerance (relative change of K), FP32    */
+  double tau_N_hi;       /* same, FP64                                               */
+  double krylov_tol_lo;  /* per-column relative residual, FP32 shifted solves        */
+  double krylov_tol_hi;  /* same, FP64                                               */
+  int krylov_maxit_lo;   /* FP32 iteration limit                                     */
+  int krylov_maxit_hi;   /* FP64 iteration limit                                     */
+  int krylov;            /* care_krylov                                              */
+  int precond;           /* care_precond                                             */
+  int krylov_chunk;      /* max right-hand-side columns per Krylov call (<= 64)      */
+  double stag_ratio;     /* refinement stops if ||R_{k+1}|| / ||R_k|| > stag_ratio   */
+  int shift_hmin;        /* min. projection basis width for shift generation         */
+  int verbose;           /* 0 silent, 1 per outer step, 2 per ADI step (stderr)      */
+} care_opts;
+
+#define CARE_HIST_MAX 32
+
+typedef struct {
+  int status;             /* care_status of the call                                  */
+  int rank;               /* columns of Z written                                     */
+  int iter0_outer;        /* NLR-ADI Newton steps                                     */
+  int iter0_inner;        /* total LR-ADI shifts in NLR-ADI                           */
+  int iter_outer;         /* refinement steps (Algorithm 1 evaluations)               */
+  int iter_inner;         /* total LR-ADI shifts in the correction solves             */
+  long long krylov_iters; /* block Krylov iterations (all shifted solves)             */
+  long long spmm_calls;   /* SpMM launches                                            */
+  int krylov_unconverged; /* shifted solves that hit the iteration limit              */
+  int nhist;              /* entries of res_hist                                      */
+  double res_hist[CARE_HIST_MAX]; /* ||R(Z_k)||_F / ||C^T C||_F per refinement step  */
+  double res_rel_CtC;     /* final ||R(Z Z^T)||_F / ||C^T C||_F (FP64, Algorithm 1)   */
+  double res_paper;       /* final Res of Section 5                                   */
+  double ms_phase[4];     /* wall ms: NLR-ADI, Algorithm 1, inner LR-ADI, Algorithm 2 */
+  double ms_total;        /* wall ms of the call                                      */
+} care_info;
+
+/* Prepared operator: A^T in CSR (FP64 and FP32 values) plus its diagonal, laid
+ * out inside caller memory by care_op_prepare.  Treat as read-only. */
+typedef struct {
+  int n, nnz;
+  int* rowptr_t;    /* A^T row pointers (n+1)                                       */
+  int* colind_t;    /* A^T column indices (nnz), sorted within rows                  */
+  double* val64_t;  /* A^T values FP64                                               */
+  float* val32_t;   /* A^T values rounded to FP32                                    */
+  double* diag64;   /* diag(A)                                                       */
+  float* diag32;
+  int diag_const;   /* 1 if all diagonal entries are equal (Jacobi is then a no-op)  */
+  double a_fro;     /* ||A||_F                                                       */
+} care_op;
+
+/* ---- parameters, status ------------------------------------------------- */
+
+/* Fills *opts with the paper's parameter values (see care_opts). */
+void care_opts_default(care_opts* opts);
+
+/* Static string for a care_status value (never NULL). */
+const char* care_status_string(int status);
+
+/* Library build string (compiler, target architecture). */
+const char* care_version(void);
+
+/* ---- operator --------------------------------------------------------- */
+
+/* Bytes of device memory care_op_prepare needs for an n x n matrix with nnz
+ * entries. */
+care_status care_op_size(int n, int nnz, size_t* bytes);
+
+/* Builds the prepared operator of A inside mem (device, >= care_op_size bytes,
+ * 256-byte aligned): transposes A on the device, sorts each row of A^T by column,
+ * rounds the values to FP32, extracts the diagonal and ||A||_F.  Synchronises s.
+ * The matrix M_p = (A + p I)^T of the shifted solves (Section 4, SMW formula)
+ * is applied from this transpose with the shift p fused in the kernel, the
+ * identity kept in the working precision (Section 5). */
+care_status care_op_prepare(const care_csr* A, void* mem, size_t bytes, care_stream_t s, care_op* op);
+
+/* ---- kernel-level entry points (row-major blocks) ----------------------- */
+
+/* Y = (A^T + p I) X for an n x b block (Section 4: the operator M_p of the shifted
+ * solves).  dtype 0 = FP64, 1 = FP32 (values of op->val64_t / val32_t).  cplx = 0:
+ * X, Y real, row i at X + i*ldx, ldx >= b; cplx = 1: X, Y complex interleaved
+ * (re, im) pairs, ldx >= 2b reals, p = p_re + i p_im.  Asynchronous on s. */
+care_status care_spmm(const care_op* op, int dtype, int cplx, double p_re, double p_im,
+                      const void* X, int ldx, int b, void* Y, int ldy, care_stream_t s);
+
+/* G = X^T Y for row-major X (n x a, ldx) and Y (n x b, ldy), dtype as above,
+ * accumulated per thread in the input precision and across threads in FP64;
+ * G is FP64 row-major a x b (ldg >= b).  work: device scratch of
+ * care_gram_work_size(n, a, b) bytes.  Asynchronous on s.  Used for the
+ * tall-skinny products of Algorithms 1 and 2 and of LR-ADI (Section 4). */
+size_t care_gram_work_size(int n, int a, int b);
+care_status care_gram(int dtype, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy,
+                      double* G, int ldg, void* work, size_t work_bytes, care_stream_t s);
+
+/* Shifted block solve with feedback (Section 4, SMW formula):
+ *   V = ((A - B K^T)^T + p I)^{-1} W,  i.e.  (A_k + p I)^{-T} W,  A_k = A - B K^T,
+ * for an n x b block W; B, K FP64 column-major n x m (K may be NULL: no
+ * feedback).  W: real FP64 column-major n x b.  V: FP64 column-major n x b,
+ * real when p_im == 0 (entry (i, j) at V[i + j*ldv]) and complex otherwise,
+ * stored as interleaved (re, im) pairs like complex128 (entry (i, j) at
+ * V[2*(i + j*ldv)] and V[2*(i + j*ldv) + 1]); ldv >= n in entries.
+ * prec selects the arithmetic of the Krylov solve.  iters (host, may be NULL)
+ * receives the Krylov iteration count. */
+care_status care_shifted_solve_workspace_size(const care_op* op, int m, int b, care_prec prec,
+                                              const care_opts* opts, size_t* bytes);
+care_status care_shifted_solve(const care_op* op, const double* B, int ldb, const double* K, int ldk,
+                               int m, double p_re, double p_im, const double* W, int ldw, int b,
+                               care_prec prec, const care_opts* opts, double* V, int ldv,
+                               void* work, size_t work_bytes, care_stream_t s, int* iters);
+
+/* ---- solver entry points ------------------------------------------------ */
+
+/* Workspace for care_solve / lyap_lradi / care_residual_factor on an n x n
+ * operator with nnz entries, m inputs, p outputs (or RHS width b for
+ * lyap_lradi), factor capacity r_cap, precision policy prec. */
+care_status care_workspace_size(int n, int nnz, int m, int p, int r_cap, care_prec prec,
+                                const care_opts* opts, size_t* bytes);
+
+/* Framework 1 (Section 2) with the ADI realisation of Section 4:
+ *   Z_1 <- NLR-ADI in u_s (FP32 for CARE_PREC_MIXED_FP32, FP64 otherwise);
+ *   loop k = 1..k_max: Algorithm 1 in FP64 -> C+, C-, ||R(Z_k)||_F;
+ *     stop if ||R||_F <= tol ||C^T C||_F (or stagnation, Section 5);
+ *     LR-ADI in u_s on A_k^T X + X A_k + [C+,C-][C+,C-]^T-split = 0;
+ *     Algorithm 2 in FP64 -> Z_{k+1}.
+ * A: CSR of A (device).  B (n x m, ldb) and C (p x n, ldc): FP64 column-major,
+ * device.  Z: output, FP64 column-major n x r_cap (ldz >= n), device; the
+ * first info->rank columns hold the factor, X ~ Z Z^T.  Returns CARE_OK on
+ * convergence; CARE_NOT_CONVERGED / CARE_STAGNATED still return the last Z.
+ * Synchronises s.  info (host) may be NULL. */
+care_status care_solve(const care_csr* A, const double* B, int ldb, int m, const double* C, int ldc,
+                       int p, double tol, care_prec prec, const care_opts* opts, double* Z, int ldz,
+                       int r_cap, void* work, size_t work_bytes, care_stream_t s, care_info* info);
+
+/* LR-ADI (Section 4) for  (A - B K^T)^T X + X (A - B K^T) + W W^T = 0,  X ~ Z Z^T.
+ * B, K: FP64 column-major n x m (both NULL or m = 0: no feedback).  W: FP64
+ * column-major n x b.  Runs in the inner precision of prec with tolerance tol on
+ * ||W_j^T W_j||_2 / ||W_0^T W_0||_2.  Z: FP64 column-major output, capacity
+ * r_cap columns; info->rank = columns written, info->iter_inner = shifts used.
+ * Requires A - B K^T stable. */
+care_status lyap_lradi(const care_csr* A, const double* B, int ldb, const double* K, int ldk, int m,
+                       const double* W, int ldw, int b, double tol, care_prec prec,
+                       const care_opts* opts, double* Z, int ldz, int r_cap, void* work,
+                       size_t work_bytes, care_stream_t s, care_info* info);
+
+/* Algorithm 1 (Section 2) in FP64: factors R(Z Z^T) = C+ C+^T - C- C-^T with
+ * eigenvalues of H kept when lambda >= eta_r or lambda <= -eta_r,
+ * eta_r = eta_r_rel * max|lambda(H)|.  Z: FP64 column-major n x r.  Cp, Cm: FP64
+ * column-major outputs with capacity c_cap columns each; *rp, *rm (host) receive
+ * their widths; *res_fro (host) receives ||R(Z Z^T)||_F = ||H||_F before
+ * truncation.  Cp/Cm may be NULL to get the norm only. */
+care_status care_residual_factor(const care_csr* A, const double* B, int ldb, int m, const double* C,
+                                 int ldc, int p, const double* Z, int ldz, int r, double eta_r_rel,
+                                 double* Cp, int ldcp, int* rp, double* Cm, int ldcm, int* rm,
+                                 int c_cap, double* res_fro, void* work, size_t work_bytes,
+                                 care_stream_t s);
+
+/* Number of kernels this library has launched in the process so far (all
+ * entry points, all streams); for launch accounting in benchmarks. */
+unsigned long long care_kernel_launches(void);
+
+/* ---- small dense host routines (exported for host-only tests) ----------- */
+
+/* Symmetric eigendecomposition of the column-major n x n matrix A (host):
+ * eigenvalues ascending in w, orthonormal eigenvectors in V (column-major,
+ * may be NULL).  Householder tridiagonalisation + implicit QL with Wilkinson
+ * shifts.  Returns CARE_OK or CARE_ERR_SMALL_DENSE. */
+care_status care_host_symeig(int n, const double* A, double* w, double* V);
+
+/* Eigenvalues of a real column-major n x n matrix (host): Hessenberg reduction
+ * and Francis double-shift QR; real parts in wr, imaginary parts in wi. */
+care_status care_host_eigvals(int n, const double* A, double* wr, double* wi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CARE_B300_H */

@@ -325,3 +325,15 @@ def framework1(A, B, C, tau_R=1e-12, kmax=20, jmax=50, tol_lyap=1e-12, tol_newto
     return Z, dict(status=status, res_hist=np.array(hist), rel_res=hist[-1] / ctc,
                    iter0=(init["newton_steps"], init["adi_steps"]), iter=(outer, inner),
                    rank=Z.shape[1], res_paper=res_paper(A, B, C, Z, hist[-1]))
+
+
+def shifted_operator_apply(A, p, X):
+    """Y = M_p X = (A + p I)^T X (Section 4): the operator of the shifted solves."""
+    At = A.T
+    Y = At @ X
+    return Y + p * X
+
+
+def gram(X, Y):
+    """G = X^T Y (tall-skinny inner products, Section 4 complexity analysis)."""
+    return X.T @ Y

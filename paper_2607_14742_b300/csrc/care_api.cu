@@ -1,0 +1,912 @@
+// Algorithms 1 and 2, Framework 1, operator preparation, and the C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <string>
+
+#include "solver.cuh"
+
+#define CARE_STR2(x) #x
+#define CARE_STR(x) CARE_STR2(x)
+
+namespace care {
+
+constexpr double kU64 = 1.1102230246251565e-16;  // FP64 unit roundoff (Section 1 table)
+unsigned long long launches();
+
+// ---------------------------------------------------------- operator ------
+static size_t op_bytes(int n, int nnz) {
+  Arena a;
+  a.get<int>((size_t)n + 1);   // rowptr_t
+  a.get<int>((size_t)nnz);     // colind_t
+  a.get<double>((size_t)nnz);  // val64_t
+  a.get<float>((size_t)nnz);   // val32_t
+  a.get<double>((size_t)n);    // diag64
+  a.get<float>((size_t)n);     // diag32
+  a.get<int>((size_t)n + 1);   // cursor / counts
+  a.get<double>(4);            // reductions
+  return a.off;
+}
+
+__global__ void k_count_cols(int n, const int* rp, const int* ci, int* cnt) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) atomicAdd(&cnt[ci[k]], 1);
+}
+
+// exclusive scan of cnt[0..n) into rp[0..n] (single CTA, 1024 threads)
+__global__ void k_scan(int n, const int* cnt, int* rp) {
+  __shared__ long part[1024];
+  const int t = threadIdx.x;
+  const long chunk = ((long)n + 1023) / 1024;
+  const long b = t * chunk, e = std::min<long>((long)n, b + chunk);
+  long s = 0;
+  for (long i = b; i < e; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long acc = 0;
+    for (int i = 0; i < 1024; ++i) {
+      const long v = part[i];
+      part[i] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  long acc = part[t];
+  for (long i = b; i < e; ++i) {
+    rp[i] = (int)acc;
+    acc += cnt[i];
+  }
+  if (e == n && b < e) rp[n] = (int)acc;
+  if (n == 0 && t == 0) rp[0] = 0;
+}
+
+__global__ void k_scatter(int n, const int* rp, const int* ci, const double* v, const int* rpt, int* cursor,
+                          int* cit, double* vt) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int j = ci[k];
+      const int pos = rpt[j] + atomicAdd(&cursor[j], 1);
+      cit[pos] = (int)i;
+      vt[pos] = v[k];
+    }
+}
+
+// sort each row of A^T by column (insertion sort; rows are short), merge
+// duplicate-free; cast values; extract the diagonal
+__global__ void k_finish_rows(int n, const int* rpt, int* cit, double* vt, float* vt32, double* d64,
+                              float* d32) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int b = rpt[i], e = rpt[i + 1];
+    for (int k = b + 1; k < e; ++k) {
+      const int c = cit[k];
+      const double v = vt[k];
+      int q = k - 1;
+      while (q >= b && cit[q] > c) {
+        cit[q + 1] = cit[q];
+        vt[q + 1] = vt[q];
+        --q;
+      }
+      cit[q + 1] = c;
+      vt[q + 1] = v;
+    }
+    double dg = 0.0;
+    for (int k = b; k < e; ++k) {
+      vt32[k] = (float)vt[k];
+      if (cit[k] == i) dg += vt[k];
+    }
+    d64[i] = dg;
+    d32[i] = (float)dg;
+  }
+}
+
+// red[0] = sum v^2, red[1] = min diag, red[2] = max diag (one CTA, fixed order)
+__global__ void k_op_stats(int n, int nnz, const double* v, const double* d, double* red) {
+  __shared__ double s0[1024], s1[1024], s2[1024];
+  const int t = threadIdx.x;
+  double a = 0.0, mn = INFINITY, mx = -INFINITY;
+  for (long k = t; k < nnz; k += 1024) a += v[k] * v[k];
+  for (long k = t; k < n; k += 1024) {
+    mn = fmin(mn, d[k]);
+    mx = fmax(mx, d[k]);
+  }
+  s0[t] = a; s1[t] = mn; s2[t] = mx;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (t < w) {
+      s0[t] += s0[t + w];
+      s1[t] = fmin(s1[t], s1[t + w]);
+      s2[t] = fmax(s2[t], s2[t + w]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    red[0] = s0[0];
+    red[1] = s1[0];
+    red[2] = s2[0];
+  }
+}
+
+static void prepare_op(const care_csr* A, void* mem, size_t bytes, cudaStream_t s, care_op* op) {
+  const int n = A->n, nnz = A->nnz;
+  CARE_REQUIRE(bytes >= op_bytes(n, nnz), CARE_ERR_WORKSPACE, "operator memory too small");
+  Arena a;
+  a.base = static_cast<char*>(mem);
+  a.cap = bytes;
+  op->n = n;
+  op->nnz = nnz;
+  op->rowptr_t = a.get<int>((size_t)n + 1);
+  op->colind_t = a.get<int>((size_t)nnz);
+  op->val64_t = a.get<double>((size_t)nnz);
+  op->val32_t = a.get<float>((size_t)nnz);
+  op->diag64 = a.get<double>((size_t)n);
+  op->diag32 = a.get<float>((size_t)n);
+  int* cnt = a.get<int>((size_t)n + 1);
+  double* red = a.get<double>(4);
+  const int g = device_sms() * 4;
+  CARE_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)n + 1), s));
+  k_count_cols<<<g, 256, 0, s>>>(n, A->rowptr, A->colind, cnt);
+  CARE_LAUNCH();
+  k_scan<<<1, 1024, 0, s>>>(n, cnt, op->rowptr_t);
+  CARE_LAUNCH();
+  CARE_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)n + 1), s));
+  k_scatter<<<g, 256, 0, s>>>(n, A->rowptr, A->colind, A->val, op->rowptr_t, cnt, op->colind_t, op->val64_t);
+  CARE_LAUNCH();
+  k_finish_rows<<<g, 256, 0, s>>>(n, op->rowptr_t, op->colind_t, op->val64_t, op->val32_t, op->diag64,
+                                    op->diag32);
+  CARE_LAUNCH();
+  k_op_stats<<<1, 1024, 0, s>>>(n, nnz, op->val64_t, op->diag64, red);
+  CARE_LAUNCH();
+  double h[4];
+  CARE_CUDA(cudaMemcpyAsync(h, red, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+  CARE_CUDA(cudaStreamSynchronize(s));
+  op->a_fro = std::sqrt(h[0]);
+  op->diag_const = (n == 0 || h[1] == h[2]) ? 1 : 0;
+}
+
+// ---------------------------------------------------------- problem -------
+struct Prob {
+  long n = 0;
+  int m = 0, p = 0;
+  double* B64 = nullptr;  // n x m row-major
+  double* Ct64 = nullptr; // n x p row-major (C^T)
+  int ldb = 0, ldc = 0;
+  double ctc_fro = 0.0, btb_fro = 0.0;
+};
+
+struct Ref {
+  double *QZ = nullptr, *QZn = nullptr, *Zm = nullptr, *Wb = nullptr, *Wb2 = nullptr;
+  int ldq = 0, ldbig = 0, rcap = 0, bigcap = 0;
+  int r = 0;
+  std::vector<double> s;  // Z = QZ diag(s)
+};
+
+static void alloc_prob(Ctx& c, Prob& P, long n, int m, int p) {
+  P.n = n; P.m = m; P.p = p;
+  P.ldb = pad_ld<double>(std::max(m, 1));
+  P.ldc = pad_ld<double>(std::max(p, 1));
+  P.B64 = c.ar.get<double>((size_t)n * P.ldb);
+  P.Ct64 = c.ar.get<double>((size_t)n * P.ldc);
+}
+
+static void alloc_ref(Ctx& c, Ref& R, long n, int rcap, int bigcap) {
+  R.rcap = rcap;
+  R.bigcap = bigcap;
+  R.ldq = pad_ld<double>(std::max(rcap, 1));
+  R.ldbig = pad_ld<double>(std::max(bigcap, 1));
+  R.QZ = c.ar.get<double>((size_t)n * R.ldq);
+  R.QZn = c.ar.get<double>((size_t)n * R.ldq);
+  R.Zm = c.ar.get<double>((size_t)n * R.ldq);
+  R.Wb = c.ar.get<double>((size_t)n * R.ldbig);
+  R.Wb2 = c.ar.get<double>((size_t)n * R.ldbig);
+}
+
+static void alloc_small(Ctx& c, long n, int maxc, int smallcap) {
+  c.dS_cap = (size_t)smallcap;
+  c.dS = c.ar.get<double>(c.dS_cap);
+  c.dG_cap = (size_t)smallcap;
+  c.dG = c.ar.get<double>(c.dG_cap);
+  const long tiles = (long)((maxc + 63) / 64) * ((maxc + 63) / 64);
+  c.gw_cap = (size_t)(2L * device_sms() + tiles + 2) * 64 * 64;
+  c.gw = c.ar.get<double>(c.gw_cap);
+}
+
+// boundary (column-major FP64) -> internal row-major problem data
+static void load_prob(Ctx& c, Prob& P, const double* B, int ldb, const double* C, int ldc) {
+  if (P.m) copy2d<double, double>(P.n, P.m, B, 1, ldb, P.B64, P.ldb, 1, 1.0, c.s);
+  if (P.p) copy2d<double, double>(P.n, P.p, C, ldc, 1, P.Ct64, P.ldc, 1, 1.0, c.s);
+  std::vector<double> G = gram_h<double>(c, P.n, P.p, P.p, P.Ct64, P.ldc, P.Ct64, P.ldc);
+  double s = 0.0;
+  for (double v : G) s += v * v;
+  P.ctc_fro = std::sqrt(s);
+  std::vector<double> Gb = gram_h<double>(c, P.n, P.m, P.m, P.B64, P.ldb, P.B64, P.ldb);
+  s = 0.0;
+  for (double v : Gb) s += v * v;
+  P.btb_fro = std::sqrt(s);
+  CARE_REQUIRE(std::isfinite(P.ctc_fro) && std::isfinite(P.btb_fro), CARE_NONFINITE, "B or C not finite");
+}
+
+// ------------------------------------------------------- Algorithm 1 ------
+struct Alg1Out {
+  double res = 0.0;  // ||R||_F = ||H||_F (before truncation)
+  int rp = 0, rm = 0;
+  std::vector<double> QB;  // rq x m = Q_Z^T B
+};
+
+// Residual factor decomposition (Algorithm 1) in FP64 for Z = Q_Z T_Z:
+// F = [Z, A^T Z, Z Z^T B, C^T] is expressed in the orthonormal basis
+// [Q_Z, Q_perp], where Q_perp spans the part of [A^T Z, C^T] outside range(Q_Z)
+// (Z Z^T B lies in range(Q_Z)), giving F = U T; H = T M T^T; its
+// eigenvalues give ||R||_F and, after truncation at +-eta_r, the factors
+// C+- = U Q+- |Lambda+-|^{1/2}, written as To (row-major) into Cout = [C+ | C-].
+template <class To>
+static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<double>& TZ, int r, double eta_rel,
+                    To* Cout, int ldco, int ccap) {
+  Alg1Out o;
+  const long n = P.n;
+  const int m = P.m, p = P.p;
+  const int q1 = r + p;
+  CARE_REQUIRE(q1 <= R.bigcap, CARE_ERR_RANK_CAPACITY, "Algorithm 1: [A^T Z, C^T] exceeds capacity");
+  // W = [A^T Z | C^T]
+  if (r) {
+    spmm<double>(op64(c.op), cd{0.0, 0.0}, false, R.Zm, R.ldq, R.Wb, R.ldbig, r, c.s);
+    c.spmm_calls++;
+  }
+  if (p) copy2d<double, double>(n, p, P.Ct64, P.ldc, 1, R.Wb + r, R.ldbig, 1, 1.0, c.s);
+  std::vector<double> Cw = cgs2<double>(c, n, R.QZ, R.ldq, rq, R.Wb, R.ldbig, q1);  // rq x q1
+  o.QB = gram_h<double>(c, n, rq, m, R.QZ, R.ldq, P.B64, P.ldb);
+  std::vector<double> fl(q1, 0.0);
+  for (int j = 0; j < q1; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < rq; ++i) s += Cw[(size_t)i * q1 + j] * Cw[(size_t)i * q1 + j];
+    fl[j] = 1e-28 * s;
+  }
+  OrthOut O = orth_rr<double>(c, n, q1, R.Wb, R.ldbig, R.Wb2, R.ldbig, 1e-12, &fl, true, 0, nullptr, 0);
+  const int qp = O.rank;
+  const int rt = rq + qp;
+  // T blocks, each rt x (r | r | m | p), row-major
+  std::vector<double> tZ((size_t)rt * r, 0.0), tA((size_t)rt * r, 0.0), tK((size_t)rt * m, 0.0),
+      tC((size_t)rt * p, 0.0);
+  for (int i = 0; i < rq; ++i)
+    for (int j = 0; j < r; ++j) tZ[(size_t)i * r + j] = TZ[(size_t)i * r + j];
+  for (int i = 0; i < rt; ++i) {
+    for (int j = 0; j < r; ++j) tA[(size_t)i * r + j] = i < rq ? Cw[(size_t)i * q1 + j] : O.T[(size_t)(i - rq) * q1 + j];
+    for (int j = 0; j < p; ++j)
+      tC[(size_t)i * p + j] = i < rq ? Cw[(size_t)i * q1 + r + j] : O.T[(size_t)(i - rq) * q1 + r + j];
+  }
+  // K = Z Z^T B -> coefficients T_Z T_Z^T (Q_Z^T B) in the Q_Z rows
+  {
+    std::vector<double> TT((size_t)rq * rq, 0.0);
+    for (int i = 0; i < rq; ++i)
+      for (int k = 0; k < rq; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < r; ++j) s += TZ[(size_t)i * r + j] * TZ[(size_t)k * r + j];
+        TT[(size_t)i * rq + k] = s;
+      }
+    for (int i = 0; i < rq; ++i)
+      for (int j = 0; j < m; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < rq; ++k) s += TT[(size_t)i * rq + k] * o.QB[(size_t)k * m + j];
+        tK[(size_t)i * m + j] = s;
+      }
+  }
+  // H = tZ tA^T + tA tZ^T - tK tK^T + tC tC^T   (= T M T^T)
+  std::vector<double> H((size_t)rt * rt, 0.0);
+  for (int i = 0; i < rt; ++i)
+    for (int k = i; k < rt; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < r; ++j)
+        s += tZ[(size_t)i * r + j] * tA[(size_t)k * r + j] + tA[(size_t)i * r + j] * tZ[(size_t)k * r + j];
+      for (int j = 0; j < m; ++j) s -= tK[(size_t)i * m + j] * tK[(size_t)k * m + j];
+      for (int j = 0; j < p; ++j) s += tC[(size_t)i * p + j] * tC[(size_t)k * p + j];
+      H[(size_t)k * rt + i] = s;
+      H[(size_t)i * rt + k] = s;
+    }
+  std::vector<double> lam(rt), V((size_t)rt * rt);
+  CARE_REQUIRE(host_symeig(rt, H.data(), lam.data(), V.data()), CARE_ERR_SMALL_DENSE, "symeig (H)");
+  double ss = 0.0, lmax = 0.0;
+  for (double l : lam) {
+    ss += l * l;
+    lmax = std::max(lmax, std::fabs(l));
+  }
+  o.res = std::sqrt(ss);
+  CARE_REQUIRE(std::isfinite(o.res), CARE_NONFINITE, "residual not finite");
+  if (!Cout) return o;
+  const double eta = eta_rel * lmax;
+  std::vector<int> jp, jm;
+  for (int t = rt - 1; t >= 0; --t)
+    if (eta > 0 ? lam[t] >= eta : lam[t] > 0) jp.push_back(t);
+  for (int t = 0; t < rt; ++t)
+    if (eta > 0 ? lam[t] <= -eta : lam[t] < 0) jm.push_back(t);
+  o.rp = (int)jp.size();
+  o.rm = (int)jm.size();
+  const int cw = o.rp + o.rm;
+  CARE_REQUIRE(cw <= ccap, CARE_ERR_RANK_CAPACITY, "Algorithm 1: residual factor exceeds capacity");
+  if (cw == 0) return o;
+  std::vector<double> S1((size_t)rq * cw, 0.0), S2((size_t)qp * cw, 0.0);
+  for (int col = 0; col < cw; ++col) {
+    const int t = col < o.rp ? jp[col] : jm[col - o.rp];
+    const double sc = std::sqrt(std::fabs(lam[t]));
+    for (int i = 0; i < rt; ++i) {
+      const double v = V[(size_t)t * rt + i] * sc;
+      if (i < rq) S1[(size_t)i * cw + col] = v;
+      else S2[(size_t)(i - rq) * cw + col] = v;
+    }
+  }
+  gemm_ts<double, To>(n, rq, cw, 1.0, R.QZ, R.ldq, upload(c, S1), cw, 0.0, Cout, ldco, c.s);
+  if (qp) gemm_ts<double, To>(n, qp, cw, 1.0, R.Wb, R.ldbig, upload(c, S2), cw, 1.0, Cout, ldco, c.s);
+  return o;
+}
+
+// ------------------------------------------------------- Algorithm 2 ------
+// Solution factor decomposition (Algorithm 2) in FP64: G = [Z, Y] with
+// Z = Q_Z diag(s) and the new factor Y (n x ny, precision Ti) carrying signs
+// N = diag(I, sign); G = V Gamma with V = [Q_Z, Q_perp]; P = Gamma N Gamma^T;
+// keep sigma >= eta_s = eta_s_mult * u * max|sigma|; Z_new = V Theta+ Sigma+^{1/2}
+// (kept as Q_Z <- V Theta+, s <- Sigma+^{1/2}).
+template <class Ti>
+static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int nm, int ldy, double eta_mult) {
+  const int ny = np + nm;
+  CARE_REQUIRE(ny <= R.bigcap, CARE_ERR_RANK_CAPACITY, "Algorithm 2: update exceeds capacity");
+  const int r = R.r;
+  std::vector<double> sign(ny, 1.0);
+  for (int j = np; j < ny; ++j) sign[j] = -1.0;
+  if (np) copy2d<Ti, double>(n, np, Yp, ldy, 1, R.Wb, R.ldbig, 1, 1.0, c.s);
+  if (nm) copy2d<Ti, double>(n, nm, Ym, ldy, 1, R.Wb + np, R.ldbig, 1, 1.0, c.s);
+  std::vector<double> Cy = cgs2<double>(c, n, R.QZ, R.ldq, r, R.Wb, R.ldbig, ny);  // r x ny
+  std::vector<double> fl(ny, 0.0);
+  for (int j = 0; j < ny; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < r; ++i) s += Cy[(size_t)i * ny + j] * Cy[(size_t)i * ny + j];
+    fl[j] = 1e-28 * s;
+  }
+  OrthOut O = orth_rr<double>(c, n, ny, R.Wb, R.ldbig, R.Wb2, R.ldbig, 1e-12, &fl, true, 0, nullptr, 0);
+  const int qp = O.rank, rt = r + qp, sc = r + ny;
+  // Gamma (rt x sc) and P = Gamma N Gamma^T
+  std::vector<double> Gam((size_t)rt * sc, 0.0), Nd(sc);
+  for (int i = 0; i < r; ++i) {
+    Gam[(size_t)i * sc + i] = R.s[i];
+    for (int j = 0; j < ny; ++j) Gam[(size_t)i * sc + r + j] = Cy[(size_t)i * ny + j];
+  }
+  for (int i = 0; i < qp; ++i)
+    for (int j = 0; j < ny; ++j) Gam[(size_t)(r + i) * sc + r + j] = O.T[(size_t)i * ny + j];
+  for (int j = 0; j < sc; ++j) Nd[j] = j < r ? 1.0 : sign[j - r];
+  std::vector<double> Pm((size_t)rt * rt, 0.0);
+  for (int i = 0; i < rt; ++i)
+    for (int k = i; k < rt; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < sc; ++j) s += Gam[(size_t)i * sc + j] * Nd[j] * Gam[(size_t)k * sc + j];
+      Pm[(size_t)k * rt + i] = s;
+      Pm[(size_t)i * rt + k] = s;
+    }
+  std::vector<double> sig(rt), Th((size_t)rt * rt);
+  CARE_REQUIRE(host_symeig(rt, Pm.data(), sig.data(), Th.data()), CARE_ERR_SMALL_DENSE, "symeig (P)");
+  double smax = 0.0;
+  for (double v : sig) smax = std::max(smax, std::fabs(v));
+  const double eta = eta_mult * kU64 * smax;
+  std::vector<int> keep;
+  for (int t = rt - 1; t >= 0; --t)
+    if (sig[t] >= eta && sig[t] > 0.0) keep.push_back(t);
+  const int rn = (int)keep.size();
+  CARE_REQUIRE(rn <= R.rcap, CARE_ERR_RANK_CAPACITY, "solution rank exceeds r_cap");
+  std::vector<double> S1((size_t)r * rn, 0.0), S2((size_t)qp * rn, 0.0);
+  std::vector<double> snew(rn);
+  for (int col = 0; col < rn; ++col) {
+    const int t = keep[col];
+    snew[col] = std::sqrt(sig[t]);
+    for (int i = 0; i < rt; ++i) {
+      const double v = Th[(size_t)t * rt + i];
+      if (i < r) S1[(size_t)i * rn + col] = v;
+      else S2[(size_t)(i - r) * rn + col] = v;
+    }
+  }
+  if (rn) {
+    if (r) gemm_ts<double, double>(n, r, rn, 1.0, R.QZ, R.ldq, upload(c, S1), rn, 0.0, R.QZn, R.ldq, c.s);
+    gemm_ts<double, double>(n, qp, rn, 1.0, R.Wb, R.ldbig, upload(c, S2), rn, r ? 1.0 : 0.0, R.QZn, R.ldq, c.s);
+  }
+  std::swap(R.QZ, R.QZn);
+  R.r = rn;
+  R.s = snew;
+}
+
+// Z = Q_Z diag(s) into R.Zm
+static void materialize_Z(Ctx& c, Ref& R, long n) {
+  if (!R.r) return;
+  copy2d<double, double>(n, R.r, R.QZ, R.ldq, 1, R.Zm, R.ldq, 1, 1.0, c.s);
+  scale_cols<double>(n, R.r, R.Zm, R.ldq, upload(c, R.s), c.s);
+}
+
+static double res_paper(const Ctx& c, const Prob& P, const Ref& R, double res) {
+  double s4 = 0.0;
+  for (double v : R.s) s4 += v * v * v * v;
+  const double ztz = std::sqrt(s4);
+  const double den = 2.0 * c.op.a_fro * ztz + P.btb_fro * ztz * ztz + P.ctc_fro;
+  return den > 0 ? res / den : 0.0;
+}
+
+// ----------------------------------------------------------- sessions -----
+struct Caps {
+  int rcap, bcap, adicap, hcap, bigcap, maxc, small;
+};
+static Caps caps_for(int n, int m, int p, int rcap, const care_opts& o) {
+  Caps k;
+  k.rcap = std::max(rcap, 1);
+  k.bcap = std::max(2 * k.rcap + p + m, p + m);
+  k.adicap = std::max(o.adi_cap, 2 * (p + m));
+  k.hcap = 64;
+  k.bigcap = std::max(k.rcap + p, k.adicap);
+  k.maxc = std::max({k.bigcap, 2 * (k.bcap + m), k.rcap + k.bigcap});
+  const size_t rt = (size_t)k.rcap + k.bigcap;
+  k.small = (int)std::min<size_t>(rt * rt + 2 * (size_t)k.bcap * k.bcap + 2 * (size_t)(2 * (k.bcap + m)) * (2 * (k.bcap + m)) + 65536,
+                                  (size_t)1 << 30);
+  (void)n;
+  return k;
+}
+
+template <class T>
+struct Session {
+  Prob P;
+  Ref R;
+  Inner<T> in;
+  T* CtT = nullptr;  // n x p, inner precision
+  int ldct = 0;
+};
+
+template <class T>
+static void alloc_session(Ctx& c, Session<T>& S, int n, int nnz, int m, int p, const Caps& k, bool ref) {
+  alloc_small(c, n, k.maxc, k.small);
+  alloc_prob(c, S.P, n, m, p);
+  S.in.alloc(c, n, m, k.bcap, k.adicap, k.hcap);
+  S.ldct = pad_ld<T>(std::max(p, 1));
+  S.CtT = c.ar.get<T>((size_t)n * S.ldct);
+  if (ref) alloc_ref(c, S.R, n, k.rcap, k.bigcap);
+  (void)nnz;
+}
+
+static void begin(Ctx& c, const care_opts* opts, cudaStream_t s, void* work, size_t bytes) {
+  if (opts) c.o = *opts;
+  else care_opts_default(&c.o);
+  set_verbose(c.o.verbose);
+  c.s = s;
+  c.ar.base = static_cast<char*>(work);
+  c.ar.cap = bytes;
+  c.ar.off = 0;
+}
+
+// Framework 1 (Section 2) with NLR-ADI / LR-ADI inner solves in precision T.
+template <class T>
+static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ldb, int m, const double* C,
+                              int ldc, int p, double tol, double* Zout, int ldz, int r_cap, care_info* info) {
+  const double t0 = now_ms();
+  const int n = A->n;
+  const Caps k = caps_for(n, m, p, r_cap, c.o);
+  // operator first (its memory leads the workspace)
+  void* opmem = c.ar.get<char>(op_bytes(n, A->nnz));
+  Session<T> S;
+  alloc_session<T>(c, S, n, A->nnz, m, p, k, true);
+  if (c.counting()) return CARE_OK;
+  prepare_op(A, opmem, op_bytes(n, A->nnz), c.s, &c.op);
+  load_prob(c, S.P, B, ldb, C, ldc);
+  copy2d<double, T>(n, m, S.P.B64, S.P.ldb, 1, S.in.B, S.in.ldm, 1, 1.0, c.s);
+  copy2d<double, T>(n, p, S.P.Ct64, S.P.ldc, 1, S.CtT, S.ldct, 1, 1.0, c.s);
+  const bool lo = sizeof(T) == 4;
+  const double tauL = lo ? c.o.tau_L_lo : c.o.tau_L_hi;
+  const double tauN = lo ? c.o.tau_N_lo : c.o.tau_N_hi;
+  care_info inf{};
+  // 1. initial approximation by NLR-ADI in u_s
+  double t1 = now_ms();
+  NlrResult nr = nlradi<T>(c, S.in, S.CtT, S.ldct, p, tauL, tauN, c.o.newton_max, c.o.jmax);
+  inf.iter0_outer = nr.newton;
+  inf.iter0_inner = nr.adi;
+  // store Z_1 in u (FP64): compress [Z_1] with N = I (Algorithm 2 on G = Z_1)
+  S.R.r = 0;
+  S.R.s.clear();
+  alg2<T>(c, S.R, n, S.in.Z, nr.cols, nullptr, 0, S.in.ldz, c.o.eta_s_mult);
+  CARE_CUDA(cudaStreamSynchronize(c.s));
+  inf.ms_phase[0] += now_ms() - t1;
+  care_status st = CARE_NOT_CONVERGED;
+  double prev = -1.0, res = 0.0;
+  for (int it = 1; it <= c.o.kmax + 1; ++it) {
+    t1 = now_ms();
+    materialize_Z(c, S.R, n);
+    std::vector<double> TZ((size_t)S.R.r * S.R.r, 0.0);
+    for (int i = 0; i < S.R.r; ++i) TZ[(size_t)i * S.R.r + i] = S.R.s[i];
+    Alg1Out a1 = alg1<T>(c, S.P, S.R, S.R.r, TZ, S.R.r, c.o.eta_r_rel, S.in.W0, S.in.ldw, S.in.bcap);
+    CARE_CUDA(cudaStreamSynchronize(c.s));
+    inf.ms_phase[1] += now_ms() - t1;
+    res = a1.res;
+    const double rel = S.P.ctc_fro > 0 ? res / S.P.ctc_fro : res;
+    if (inf.nhist < CARE_HIST_MAX) inf.res_hist[inf.nhist++] = rel;
+    inf.iter_outer = it;
+    if (verbose_level() >= 1)
+      fprintf(stderr, "[care] refine k=%d rank=%d res=%.3e rp=%d rm=%d\n", it, S.R.r, rel, a1.rp, a1.rm);
+    if (rel <= tol) {
+      st = CARE_OK;
+      break;
+    }
+    if (prev > 0 && res / prev > c.o.stag_ratio) {
+      st = CARE_STAGNATED;
+      break;
+    }
+    if (it == c.o.kmax + 1) break;
+    prev = res;
+    // K_k = Z Z^T B = Q_Z (s^2 .* Q_Z^T B) in u_s
+    const int r = S.R.r;
+    std::vector<double> KB((size_t)r * m);
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < m; ++j) KB[(size_t)i * m + j] = S.R.s[i] * S.R.s[i] * a1.QB[(size_t)i * m + j];
+    gemm_ts<double, T>(n, r, m, 1.0, S.R.QZ, S.R.ldq, upload(c, KB), m, 0.0, S.in.K, S.in.ldm, c.s);
+    t1 = now_ms();
+    const int bw = a1.rp + a1.rm;
+    AdiResult ad = lradi<T>(c, S.in, bw, a1.rp, true, tauL, c.o.jmax, false);
+    inf.iter_inner += ad.steps;
+    CARE_CUDA(cudaStreamSynchronize(c.s));
+    inf.ms_phase[2] += now_ms() - t1;
+    t1 = now_ms();
+    alg2<T>(c, S.R, n, S.in.Z, ad.np, S.in.Z + (S.in.adicap - ad.nm), ad.nm, S.in.ldz, c.o.eta_s_mult);
+    CARE_CUDA(cudaStreamSynchronize(c.s));
+    inf.ms_phase[3] += now_ms() - t1;
+  }
+  // output Z = Q_Z diag(s), column-major FP64
+  CARE_REQUIRE(S.R.r <= r_cap, CARE_ERR_RANK_CAPACITY, "rank exceeds r_cap");
+  materialize_Z(c, S.R, n);
+  if (S.R.r) copy2d<double, double>(n, S.R.r, S.R.Zm, S.R.ldq, 1, Zout, 1, ldz, 1.0, c.s);
+  CARE_CUDA(cudaStreamSynchronize(c.s));
+  inf.status = st;
+  inf.rank = S.R.r;
+  inf.res_rel_CtC = S.P.ctc_fro > 0 ? res / S.P.ctc_fro : res;
+  inf.res_paper = res_paper(c, S.P, S.R, res);
+  inf.krylov_iters = c.krylov_iters;
+  inf.spmm_calls = c.spmm_calls;
+  inf.krylov_unconverged = c.krylov_unconverged;
+  inf.ms_total = now_ms() - t0;
+  if (info) *info = inf;
+  return st;
+}
+
+template <class T>
+static care_status lradi_impl(Ctx& c, const care_csr* A, const double* B, int ldb, const double* K, int ldk,
+                              int m, const double* W, int ldw, int b, double tol, double* Zout, int ldz,
+                              int r_cap, care_info* info) {
+  const double t0 = now_ms();
+  const int n = A->n;
+  care_opts o2 = c.o;
+  o2.adi_cap = std::max(c.o.adi_cap, r_cap);
+  const Caps k = caps_for(n, std::max(m, 1), b, 1, o2);
+  void* opmem = c.ar.get<char>(op_bytes(n, A->nnz));
+  Session<T> S;
+  alloc_session<T>(c, S, n, A->nnz, std::max(m, 1), b, k, false);
+  if (c.counting()) return CARE_OK;
+  prepare_op(A, opmem, op_bytes(n, A->nnz), c.s, &c.op);
+  const bool hasK = m > 0 && B && K;
+  if (hasK) {
+    copy2d<double, T>(n, m, B, 1, ldb, S.in.B, S.in.ldm, 1, 1.0, c.s);
+    copy2d<double, T>(n, m, K, 1, ldk, S.in.K, S.in.ldm, 1, 1.0, c.s);
+  } else {
+    S.in.m = 0;
+  }
+  copy2d<double, T>(n, b, W, 1, ldw, S.in.W0, S.in.ldw, 1, 1.0, c.s);
+  AdiResult a = lradi<T>(c, S.in, b, b, hasK, tol, c.o.jmax, false);
+  CARE_REQUIRE(a.np <= r_cap, CARE_ERR_RANK_CAPACITY, "LR-ADI factor exceeds r_cap");
+  if (a.np) copy2d<T, double>(n, a.np, S.in.Z, S.in.ldz, 1, Zout, 1, ldz, 1.0, c.s);
+  CARE_CUDA(cudaStreamSynchronize(c.s));
+  care_info inf{};
+  inf.rank = a.np;
+  inf.iter_inner = a.steps;
+  inf.krylov_iters = c.krylov_iters;
+  inf.spmm_calls = c.spmm_calls;
+  inf.krylov_unconverged = c.krylov_unconverged;
+  inf.res_rel_CtC = a.res;
+  inf.status = a.converged ? CARE_OK : CARE_NOT_CONVERGED;
+  inf.ms_total = now_ms() - t0;
+  if (info) *info = inf;
+  return (care_status)inf.status;
+}
+
+static care_status resfac_impl(Ctx& c, const care_csr* A, const double* B, int ldb, int m, const double* C,
+                               int ldc, int p, const double* Z, int ldz, int r, double eta_r_rel, double* Cp,
+                               int ldcp, int* rp, double* Cm, int ldcm, int* rm, int c_cap, double* res_fro) {
+  const int n = A->n;
+  care_opts o2 = c.o;
+  o2.adi_cap = 1;
+  const Caps k = caps_for(n, m, p, std::max(r, 1), o2);
+  void* opmem = c.ar.get<char>(op_bytes(n, A->nnz));
+  Prob P;
+  Ref R;
+  alloc_small(c, n, k.maxc, k.small);
+  alloc_prob(c, P, n, m, p);
+  alloc_ref(c, R, n, k.rcap, std::max(k.rcap + p, k.rcap));
+  const int ccap = std::max(c_cap, 0);
+  const int ldo = pad_ld<double>(std::max(2 * k.rcap + m + p, 1));
+  double* Cout = c.ar.get<double>((size_t)n * ldo);
+  if (c.counting()) return CARE_OK;
+  prepare_op(A, opmem, op_bytes(n, A->nnz), c.s, &c.op);
+  load_prob(c, P, B, ldb, C, ldc);
+  // Z (column-major) -> row-major; orthonormal basis Q_Z with Z = Q_Z T_Z
+  std::vector<double> TZ;
+  int rq = 0;
+  if (r) {
+    copy2d<double, double>(n, r, Z, 1, ldz, R.Zm, R.ldq, 1, 1.0, c.s);
+    copy2d<double, double>(n, r, R.Zm, R.ldq, 1, R.QZ, R.ldq, 1, 1.0, c.s);
+    OrthOut O = orth_rr<double>(c, n, r, R.QZ, R.ldq, R.QZn, R.ldq, 1e-12, nullptr, true, 0, nullptr, 0);
+    rq = O.rank;
+    TZ = O.T;
+  }
+  const bool want = Cp != nullptr || Cm != nullptr;
+  Alg1Out a = alg1<double>(c, P, R, rq, TZ, r, eta_r_rel, want ? Cout : nullptr, ldo, 2 * k.rcap + m + p);
+  if (res_fro) *res_fro = a.res;
+  if (rp) *rp = a.rp;
+  if (rm) *rm = a.rm;
+  if (want) {
+    CARE_REQUIRE(a.rp <= ccap && a.rm <= ccap, CARE_ERR_RANK_CAPACITY, "residual factor exceeds c_cap");
+    if (Cp && a.rp) copy2d<double, double>(n, a.rp, Cout, ldo, 1, Cp, 1, ldcp, 1.0, c.s);
+    if (Cm && a.rm) copy2d<double, double>(n, a.rm, Cout + a.rp, ldo, 1, Cm, 1, ldcm, 1.0, c.s);
+  }
+  CARE_CUDA(cudaStreamSynchronize(c.s));
+  return CARE_OK;
+}
+
+template <class T>
+static care_status shifted_impl(Ctx& c, const care_op* op, const double* B, int ldb, const double* K, int ldk,
+                                int m, double pre, double pim, const double* W, int ldw, int b, double* V,
+                                int ldv, int* iters) {
+  const long n = op->n;
+  Inner<T> in;
+  alloc_small(c, n, 2 * (b + m) + 64, 4 * (b + m + 8) * (b + m + 8) + 65536);
+  in.alloc(c, (int)n, std::max(m, 1), b, 1, 1);
+  if (c.counting()) return CARE_OK;
+  c.op = *op;
+  const bool hasK = m > 0 && K != nullptr && B != nullptr;
+  if (hasK) {
+    copy2d<double, T>(n, m, B, 1, ldb, in.B, in.ldm, 1, 1.0, c.s);
+    copy2d<double, T>(n, m, K, 1, ldk, in.K, in.ldm, 1, 1.0, c.s);
+  }
+  copy2d<double, T>(n, b, W, 1, ldw, in.W, in.ldw, 1, 1.0, c.s);
+  // the SMW solve of the LR-ADI step, without the ADI update
+  const long long it0 = c.krylov_iters;
+  smw_solve_public<T>(c, in, pre, pim, b, hasK);
+  const bool cplx = pim != 0.0;
+  if (cplx) {
+    // complex interleaved column-major output: re/im of entry (i, j) at 2(i + j ldv) (+1)
+    copy2d<T, double>(n, b, in.SOL, in.ldr, 2, V, 2, 2L * ldv, 1.0, c.s);
+    copy2d<T, double>(n, b, in.SOL + 1, in.ldr, 2, V + 1, 2, 2L * ldv, 1.0, c.s);
+  } else {
+    copy2d<T, double>(n, b, in.SOL, in.ldr, 1, V, 1, ldv, 1.0, c.s);
+  }
+  CARE_CUDA(cudaStreamSynchronize(c.s));
+  if (iters) *iters = (int)(c.krylov_iters - it0);
+  return c.krylov_unconverged ? CARE_INNER_FAILED : CARE_OK;
+}
+
+}  // namespace care
+
+// ================================================================ C ABI ====
+using namespace care;
+
+static care_status run_guarded(const std::function<care_status()>& f) {
+  try {
+    return f();
+  } catch (const CudaError& e) {
+    if (verbose_level() > 0) fprintf(stderr, "[care] CUDA error %s at %s (line %d)\n", cudaGetErrorString(e.err), e.what, e.line);
+    return CARE_ERR_CUDA;
+  } catch (const StatusError& e) {
+    if (verbose_level() > 0) fprintf(stderr, "[care] %s: %s\n", care_status_string(e.status), e.what);
+    return e.status;
+  } catch (...) {
+    return CARE_ERR_CUDA;
+  }
+}
+
+extern "C" {
+
+void care_opts_default(care_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->kmax = 20;
+  o->jmax = 50;
+  o->newton_max = 50;
+  o->adi_cap = 1024;
+  o->eta_r_rel = 1e-4;
+  o->eta_s_mult = 10.0;
+  o->tau_L_lo = 1e-5;
+  o->tau_L_hi = 1e-12;
+  o->tau_N_lo = 1e-5;
+  o->tau_N_hi = 1e-10;
+  o->krylov_tol_lo = 1e-5;
+  o->krylov_tol_hi = 1e-10;
+  o->krylov_maxit_lo = 100;
+  o->krylov_maxit_hi = 200;
+  o->krylov = CARE_KRYLOV_BICGSTAB;
+  o->precond = CARE_PRECOND_JACOBI;
+  o->krylov_chunk = 64;
+  o->stag_ratio = 0.999;
+  o->shift_hmin = 4;
+  o->verbose = 0;
+}
+
+const char* care_status_string(int s) {
+  switch (s) {
+    case CARE_OK: return "CARE_OK";
+    case CARE_ERR_INVALID_ARG: return "CARE_ERR_INVALID_ARG";
+    case CARE_ERR_CUDA: return "CARE_ERR_CUDA";
+    case CARE_ERR_WORKSPACE: return "CARE_ERR_WORKSPACE";
+    case CARE_ERR_RANK_CAPACITY: return "CARE_ERR_RANK_CAPACITY";
+    case CARE_NOT_CONVERGED: return "CARE_NOT_CONVERGED";
+    case CARE_STAGNATED: return "CARE_STAGNATED";
+    case CARE_INNER_FAILED: return "CARE_INNER_FAILED";
+    case CARE_UNSTABLE: return "CARE_UNSTABLE";
+    case CARE_NONFINITE: return "CARE_NONFINITE";
+    case CARE_ERR_SMALL_DENSE: return "CARE_ERR_SMALL_DENSE";
+    default: return "CARE_UNKNOWN_STATUS";
+  }
+}
+
+const char* care_version(void) {
+  return "b300-care 0.1 (sm_103a, CUDA " CARE_STR(__CUDACC_VER_MAJOR__) "." CARE_STR(__CUDACC_VER_MINOR__) ")";
+}
+
+care_status care_op_size(int n, int nnz, size_t* bytes) {
+  if (n < 0 || nnz < 0 || !bytes) return CARE_ERR_INVALID_ARG;
+  *bytes = op_bytes(n, nnz);
+  return CARE_OK;
+}
+
+care_status care_op_prepare(const care_csr* A, void* mem, size_t bytes, care_stream_t s, care_op* op) {
+  if (!A || !op || A->n < 0 || A->nnz < 0 || (A->n > 0 && (!A->rowptr || !mem))) return CARE_ERR_INVALID_ARG;
+  if (A->nnz > 0 && (!A->colind || !A->val)) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    prepare_op(A, mem, bytes, (cudaStream_t)s, op);
+    return CARE_OK;
+  });
+}
+
+care_status care_spmm(const care_op* op, int dtype, int cplx, double pre, double pim, const void* X, int ldx,
+                      int b, void* Y, int ldy, care_stream_t s) {
+  if (!op || b < 0 || (dtype != 0 && dtype != 1) || (!cplx && pim != 0.0)) return CARE_ERR_INVALID_ARG;
+  const int w = cplx ? 2 * b : b;
+  if (ldx < w || ldy < w || (op->n > 0 && b > 0 && (!X || !Y))) return CARE_ERR_INVALID_ARG;
+  const int vec = dtype == 0 ? 2 : 4;
+  if (ldx % vec || ldy % vec || ((uintptr_t)X % 16) || ((uintptr_t)Y % 16)) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    if (dtype == 0)
+      spmm<double>(op64(*op), cd{pre, pim}, cplx != 0, (const double*)X, ldx, (double*)Y, ldy, w, (cudaStream_t)s);
+    else
+      spmm<float>(op32(*op), cd{pre, pim}, cplx != 0, (const float*)X, ldx, (float*)Y, ldy, w, (cudaStream_t)s);
+    return CARE_OK;
+  });
+}
+
+size_t care_gram_work_size(int n, int a, int b) { return gram_work_elems(n, a, b) * sizeof(double); }
+
+care_status care_gram(int dtype, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy, double* G,
+                      int ldg, void* work, size_t work_bytes, care_stream_t s) {
+  if (n < 0 || a < 0 || b < 0 || (dtype != 0 && dtype != 1) || ldx < a || ldy < b || ldg < b) return CARE_ERR_INVALID_ARG;
+  if (a > 0 && b > 0 && (!G || !work || (n > 0 && (!X || !Y)))) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    const size_t el = work_bytes / sizeof(double);
+    if (dtype == 0) gram<double>(n, a, b, (const double*)X, ldx, (const double*)Y, ldy, G, ldg, (double*)work, el, (cudaStream_t)s);
+    else gram<float>(n, a, b, (const float*)X, ldx, (const float*)Y, ldy, G, ldg, (double*)work, el, (cudaStream_t)s);
+    return CARE_OK;
+  });
+}
+
+care_status care_shifted_solve_workspace_size(const care_op* op, int m, int b, care_prec prec, const care_opts* opts,
+                                              size_t* bytes) {
+  if (!op || !bytes || m < 0 || b <= 0) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    Ctx c;
+    begin(c, opts, nullptr, nullptr, 0);
+    c.op = *op;
+    if (prec == CARE_PREC_FP64)
+      shifted_impl<double>(c, op, nullptr, 0, nullptr, 0, m, 0, 0, nullptr, 0, b, nullptr, 0, nullptr);
+    else
+      shifted_impl<float>(c, op, nullptr, 0, nullptr, 0, m, 0, 0, nullptr, 0, b, nullptr, 0, nullptr);
+    *bytes = c.ar.peak + 256;
+    return CARE_OK;
+  });
+}
+
+care_status care_shifted_solve(const care_op* op, const double* B, int ldb, const double* K, int ldk, int m,
+                               double pre, double pim, const double* W, int ldw, int b, care_prec prec,
+                               const care_opts* opts, double* V, int ldv, void* work, size_t work_bytes,
+                               care_stream_t s, int* iters) {
+  if (!op || !W || !V || b <= 0 || m < 0 || ldw < op->n || ldv < op->n || !work) return CARE_ERR_INVALID_ARG;
+  if (m > 0 && K && (!B || ldb < op->n || ldk < op->n)) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    Ctx c;
+    begin(c, opts, (cudaStream_t)s, work, work_bytes);
+    if (prec == CARE_PREC_FP64)
+      return shifted_impl<double>(c, op, B, ldb, K, ldk, K ? m : 0, pre, pim, W, ldw, b, V, ldv, iters);
+    return shifted_impl<float>(c, op, B, ldb, K, ldk, K ? m : 0, pre, pim, W, ldw, b, V, ldv, iters);
+  });
+}
+
+care_status care_workspace_size(int n, int nnz, int m, int p, int r_cap, care_prec prec, const care_opts* opts,
+                                size_t* bytes) {
+  if (n < 0 || nnz < 0 || m < 0 || p < 0 || r_cap <= 0 || !bytes) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    size_t best = 0;
+    for (int mode = 0; mode < 3; ++mode) {
+      Ctx c;
+      begin(c, opts, nullptr, nullptr, 0);
+      care_csr A{n, nnz, nullptr, nullptr, nullptr};
+      if (mode == 0) {
+        if (prec == CARE_PREC_FP64) solve_impl<double>(c, &A, nullptr, n, m, nullptr, p, p, 0, nullptr, n, r_cap, nullptr);
+        else solve_impl<float>(c, &A, nullptr, n, m, nullptr, p, p, 0, nullptr, n, r_cap, nullptr);
+      } else if (mode == 1) {
+        // lyap_lradi with right-hand side width p and feedback width m
+        if (prec == CARE_PREC_FP64) lradi_impl<double>(c, &A, nullptr, n, nullptr, n, m, nullptr, n, p, 0, nullptr, n, r_cap, nullptr);
+        else lradi_impl<float>(c, &A, nullptr, n, nullptr, n, m, nullptr, n, p, 0, nullptr, n, r_cap, nullptr);
+      } else {
+        resfac_impl(c, &A, nullptr, n, m, nullptr, p, p, nullptr, n, r_cap, 0, nullptr, n, nullptr, nullptr, n, nullptr, 0, nullptr);
+      }
+      best = std::max(best, c.ar.peak);
+    }
+    *bytes = best + 256;
+    return CARE_OK;
+  });
+}
+
+care_status care_solve(const care_csr* A, const double* B, int ldb, int m, const double* C, int ldc, int p,
+                       double tol, care_prec prec, const care_opts* opts, double* Z, int ldz, int r_cap, void* work,
+                       size_t work_bytes, care_stream_t s, care_info* info) {
+  if (!A || A->n <= 0 || m <= 0 || p <= 0 || !B || !C || !Z || !work || ldb < A->n || ldc < p || ldz < A->n ||
+      r_cap <= 0 || !(tol > 0))
+    return CARE_ERR_INVALID_ARG;
+  if (!A->rowptr || !A->colind || !A->val) return CARE_ERR_INVALID_ARG;
+  care_status st = run_guarded([&] {
+    Ctx c;
+    begin(c, opts, (cudaStream_t)s, work, work_bytes);
+    if (prec == CARE_PREC_FP64) return solve_impl<double>(c, A, B, ldb, m, C, ldc, p, tol, Z, ldz, r_cap, info);
+    return solve_impl<float>(c, A, B, ldb, m, C, ldc, p, tol, Z, ldz, r_cap, info);
+  });
+  if (info) info->status = st;
+  return st;
+}
+
+care_status lyap_lradi(const care_csr* A, const double* B, int ldb, const double* K, int ldk, int m, const double* W,
+                       int ldw, int b, double tol, care_prec prec, const care_opts* opts, double* Z, int ldz,
+                       int r_cap, void* work, size_t work_bytes, care_stream_t s, care_info* info) {
+  if (!A || A->n <= 0 || b <= 0 || !W || !Z || !work || ldw < A->n || ldz < A->n || r_cap <= 0 || !(tol > 0))
+    return CARE_ERR_INVALID_ARG;
+  if (m > 0 && B && K && (ldb < A->n || ldk < A->n)) return CARE_ERR_INVALID_ARG;
+  care_status st = run_guarded([&] {
+    Ctx c;
+    begin(c, opts, (cudaStream_t)s, work, work_bytes);
+    const int mm = (B && K) ? m : 0;
+    if (prec == CARE_PREC_FP64) return lradi_impl<double>(c, A, B, ldb, K, ldk, mm, W, ldw, b, tol, Z, ldz, r_cap, info);
+    return lradi_impl<float>(c, A, B, ldb, K, ldk, mm, W, ldw, b, tol, Z, ldz, r_cap, info);
+  });
+  if (info) info->status = st;
+  return st;
+}
+
+care_status care_residual_factor(const care_csr* A, const double* B, int ldb, int m, const double* C, int ldc, int p,
+                                 const double* Z, int ldz, int r, double eta_r_rel, double* Cp, int ldcp, int* rp,
+                                 double* Cm, int ldcm, int* rm, int c_cap, double* res_fro, void* work,
+                                 size_t work_bytes, care_stream_t s) {
+  if (!A || A->n <= 0 || m <= 0 || p <= 0 || r < 0 || !B || !C || (r > 0 && !Z) || !work || ldb < A->n ||
+      ldc < p || (r > 0 && ldz < A->n) || eta_r_rel < 0)
+    return CARE_ERR_INVALID_ARG;
+  if ((Cp && ldcp < A->n) || (Cm && ldcm < A->n)) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    Ctx c;
+    begin(c, nullptr, (cudaStream_t)s, work, work_bytes);
+    return resfac_impl(c, A, B, ldb, m, C, ldc, p, Z, ldz, r, eta_r_rel, Cp, ldcp, rp, Cm, ldcm, rm, c_cap, res_fro);
+  });
+}
+
+unsigned long long care_kernel_launches(void) { return care::launches(); }
+
+care_status care_host_symeig(int n, const double* A, double* w, double* V) {
+  if (n < 0 || (n > 0 && (!A || !w))) return CARE_ERR_INVALID_ARG;
+  return host_symeig(n, A, w, V) ? CARE_OK : CARE_ERR_SMALL_DENSE;
+}
+
+care_status care_host_eigvals(int n, const double* A, double* wr, double* wi) {
+  if (n < 0 || (n > 0 && (!A || !wr || !wi))) return CARE_ERR_INVALID_ARG;
+  return host_eigvals(n, A, wr, wi) ? CARE_OK : CARE_ERR_SMALL_DENSE;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Shared utilities of the CARE library: error handling, workspace arena,
+// small complex helpers and the launch geometry of the row-block kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "care_b300.h"
+
+namespace care {
+
+// ---------------------------------------------------------------- errors --
+struct CudaError {
+  cudaError_t err;
+  const char* what;
+  int line;
+};
+struct StatusError {
+  care_status status;
+  const char* what;
+};
+
+#define CARE_CUDA(x)                                                         \
+  do {                                                                       \
+    cudaError_t care_e_ = (x);                                               \
+    if (care_e_ != cudaSuccess) throw ::care::CudaError{care_e_, #x, __LINE__}; \
+  } while (0)
+// every kernel launch site ends with CARE_LAUNCH(): it checks the launch and
+// counts it (care_kernel_launches)
+void count_launch();
+#define CARE_LAUNCH()               \
+  do {                              \
+    ::care::count_launch();         \
+    CARE_CUDA(cudaGetLastError());  \
+  } while (0)
+#define CARE_THROW(st, msg) throw ::care::StatusError{st, msg}
+#define CARE_REQUIRE(cond, st, msg) \
+  do {                              \
+    if (!(cond)) CARE_THROW(st, msg); \
+  } while (0)
+
+int device_sms();          // SM count of the current device (cached per device)
+int verbose_level();       // set per call from care_opts.verbose
+void set_verbose(int v);
+
+// --------------------------------------------------------------- arena ----
+// Bump allocator over caller-provided device memory.  With base == nullptr it
+// only counts, which is how the workspace queries are answered: the query runs
+// the same allocation sequence as the solver.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  size_t peak = 0;
+  bool counting() const { return base == nullptr; }
+  template <class T>
+  T* get(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    if (!counting() && off + bytes > cap) CARE_THROW(CARE_ERR_WORKSPACE, "workspace too small");
+    T* p = counting() ? nullptr : reinterpret_cast<T*>(base + off);
+    off += bytes;
+    if (off > peak) peak = off;
+    return p;
+  }
+  size_t mark() const { return off; }
+  void release(size_t m) { off = m; }
+};
+
+// -------------------------------------------------------------- complex ---
+struct cd {
+  double re, im;
+};
+__host__ __device__ inline cd cmul(cd a, cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__host__ __device__ inline cd cdivz(cd a, cd b) {
+  // Smith's algorithm (Smith 1962) for a / b.
+  if (fabs(b.re) >= fabs(b.im)) {
+    double r = b.im / b.re, d = b.re + b.im * r;
+    return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+  }
+  double r = b.re / b.im, d = b.im + b.re * r;
+  return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+}
+__host__ __device__ inline cd cconj(cd a) { return {a.re, -a.im}; }
+
+// ------------------------------------------------------------ vectors -----
+template <class T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+template <class T>
+__device__ __forceinline__ void vload(const T* p, T (&v)[16 / sizeof(T)]) {
+  using V = typename Vec<T>::type;
+  V x = *reinterpret_cast<const V*>(p);
+  if constexpr (sizeof(T) == 4) {
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    v[0] = x.x; v[1] = x.y;
+  }
+}
+template <class T>
+__device__ __forceinline__ void vstore(T* p, const T (&v)[16 / sizeof(T)]) {
+  using V = typename Vec<T>::type;
+  V x;
+  if constexpr (sizeof(T) == 4) {
+    x.x = v[0]; x.y = v[1]; x.z = v[2]; x.w = v[3];
+  } else {
+    x.x = v[0]; x.y = v[1];
+  }
+  *reinterpret_cast<V*>(p) = x;
+}
+
+// Leading dimension (in reals) of a row-major block with `cols` real columns:
+// padded to a whole number of 16-byte vectors.
+template <class T>
+inline int pad_ld(int cols) {
+  const int v = 16 / sizeof(T);
+  return ((cols + v - 1) / v) * v;
+}
+
+// Threads per row for a row of `nvec` 16-byte vectors: the smallest power of two
+// >= nvec, at most 32; rows wider than 32 vectors loop (NVPT vectors per thread).
+inline int tpr_for(int nvec) {
+  int t = 1;
+  while (t < nvec && t < 32) t <<= 1;
+  return t;
+}
+
+constexpr int kBlock = 256;    // threads per CTA of the row-block kernels
+constexpr int kMaxRealCols = 128;  // widest row-block handled by the fused kernels
+
+inline int grid_rows(long rows, int tpr, int ctas_per_sm = 4) {
+  long rows_per_cta = (kBlock / 32) * (32 / tpr);
+  long need = (rows + rows_per_cta - 1) / rows_per_cta;
+  long cap = (long)device_sms() * ctas_per_sm;
+  long g = need < cap ? need : cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace care

@@ -1,0 +1,47 @@
+// Tall-skinny dense kernels: Gram matrices X^T Y, block products X S, layout
+// conversions, and the host small-dense routines.
+#pragma once
+
+#include "common.cuh"
+
+namespace care {
+
+// G (a x b, row-major, FP64, ldg) = X^T Y for row-major X (n x a) and Y (n x b).
+size_t gram_work_elems(long n, int a, int b);
+template <class T>
+void gram(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double* G, int ldg,
+          double* work, size_t work_elems, cudaStream_t s);
+
+// Y (n x b, row-major To, ldy) = alpha X S + beta Y,  X row-major Ti (n x a, ldx),
+// S device FP64 row-major (a x b, lds).
+template <class Ti, class To>
+void gemm_ts(long n, int a, int b, double alpha, const Ti* X, int ldx, const double* S, int lds,
+             double beta, To* Y, int ldy, cudaStream_t s);
+
+// dst(i, j) = scale * src(i, j) for i < rows, j < cols with independent row
+// and column strides (any layout; a 32x32 shared-memory tile makes both sides
+// coalesced when one is row-major and the other column-major).
+template <class Ti, class To>
+void copy2d(long rows, int cols, const Ti* src, long src_rs, long src_cs, To* dst, long dst_rs,
+            long dst_cs, double scale, cudaStream_t s);
+
+// Y = alpha X + beta Y (row-major, same shape)
+template <class T>
+void axpby(long n, int cols, double alpha, const T* X, int ldx, double beta, T* Y, int ldy,
+           cudaStream_t s);
+
+// Y(:, j) *= d[j] (row-major; d on device, FP64)
+template <class T>
+void scale_cols(long n, int cols, T* Y, int ldy, const double* d, cudaStream_t s);
+
+// ---- host small dense (column-major) ---------------------------------------
+// symmetric eigendecomposition, ascending eigenvalues; V may be null
+bool host_symeig(int n, const double* A, double* w, double* V);
+// eigenvalues of a general real matrix
+bool host_eigvals(int n, const double* A, double* wr, double* wi);
+// upper Cholesky factor of SPD G = R^T R (column-major); false if not SPD
+bool host_cholesky_upper(int n, const double* G, double* R);
+// complex LU solve A X = B (A n x n col-major, B n x k col-major), in place on B
+bool host_lu_solve_complex(int n, std::vector<cd> A, cd* B, int k);
+
+}  // namespace care

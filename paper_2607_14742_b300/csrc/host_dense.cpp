@@ -1,0 +1,375 @@
+// Small dense host routines for the q x q, s x s, h x h and m x m matrices of
+// Algorithms 1-2, the projection shifts and the SMW capacitance matrix.
+// Textbook algorithms (Golub & Van Loan, Matrix Computations, 4th ed.):
+//   symmetric eigenproblem: Householder tridiagonalisation (Alg. 8.3.1) and the
+//     implicit symmetric QR step with Wilkinson shift (Alg. 8.3.2) with
+//     deflation, rotations accumulated into the eigenvector matrix;
+//   nonsymmetric eigenvalues: Householder Hessenberg reduction (Alg. 7.4.2) and
+//     the Francis double-shift QR step (Alg. 7.5.1) with deflation;
+//   Cholesky (Alg. 4.2.2) and LU with partial pivoting (Alg. 3.4.1).
+// All matrices are column-major.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dense.cuh"
+
+namespace care {
+
+namespace {
+
+inline double& at(std::vector<double>& a, int n, int i, int j) { return a[(size_t)j * n + i]; }
+
+// Givens pair (c, s) with [c s; -s c]^T [x; z] = [r; 0].
+inline void givens(double x, double z, double& c, double& s) {
+  if (z == 0.0) {
+    c = 1.0;
+    s = 0.0;
+  } else if (std::fabs(z) > std::fabs(x)) {
+    const double t = -x / z;
+    s = 1.0 / std::sqrt(1.0 + t * t);
+    c = s * t;
+  } else {
+    const double t = -z / x;
+    c = 1.0 / std::sqrt(1.0 + t * t);
+    s = c * t;
+  }
+}
+
+}  // namespace
+
+bool host_symeig(int n, const double* A, double* w, double* V) {
+  if (n <= 0) return true;
+  std::vector<double> a(A, A + (size_t)n * n);
+  // symmetrise (callers pass numerically symmetric matrices)
+  for (int j = 0; j < n; ++j)
+    for (int i = j + 1; i < n; ++i) {
+      const double s = 0.5 * (at(a, n, i, j) + at(a, n, j, i));
+      at(a, n, i, j) = s;
+      at(a, n, j, i) = s;
+    }
+  std::vector<double> Q;
+  const bool vec = V != nullptr;
+  if (vec) {
+    Q.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  }
+  // 1. Householder tridiagonalisation: A <- H_k A H_k, Q <- Q H_k
+  std::vector<double> v(n), p(n), wv(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double xnorm = 0.0;
+    for (int i = 0; i < m; ++i) xnorm = std::hypot(xnorm, at(a, n, k + 1 + i, k));
+    if (xnorm == 0.0) continue;
+    const double x0 = at(a, n, k + 1, k);
+    const double alpha = x0 > 0 ? -xnorm : xnorm;
+    for (int i = 0; i < m; ++i) v[i] = at(a, n, k + 1 + i, k);
+    v[0] -= alpha;
+    double vn2 = 0.0;
+    for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
+    if (vn2 == 0.0) continue;
+    const double beta = 2.0 / vn2;
+    // p = beta * A22 v
+    for (int i = 0; i < m; ++i) p[i] = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double vj = v[j];
+      const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
+      for (int i = 0; i < m; ++i) p[i] += col[i] * vj;
+    }
+    double pv = 0.0;
+    for (int i = 0; i < m; ++i) {
+      p[i] *= beta;
+      pv += p[i] * v[i];
+    }
+    const double K = 0.5 * beta * pv;
+    for (int i = 0; i < m; ++i) wv[i] = p[i] - K * v[i];
+    for (int j = 0; j < m; ++j) {
+      double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
+      const double vj = v[j], wj = wv[j];
+      for (int i = 0; i < m; ++i) col[i] -= v[i] * wj + wv[i] * vj;
+    }
+    at(a, n, k + 1, k) = alpha;
+    at(a, n, k, k + 1) = alpha;
+    for (int i = k + 2; i < n; ++i) {
+      at(a, n, i, k) = 0.0;
+      at(a, n, k, i) = 0.0;
+    }
+    if (vec) {
+      // Q[:, k+1:] -= beta (Q[:, k+1:] v) v^T
+      for (int r = 0; r < n; ++r) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += Q[(size_t)(k + 1 + i) * n + r] * v[i];
+        s *= beta;
+        for (int i = 0; i < m; ++i) Q[(size_t)(k + 1 + i) * n + r] -= s * v[i];
+      }
+    }
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = at(a, n, i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = at(a, n, i + 1, i);
+  // 2. implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e)
+  const double eps = 2.220446049250313e-16;
+  int u = n - 1;
+  int iters = 0;
+  while (u > 0) {
+    // deflate negligible off-diagonals at the bottom
+    if (std::fabs(e[u - 1]) <= eps * (std::fabs(d[u - 1]) + std::fabs(d[u]))) {
+      e[u - 1] = 0.0;
+      --u;
+      iters = 0;
+      continue;
+    }
+    int l = u - 1;
+    while (l > 0 && std::fabs(e[l - 1]) > eps * (std::fabs(d[l - 1]) + std::fabs(d[l]))) --l;
+    if (l > 0) e[l - 1] = 0.0;
+    if (++iters > 60 * n) return false;
+    // Wilkinson shift from the trailing 2 x 2 block
+    const double dd = 0.5 * (d[u - 1] - d[u]);
+    const double eu = e[u - 1];
+    const double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::hypot(dd, eu);
+    const double mu = d[u] - (den != 0.0 ? eu * eu / den : 0.0);
+    double x = d[l] - mu, z = e[l];
+    double bulge = 0.0;
+    for (int k = l; k < u; ++k) {
+      double c, s;
+      givens(x, z, c, s);
+      // rotate rows/cols k, k+1 of T (symmetric tridiagonal + bulge)
+      if (k > l) e[k - 1] = c * e[k - 1] - s * bulge;
+      const double dk = d[k], dk1 = d[k + 1], ek = e[k];
+      d[k] = c * c * dk - 2.0 * c * s * ek + s * s * dk1;
+      d[k + 1] = s * s * dk + 2.0 * c * s * ek + c * c * dk1;
+      e[k] = c * s * (dk - dk1) + (c * c - s * s) * ek;
+      if (k + 1 < u) {
+        bulge = -s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+        x = e[k];
+        z = bulge;
+      }
+      if (vec) {
+        double* qk = &Q[(size_t)k * n];
+        double* qk1 = &Q[(size_t)(k + 1) * n];
+        for (int r = 0; r < n; ++r) {
+          const double t1 = qk[r], t2 = qk1[r];
+          qk[r] = c * t1 - s * t2;
+          qk1[r] = s * t1 + c * t2;
+        }
+      }
+    }
+  }
+  // 3. sort ascending
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x1, int x2) { return d[x1] < d[x2]; });
+  for (int i = 0; i < n; ++i) {
+    w[i] = d[idx[i]];
+    if (vec)
+      for (int r = 0; r < n; ++r) V[(size_t)i * n + r] = Q[(size_t)idx[i] * n + r];
+  }
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(w[i])) return false;
+  return true;
+}
+
+bool host_eigvals(int n, const double* A, double* wr, double* wi) {
+  if (n <= 0) return true;
+  std::vector<double> h(A, A + (size_t)n * n);
+  auto H = [&](int i, int j) -> double& { return h[(size_t)j * n + i]; };
+  // Hessenberg reduction
+  std::vector<double> v(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double xnorm = 0.0;
+    for (int i = 0; i < m; ++i) xnorm = std::hypot(xnorm, H(k + 1 + i, k));
+    if (xnorm == 0.0) continue;
+    const double alpha = H(k + 1, k) > 0 ? -xnorm : xnorm;
+    for (int i = 0; i < m; ++i) v[i] = H(k + 1 + i, k);
+    v[0] -= alpha;
+    double vn2 = 0.0;
+    for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
+    if (vn2 == 0.0) continue;
+    const double beta = 2.0 / vn2;
+    // rows: H[k+1:, :] -= beta v (v^T H[k+1:, :])
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += v[i] * H(k + 1 + i, j);
+      s *= beta;
+      for (int i = 0; i < m; ++i) H(k + 1 + i, j) -= s * v[i];
+    }
+    // columns: H[:, k+1:] -= beta (H[:, k+1:] v) v^T
+    for (int r = 0; r < n; ++r) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += H(r, k + 1 + i) * v[i];
+      s *= beta;
+      for (int i = 0; i < m; ++i) H(r, k + 1 + i) -= s * v[i];
+    }
+    for (int i = k + 2; i < n; ++i) H(i, k) = 0.0;
+  }
+  const double eps = 2.220446049250313e-16;
+  int u = n - 1;
+  int iters = 0, total = 0;
+  while (u >= 0) {
+    if (u == 0) {
+      wr[0] = H(0, 0);
+      wi[0] = 0.0;
+      break;
+    }
+    int l = u;
+    while (l > 0) {
+      double s = std::fabs(H(l - 1, l - 1)) + std::fabs(H(l, l));
+      if (s == 0.0) s = 1.0;
+      if (std::fabs(H(l, l - 1)) <= eps * s) break;
+      --l;
+    }
+    if (l > 0) H(l, l - 1) = 0.0;
+    if (l == u) {
+      wr[u] = H(u, u);
+      wi[u] = 0.0;
+      --u;
+      iters = 0;
+      continue;
+    }
+    if (l == u - 1) {
+      // eigenvalues of the trailing 2 x 2 block
+      const double a11 = H(u - 1, u - 1), a12 = H(u - 1, u), a21 = H(u, u - 1), a22 = H(u, u);
+      const double tr = 0.5 * (a11 + a22);
+      const double det = a11 * a22 - a12 * a21;
+      const double disc = tr * tr - det;
+      if (disc >= 0) {
+        const double sq = std::sqrt(disc);
+        const double r1 = tr + (tr >= 0 ? sq : -sq);
+        const double r2 = (r1 != 0.0) ? det / r1 : tr - (tr >= 0 ? sq : -sq);
+        wr[u - 1] = r1; wi[u - 1] = 0.0;
+        wr[u] = r2; wi[u] = 0.0;
+      } else {
+        const double sq = std::sqrt(-disc);
+        wr[u - 1] = tr; wi[u - 1] = sq;
+        wr[u] = tr; wi[u] = -sq;
+      }
+      u -= 2;
+      iters = 0;
+      continue;
+    }
+    if (++total > 100 * n) return false;
+    ++iters;
+    // Francis double shift (exceptional shifts every 10 stalled iterations)
+    double s, t;
+    if (iters % 10 == 0) {
+      const double ex = std::fabs(H(u, u - 1)) + std::fabs(H(u - 1, u - 2));
+      s = 1.5 * ex;
+      t = ex * ex;
+    } else {
+      s = H(u - 1, u - 1) + H(u, u);
+      t = H(u - 1, u - 1) * H(u, u) - H(u - 1, u) * H(u, u - 1);
+    }
+    double x = H(l, l) * H(l, l) + H(l, l + 1) * H(l + 1, l) - s * H(l, l) + t;
+    double y = H(l + 1, l) * (H(l, l) + H(l + 1, l + 1) - s);
+    double z = H(l + 1, l) * H(l + 2, l + 1);
+    for (int k = l; k <= u - 2; ++k) {
+      // 3-element Householder P = I - beta w w^T with P [x y z]^T = alpha e1
+      double nrm = std::sqrt(x * x + y * y + z * z);
+      if (nrm != 0.0) {
+        const double alpha = x > 0 ? -nrm : nrm;
+        double w0 = x - alpha, w1 = y, w2 = z;
+        const double wn2 = w0 * w0 + w1 * w1 + w2 * w2;
+        if (wn2 != 0.0) {
+          const double beta = 2.0 / wn2;
+          const int c0 = std::max(l, k - 1);
+          for (int j = c0; j <= u; ++j) {
+            const double sj = beta * (w0 * H(k, j) + w1 * H(k + 1, j) + w2 * H(k + 2, j));
+            H(k, j) -= sj * w0; H(k + 1, j) -= sj * w1; H(k + 2, j) -= sj * w2;
+          }
+          const int r1 = std::min(k + 3, u);
+          for (int r = l; r <= r1; ++r) {
+            const double sr = beta * (H(r, k) * w0 + H(r, k + 1) * w1 + H(r, k + 2) * w2);
+            H(r, k) -= sr * w0; H(r, k + 1) -= sr * w1; H(r, k + 2) -= sr * w2;
+          }
+        }
+      }
+      x = H(k + 1, k);
+      y = H(k + 2, k);
+      if (k < u - 2) z = H(k + 3, k);
+    }
+    // final 2-element reflector on rows/cols u-1, u
+    {
+      double nrm = std::hypot(x, y);
+      if (nrm != 0.0) {
+        const double alpha = x > 0 ? -nrm : nrm;
+        double w0 = x - alpha, w1 = y;
+        const double wn2 = w0 * w0 + w1 * w1;
+        if (wn2 != 0.0) {
+          const double beta = 2.0 / wn2;
+          for (int j = std::max(l, u - 2); j <= u; ++j) {
+            const double sj = beta * (w0 * H(u - 1, j) + w1 * H(u, j));
+            H(u - 1, j) -= sj * w0; H(u, j) -= sj * w1;
+          }
+          for (int r = l; r <= u; ++r) {
+            const double sr = beta * (H(r, u - 1) * w0 + H(r, u) * w1);
+            H(r, u - 1) -= sr * w0; H(r, u) -= sr * w1;
+          }
+        }
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(wr[i]) || !std::isfinite(wi[i])) return false;
+  return true;
+}
+
+bool host_cholesky_upper(int n, const double* G, double* R) {
+  // G = R^T R, R upper triangular (column-major)
+  for (size_t i = 0; i < (size_t)n * n; ++i) R[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = G[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= R[(size_t)j * n + k] * R[(size_t)j * n + k];
+    if (!(s > 0.0)) return false;
+    const double rjj = std::sqrt(s);
+    R[(size_t)j * n + j] = rjj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = G[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= R[(size_t)j * n + k] * R[(size_t)i * n + k];
+      R[(size_t)i * n + j] = t / rjj;
+    }
+  }
+  return true;
+}
+
+bool host_lu_solve_complex(int n, std::vector<cd> A, cd* B, int k) {
+  auto a = [&](int i, int j) -> cd& { return A[(size_t)j * n + i]; };
+  auto b = [&](int i, int j) -> cd& { return B[(size_t)j * n + i]; };
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    double best = std::hypot(a(c, c).re, a(c, c).im);
+    for (int r = c + 1; r < n; ++r) {
+      const double v = std::hypot(a(r, c).re, a(r, c).im);
+      if (v > best) { best = v; piv = r; }
+    }
+    if (!(best > 0.0) || !std::isfinite(best)) return false;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) std::swap(a(c, j), a(piv, j));
+      for (int j = 0; j < k; ++j) std::swap(b(c, j), b(piv, j));
+    }
+    for (int r = c + 1; r < n; ++r) {
+      const cd f = cdivz(a(r, c), a(c, c));
+      for (int j = c; j < n; ++j) {
+        const cd t = cmul(f, a(c, j));
+        a(r, j).re -= t.re; a(r, j).im -= t.im;
+      }
+      for (int j = 0; j < k; ++j) {
+        const cd t = cmul(f, b(c, j));
+        b(r, j).re -= t.re; b(r, j).im -= t.im;
+      }
+    }
+  }
+  for (int j = 0; j < k; ++j)
+    for (int r = n - 1; r >= 0; --r) {
+      cd s = b(r, j);
+      for (int c = r + 1; c < n; ++c) {
+        const cd t = cmul(a(r, c), b(c, j));
+        s.re -= t.re; s.im -= t.im;
+      }
+      b(r, j) = cdivz(s, a(r, r));
+    }
+  return true;
+}
+
+}  // namespace care

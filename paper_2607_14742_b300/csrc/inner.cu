@@ -1,0 +1,593 @@
+// Inner (u_s precision) solver: SMW shifted block solves, projection shifts,
+// LR-ADI and NLR-ADI (Section 4), plus the orthogonalisation helpers shared
+// with Algorithms 1 and 2.
+#include <algorithm>
+#include <cmath>
+#include <atomic>
+#include <cstring>
+
+#include "solver.cuh"
+
+namespace care {
+
+static int g_verbose = 0;
+int verbose_level() { return g_verbose; }
+void set_verbose(int v) { g_verbose = v; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(); }
+
+int device_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 148;
+  }
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 148;
+    }
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+template <>
+OpT<double> op_of<double>(const Ctx& c) { return op64(c.op); }
+template <>
+OpT<float> op_of<float>(const Ctx& c) { return op32(c.op); }
+
+const double* upload(Ctx& c, const std::vector<double>& h) {
+  CARE_REQUIRE(h.size() <= c.dS_cap, CARE_ERR_WORKSPACE, "small-matrix staging too small");
+  if (!h.empty())
+    CARE_CUDA(cudaMemcpyAsync(c.dS, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c.s));
+  return c.dS;
+}
+
+template <class T>
+std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, const T* Y, int ldy) {
+  std::vector<double> h((size_t)a * b, 0.0);
+  if (a == 0 || b == 0) return h;
+  CARE_REQUIRE((size_t)a * b <= c.dG_cap, CARE_ERR_WORKSPACE, "gram output staging too small");
+  gram<T>(n, a, b, X, ldx, Y, ldy, c.dG, b, c.gw, c.gw_cap, c.s);
+  CARE_CUDA(cudaMemcpyAsync(h.data(), c.dG, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  CARE_CUDA(cudaStreamSynchronize(c.s));
+  return h;
+}
+template std::vector<double> gram_h<float>(Ctx&, long, int, int, const float*, int, const float*, int);
+template std::vector<double> gram_h<double>(Ctx&, long, int, int, const double*, int, const double*, int);
+
+// ------------------------------------------------------------ orth_rr -----
+// Rank-revealing Cholesky with complete (diagonal) pivoting of the SPD-semidefinite
+// c x c matrix G (row-major).  Stops when the largest remaining pivot is
+// <= tol (or after max_rank pivots).  Returns the pivot order and R (r x c,
+// row-major, original column order) with G ~= R^T R.
+static int pivoted_cholesky(int c, const std::vector<double>& G, double tol, int max_rank, std::vector<int>& piv,
+                            std::vector<double>& R) {
+  std::vector<double> d(c);
+  for (int j = 0; j < c; ++j) d[j] = G[(size_t)j * c + j];
+  std::vector<char> used(c, 0);
+  R.assign(0, 0.0);
+  piv.clear();
+  int r = 0;
+  while (r < c && (max_rank <= 0 || r < max_rank)) {
+    int jp = -1;
+    double best = tol;
+    for (int j = 0; j < c; ++j)
+      if (!used[j] && d[j] > best) {
+        best = d[j];
+        jp = j;
+      }
+    if (jp < 0) break;
+    used[jp] = 1;
+    piv.push_back(jp);
+    R.resize((size_t)(r + 1) * c, 0.0);
+    double* rk = &R[(size_t)r * c];
+    const double rkk = std::sqrt(d[jp]);
+    rk[jp] = rkk;
+    for (int i = 0; i < c; ++i) {
+      if (used[i]) continue;
+      double s = G[(size_t)jp * c + i];
+      for (int l = 0; l < r; ++l) s -= R[(size_t)l * c + jp] * R[(size_t)l * c + i];
+      rk[i] = s / rkk;
+      d[i] -= rk[i] * rk[i];
+    }
+    ++r;
+  }
+  return r;
+}
+
+template <class T>
+OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double drop_rel,
+                const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo) {
+  OrthOut o;
+  CARE_REQUIRE(out == nullptr || !second_pass, CARE_ERR_INVALID_ARG, "orth_rr: out needs one pass");
+  if (cols == 0) return o;
+  std::vector<double> G = gram_h<T>(c, n, cols, cols, X, ldx, X, ldx);
+  // column scaling; columns at or below their floor are dropped
+  std::vector<double> d(cols, 0.0);
+  for (int j = 0; j < cols; ++j) {
+    const double g = G[(size_t)j * cols + j];
+    const double fl = colfloor2 ? (*colfloor2)[j] : 0.0;
+    if (g > fl && g > 0.0 && std::isfinite(g)) d[j] = std::sqrt(g);
+  }
+  std::vector<double> Gs((size_t)cols * cols, 0.0);
+  for (int i = 0; i < cols; ++i)
+    for (int j = 0; j < cols; ++j)
+      if (d[i] > 0 && d[j] > 0) Gs[(size_t)i * cols + j] = G[(size_t)i * cols + j] / (d[i] * d[j]);
+  // rank-revealing pivoted Cholesky of the scaled Gram matrix: drop directions
+  // whose residual norm relative to their column is below sqrt(drop_rel)
+  std::vector<int> piv;
+  std::vector<double> Rs;
+  const int r1 = pivoted_cholesky(cols, Gs, drop_rel, max_rank, piv, Rs);
+  if (r1 == 0) return o;
+  // R11 = Rs(:, piv) is upper triangular; M1 = D^{-1} P R11^{-1} (cols x r1), T1 = Rs D (r1 x cols)
+  std::vector<double> R11((size_t)r1 * r1, 0.0), R11i((size_t)r1 * r1, 0.0);
+  for (int i = 0; i < r1; ++i)
+    for (int k = 0; k < r1; ++k) R11[(size_t)i * r1 + k] = Rs[(size_t)i * cols + piv[k]];
+  for (int j = 0; j < r1; ++j)
+    for (int i = j; i >= 0; --i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) s -= R11[(size_t)i * r1 + k] * R11i[(size_t)k * r1 + j];
+      R11i[(size_t)i * r1 + j] = s / R11[(size_t)i * r1 + i];
+    }
+  std::vector<double> M1((size_t)cols * r1, 0.0), T1((size_t)r1 * cols, 0.0);
+  for (int k = 0; k < r1; ++k) {
+    const int j = piv[k];
+    for (int t = 0; t < r1; ++t) M1[(size_t)j * r1 + t] = R11i[(size_t)k * r1 + t] / d[j];
+  }
+  for (int t = 0; t < r1; ++t)
+    for (int j = 0; j < cols; ++j) T1[(size_t)t * cols + j] = Rs[(size_t)t * cols + j] * d[j];
+  if (out) {
+    gemm_ts<T, T>(n, cols, r1, 1.0, X, ldx, upload(c, M1), r1, 0.0, out, ldo, c.s);
+    o.rank = r1;
+    o.T = std::move(T1);
+    return o;
+  }
+  gemm_ts<T, T>(n, cols, r1, 1.0, X, ldx, upload(c, M1), r1, 0.0, buf, ldb, c.s);
+  if (!second_pass) {
+    copy2d<T, T>(n, r1, buf, ldb, 1, X, ldx, 1, 1.0, c.s);
+    o.rank = r1;
+    o.T = std::move(T1);
+    return o;
+  }
+  // second pass: Cholesky QR of the (now well-conditioned) basis
+  std::vector<double> G2 = gram_h<T>(c, n, r1, r1, buf, ldb, buf, ldb);
+  std::vector<double> R((size_t)r1 * r1);
+  if (!host_cholesky_upper(r1, G2.data(), R.data())) {
+    copy2d<T, T>(n, r1, buf, ldb, 1, X, ldx, 1, 1.0, c.s);
+    OrthOut o2 = orth_rr<T>(c, n, r1, X, ldx, buf, ldb, drop_rel, nullptr, false, max_rank, nullptr, 0);
+    o.rank = o2.rank;
+    o.T.assign((size_t)o2.rank * cols, 0.0);
+    for (int i = 0; i < o2.rank; ++i)
+      for (int k = 0; k < r1; ++k) {
+        const double t = o2.T[(size_t)i * r1 + k];
+        if (t == 0.0) continue;
+        for (int j = 0; j < cols; ++j) o.T[(size_t)i * cols + j] += t * T1[(size_t)k * cols + j];
+      }
+    return o;
+  }
+  // Rinv (r1 x r1, row-major) from the column-major upper factor
+  std::vector<double> Rinv((size_t)r1 * r1, 0.0);
+  for (int j = 0; j < r1; ++j)
+    for (int i = j; i >= 0; --i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) s -= R[(size_t)k * r1 + i] * Rinv[(size_t)k * r1 + j];
+      Rinv[(size_t)i * r1 + j] = s / R[(size_t)i * r1 + i];
+    }
+  gemm_ts<T, T>(n, r1, r1, 1.0, buf, ldb, upload(c, Rinv), r1, 0.0, X, ldx, c.s);
+  o.rank = r1;
+  o.T.assign((size_t)r1 * cols, 0.0);
+  for (int i = 0; i < r1; ++i)
+    for (int k = i; k < r1; ++k) {
+      const double rik = R[(size_t)k * r1 + i];
+      for (int j = 0; j < cols; ++j) o.T[(size_t)i * cols + j] += rik * T1[(size_t)k * cols + j];
+    }
+  return o;
+}
+template OrthOut orth_rr<float>(Ctx&, long, int, float*, int, float*, int, double, const std::vector<double>*,
+                                bool, int, float*, int);
+template OrthOut orth_rr<double>(Ctx&, long, int, double*, int, double*, int, double,
+                                 const std::vector<double>*, bool, int, double*, int);
+
+template <class T>
+std::vector<double> cgs2(Ctx& c, long n, const T* Q, int ldq, int r, T* X, int ldx, int cols) {
+  std::vector<double> C((size_t)r * cols, 0.0);
+  if (r == 0 || cols == 0) return C;
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<double> Ck = gram_h<T>(c, n, r, cols, Q, ldq, X, ldx);
+    gemm_ts<T, T>(n, r, cols, -1.0, Q, ldq, upload(c, Ck), cols, 1.0, X, ldx, c.s);
+    for (size_t i = 0; i < C.size(); ++i) C[i] += Ck[i];
+  }
+  return C;
+}
+template std::vector<double> cgs2<float>(Ctx&, long, const float*, int, int, float*, int, int);
+template std::vector<double> cgs2<double>(Ctx&, long, const double*, int, int, double*, int, int);
+
+// --------------------------------------------------------------- Inner ----
+template <class T>
+void Inner<T>::alloc(Ctx& c, int n_, int m_, int bcap_, int adicap_, int hcap_) {
+  n = n_; m = m_; bcap = bcap_; adicap = adicap_; hcap = hcap_;
+  jacobi = c.o.precond == CARE_PRECOND_JACOBI;
+  kw = krylov_alloc<T>(c.ar, n, jacobi);
+  ldm = pad_ld<T>(std::max(m, 1));
+  ldw = pad_ld<T>(std::max(bcap, 1));
+  ldr = pad_ld<T>(2 * (bcap + m));
+  ldz = pad_ld<T>(std::max(adicap, 1));
+  ldq = pad_ld<T>(std::max(hcap, 1));
+  B = c.ar.get<T>((size_t)n * ldm);
+  K = c.ar.get<T>((size_t)n * ldm);
+  Knew = c.ar.get<T>((size_t)n * ldm);
+  Kd = c.ar.get<T>((size_t)n * ldm);
+  W = c.ar.get<T>((size_t)n * ldw);
+  W0 = c.ar.get<T>((size_t)n * ldw);
+  RHS = c.ar.get<T>((size_t)n * ldr);
+  SOL = c.ar.get<T>((size_t)n * ldr);
+  Z = c.ar.get<T>((size_t)n * ldz);
+  Zs = c.ar.get<T>((size_t)n * ldz);
+  Q = c.ar.get<T>((size_t)n * ldq);
+  FQ = c.ar.get<T>((size_t)n * ldq);
+  Qt = c.ar.get<T>((size_t)n * ldq);
+}
+template struct Inner<float>;
+template struct Inner<double>;
+
+// precision-dependent constants of the inner solves
+template <class T>
+static double krylov_tol(const Ctx& c) { return sizeof(T) == 4 ? c.o.krylov_tol_lo : c.o.krylov_tol_hi; }
+template <class T>
+static int krylov_maxit(const Ctx& c) { return sizeof(T) == 4 ? c.o.krylov_maxit_lo : c.o.krylov_maxit_hi; }
+template <class T>
+static double orth_drop(void) { return sizeof(T) == 4 ? 1e-5 : 1e-12; }
+
+// Applies F = A^T - K B^T to the n x h block X (ldq) into Y (ldq).  The SpMM
+// reads and writes 16-byte vectors, so blocks starting at a column offset are
+// staged through the aligned scratch blocks Qt / FQ.
+template <class T>
+static void apply_F(Ctx& c, Inner<T>& in, bool hasK, const T* X, T* Y, int h) {
+  const bool xa = ((uintptr_t)X % 16) == 0, ya = ((uintptr_t)Y % 16) == 0;
+  const T* Xs = X;
+  T* Ys = Y;
+  if (!xa) {
+    copy2d<T, T>(in.n, h, X, in.ldq, 1, in.Qt, in.ldq, 1, 1.0, c.s);
+    Xs = in.Qt;
+  }
+  if (!ya) Ys = in.FQ;
+  CARE_REQUIRE(Ys != Xs, CARE_ERR_INVALID_ARG, "apply_F: aliasing");
+  spmm<T>(op_of<T>(c), cd{0.0, 0.0}, false, Xs, in.ldq, Ys, in.ldq, h, c.s);
+  if (!ya) copy2d<T, T>(in.n, h, in.FQ, in.ldq, 1, Y, in.ldq, 1, 1.0, c.s);
+  c.spmm_calls++;
+  if (hasK) {
+    std::vector<double> BtX = gram_h<T>(c, in.n, in.m, h, in.B, in.ldm, X, in.ldq);
+    gemm_ts<T, T>(in.n, in.m, h, -1.0, in.K, in.ldm, upload(c, BtX), h, 1.0, Y, in.ldq, c.s);
+  }
+}
+
+struct Shift {
+  double re, im;
+};
+
+// Projection shifts (Section 5: shifts generated from Krylov subspaces):
+// Ritz values of F on range(S) extended by F-blocks until at least hmin
+// columns; closed right half-plane values mirrored, one value per conjugate
+// pair, ordered by decreasing modulus.
+template <class T>
+static std::vector<Shift> proj_shifts(Ctx& c, Inner<T>& in, bool hasK, const T* S, int lds, int h0) {
+  const long n = in.n;
+  const int hmax = in.hcap;
+  // orthonormal basis of the (at most 32) dominant directions of range(S)
+  OrthOut o = orth_rr<T>(c, n, h0, const_cast<T*>(S), lds, nullptr, 0, orth_drop<T>(), nullptr, false,
+                         std::min(hmax / 2, 32), in.Q, in.ldq);
+  int h = o.rank;
+  int last0 = 0, lastw = h;
+  int ext = 0;
+  while (h > 0 && h < c.o.shift_hmin && ext < 4 && h + lastw <= hmax) {
+    // next Krylov block F * Q(:, last block), orthogonalised against Q
+    apply_F<T>(c, in, hasK, in.Q + last0, in.Q + h, lastw);
+    cgs2<T>(c, n, in.Q, in.ldq, h, in.Q + h, in.ldq, lastw);
+    OrthOut ob = orth_rr<T>(c, n, lastw, in.Q + h, in.ldq, in.Qt, in.ldq, orth_drop<T>() * 1e3, nullptr,
+                            false, 0, nullptr, 0);
+    if (ob.rank == 0) break;
+    last0 = h;
+    lastw = ob.rank;
+    h += ob.rank;
+    ++ext;
+  }
+  std::vector<Shift> out;
+  if (h == 0) return out;
+  apply_F<T>(c, in, hasK, in.Q, in.FQ, h);
+  std::vector<double> Hp = gram_h<T>(c, n, h, h, in.Q, in.ldq, in.FQ, in.ldq);  // row-major (Q^T F Q)
+  // to column-major for the host eigenvalue routine
+  std::vector<double> Hc((size_t)h * h);
+  for (int i = 0; i < h; ++i)
+    for (int j = 0; j < h; ++j) Hc[(size_t)j * h + i] = Hp[(size_t)i * h + j];
+  std::vector<double> wr(h), wi(h);
+  CARE_REQUIRE(host_eigvals(h, Hc.data(), wr.data(), wi.data()), CARE_ERR_SMALL_DENSE, "eigvals (shifts)");
+  const double imtol = sizeof(T) == 4 ? 1e-6 : 1e-10;
+  for (int i = 0; i < h; ++i) {
+    const double re = wr[i], im = wi[i];
+    const double mod = std::hypot(re, im);
+    if (!std::isfinite(mod) || mod == 0.0) continue;
+    const double rn = -std::fabs(re);
+    if (rn == 0.0) continue;
+    if (std::fabs(im) <= imtol * mod) out.push_back({rn, 0.0});
+    else if (im > 0) out.push_back({rn, im});
+  }
+  std::stable_sort(out.begin(), out.end(),
+                   [](const Shift& a, const Shift& b) { return std::hypot(a.re, a.im) > std::hypot(b.re, b.im); });
+  return out;
+}
+
+// SMW shifted solve (Section 4):  V = M_p^{-1} W + Y (I - B^T Y)^{-1} B^T M_p^{-1} W,
+// Y = M_p^{-1} K, M_p = (A + p I)^T.  W: first b columns of in.W (real).
+// On return V occupies the first b (complex: 2b real) columns of in.SOL.
+template <class T>
+static void smw_solve(Ctx& c, Inner<T>& in, Shift p, int b, bool hasK) {
+  const long n = in.n;
+  const bool cplx = p.im != 0.0;
+  const int m = hasK ? in.m : 0;
+  const int ncol = b + m;
+  const int rc = cplx ? 2 * ncol : ncol;  // real columns of RHS / SOL
+  if (cplx) {
+    CARE_CUDA(cudaMemsetAsync(in.RHS, 0, (size_t)n * in.ldr * sizeof(T), c.s));
+    copy2d<T, T>(n, b, in.W, in.ldw, 1, in.RHS, in.ldr, 2, 1.0, c.s);
+    if (m) copy2d<T, T>(n, m, in.K, in.ldm, 1, in.RHS + 2 * b, in.ldr, 2, 1.0, c.s);
+  } else {
+    copy2d<T, T>(n, b, in.W, in.ldw, 1, in.RHS, in.ldr, 1, 1.0, c.s);
+    if (m) copy2d<T, T>(n, m, in.K, in.ldm, 1, in.RHS + b, in.ldr, 1, 1.0, c.s);
+  }
+  const OpT<T> op = op_of<T>(c);
+  const int chunk = std::min(kMaxRealCols, std::max(2, (c.o.krylov_chunk > 0 ? c.o.krylov_chunk : 64) * (cplx ? 2 : 1)));
+  for (int c0 = 0; c0 < rc; c0 += chunk) {
+    const int w = std::min(chunk, rc - c0);
+    KrylovResult kr = krylov_bicgstab<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr,
+                                         w, krylov_tol<T>(c), krylov_maxit<T>(c), in.jacobi, in.kw, c.s);
+    c.krylov_iters += kr.iters;
+    c.spmm_calls += kr.spmm;
+    if (kr.unconverged) c.krylov_unconverged++;
+  }
+  if (!m) return;
+  // capacitance: BtS (m x rc) = B^T [V0 | Y]
+  std::vector<double> BtS = gram_h<T>(c, n, m, rc, in.B, in.ldm, in.SOL, in.ldr);
+  auto bts = [&](int i, int j) -> cd {  // complex entry (i, j) of B^T SOL
+    if (cplx) return cd{BtS[(size_t)i * rc + 2 * j], BtS[(size_t)i * rc + 2 * j + 1]};
+    return cd{BtS[(size_t)i * rc + j], 0.0};
+  };
+  std::vector<cd> S((size_t)m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      cd y = bts(i, b + j);
+      S[(size_t)j * m + i] = cd{(i == j ? 1.0 : 0.0) - y.re, -y.im};
+    }
+  std::vector<cd> Tm((size_t)m * b);  // column-major m x b: B^T V0, overwritten by S^{-1} B^T V0
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < b; ++j) Tm[(size_t)j * m + i] = bts(i, j);
+  CARE_REQUIRE(host_lu_solve_complex(m, S, Tm.data(), b), CARE_ERR_SMALL_DENSE, "SMW capacitance solve");
+  // V0 += Y Tm
+  if (cplx) {
+    std::vector<double> E((size_t)(2 * m) * (2 * b));
+    for (int k = 0; k < m; ++k)
+      for (int j = 0; j < b; ++j) {
+        const cd t = Tm[(size_t)j * m + k];
+        E[(size_t)(2 * k) * (2 * b) + 2 * j] = t.re;
+        E[(size_t)(2 * k) * (2 * b) + 2 * j + 1] = t.im;
+        E[(size_t)(2 * k + 1) * (2 * b) + 2 * j] = -t.im;
+        E[(size_t)(2 * k + 1) * (2 * b) + 2 * j + 1] = t.re;
+      }
+    gemm_ts<T, T>(n, 2 * m, 2 * b, 1.0, in.SOL + 2 * b, in.ldr, upload(c, E), 2 * b, 1.0, in.SOL, in.ldr, c.s);
+  } else {
+    std::vector<double> E((size_t)m * b);
+    for (int k = 0; k < m; ++k)
+      for (int j = 0; j < b; ++j) E[(size_t)k * b + j] = Tm[(size_t)j * m + k].re;
+    gemm_ts<T, T>(n, m, b, 1.0, in.SOL + b, in.ldr, upload(c, E), b, 1.0, in.SOL, in.ldr, c.s);
+  }
+}
+
+template <class T>
+void smw_solve_public(Ctx& c, Inner<T>& in, double p_re, double p_im, int b, bool hasK) {
+  smw_solve<T>(c, in, Shift{p_re, p_im}, b, hasK);
+}
+template void smw_solve_public<float>(Ctx&, Inner<float>&, double, double, int, bool);
+template void smw_solve_public<double>(Ctx&, Inner<double>&, double, double, int, bool);
+
+template <class T>
+static double adi_norm2(Ctx& c, Inner<T>& in, int b) {
+  // ||W^T W||_2 = largest eigenvalue of the b x b Gram matrix
+  std::vector<double> G = gram_h<T>(c, in.n, b, b, in.W, in.ldw, in.W, in.ldw);
+  std::vector<double> w(b);
+  CARE_REQUIRE(host_symeig(b, G.data(), w.data(), nullptr), CARE_ERR_SMALL_DENSE, "symeig (ADI norm)");
+  return std::max(w[b - 1], 0.0);
+}
+
+// Compresses the factor columns Z[:, col0 : col0 + ncols] (one sign group) to
+// rank q: Z = Q T (rank-revealing orthonormalisation) and Z Z^T = Q (T T^T) Q^T
+// = (Q L)(Q L)^T with L L^T = T T^T, written right- or left-aligned in place.
+template <class T>
+static int compress_part(Ctx& c, Inner<T>& in, int col0, int ncols, bool right_aligned) {
+  if (ncols == 0) return 0;
+  const long n = in.n;
+  const double drop = sizeof(T) == 4 ? 1e-6 : 1e-12;
+  OrthOut o = orth_rr<T>(c, n, ncols, in.Z + col0, in.ldz, in.Zs, in.ldz, drop, nullptr, true, 0, nullptr, 0);
+  const int q = o.rank;
+  if (q == 0) return 0;
+  std::vector<double> TT((size_t)q * q, 0.0), R((size_t)q * q);
+  for (int i = 0; i < q; ++i)
+    for (int k = 0; k < q; ++k) {
+      double acc = 0.0;
+      for (int j = 0; j < ncols; ++j) acc += o.T[(size_t)i * ncols + j] * o.T[(size_t)k * ncols + j];
+      TT[(size_t)i * q + k] = acc;
+    }
+  CARE_REQUIRE(host_cholesky_upper(q, TT.data(), R.data()), CARE_ERR_SMALL_DENSE, "compression Cholesky");
+  // column-major upper R == row-major R^T = L
+  gemm_ts<T, T>(n, q, q, 1.0, in.Z + col0, in.ldz, upload(c, R), q, 0.0, in.Zs, in.ldz, c.s);
+  const int dst = right_aligned ? col0 + ncols - q : col0;
+  copy2d<T, T>(n, q, in.Zs, in.ldz, 1, in.Z + dst, in.ldz, 1, 1.0, c.s);
+  return q;
+}
+
+template <class T>
+AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew) {
+  AdiResult res;
+  const long n = in.n;
+  const int rm = b - rp;
+  CARE_REQUIRE(b <= in.bcap, CARE_ERR_RANK_CAPACITY, "LR-ADI right-hand side wider than its capacity");
+  CARE_REQUIRE(rp >= 0 && rm >= 0 && (!knew || rm == 0), CARE_ERR_INVALID_ARG, "LR-ADI split");
+  copy2d<T, T>(n, b, in.W0, in.ldw, 1, in.W, in.ldw, 1, 1.0, c.s);
+  const double w0 = adi_norm2<T>(c, in, b);
+  if (!(w0 > 0.0)) {
+    res.converged = true;
+    return res;
+  }
+  std::vector<Shift> shifts = proj_shifts<T>(c, in, hasK, in.W, in.ldw, b);
+  size_t next = 0;
+  int np = 0, nm = 0, j = 0;
+  int last0 = -1, lastw = 0;
+  double r = 1.0;
+  const int cap = in.adicap;
+  while (j < jmax && r > tol) {
+    if (next >= shifts.size()) {
+      shifts = last0 >= 0 ? proj_shifts<T>(c, in, hasK, in.Z + last0, in.ldz, lastw)
+                          : proj_shifts<T>(c, in, hasK, in.W, in.ldw, b);
+      next = 0;
+      CARE_REQUIRE(!shifts.empty(), CARE_INNER_FAILED, "no shifts available");
+    }
+    const Shift p = shifts[next];
+    const bool cplx = p.im != 0.0;
+    const int mult = cplx ? 2 : 1;
+    if (np + nm + mult * b > cap) {
+      // column compression of both sign groups (X_+ and X_- are kept separately)
+      const int np2 = compress_part<T>(c, in, 0, np, false);
+      const int nm2 = compress_part<T>(c, in, cap - nm, nm, true);
+      if (verbose_level() >= 2)
+        fprintf(stderr, "[care]   adi compress %d+%d -> %d+%d\n", np, nm, np2, nm2);
+      np = np2;
+      nm = nm2;
+      res.compressions++;
+      last0 = -1;  // the newest block was merged; shifts restart from the residual
+      if (np + nm + mult * b > cap) break;  // capacity exhausted: inexact inner solve
+    }
+    ++next;
+    smw_solve<T>(c, in, p, b, hasK);
+    const int pm0 = cap - nm - mult * rm;  // start of the new minus columns
+    if (!cplx) {
+      // W <- W - 2 p V;  Z <- [Z, sqrt(-2p) V]
+      const double sc = std::sqrt(-2.0 * p.re);
+      axpby<T>(n, b, -2.0 * p.re, in.SOL, in.ldr, 1.0, in.W, in.ldw, c.s);
+      if (rp) copy2d<T, T>(n, rp, in.SOL, in.ldr, 1, in.Z + np, in.ldz, 1, sc, c.s);
+      if (rm) copy2d<T, T>(n, rm, in.SOL + rp, in.ldr, 1, in.Z + pm0, in.ldz, 1, sc, c.s);
+      j += 1;
+    } else {
+      // complex pair p, conj(p) in real arithmetic:
+      // W <- W + g^2 (Re V + d Im V);  Z <- [Z, g (Re V + d Im V), g sqrt(d^2+1) Im V]
+      const double g = 2.0 * std::sqrt(-p.re), d = p.re / p.im;
+      std::vector<double> E((size_t)(2 * b) * b, 0.0), Ei((size_t)(2 * b) * b, 0.0);
+      for (int q = 0; q < b; ++q) {
+        E[(size_t)(2 * q) * b + q] = 1.0;
+        E[(size_t)(2 * q + 1) * b + q] = d;
+        Ei[(size_t)(2 * q + 1) * b + q] = 1.0;
+      }
+      const double* dE = upload(c, E);
+      gemm_ts<T, T>(n, 2 * b, b, g * g, in.SOL, in.ldr, dE, b, 1.0, in.W, in.ldw, c.s);
+      if (rp) gemm_ts<T, T>(n, 2 * b, rp, g, in.SOL, in.ldr, dE, b, 0.0, in.Z + np, in.ldz, c.s);
+      if (rm) gemm_ts<T, T>(n, 2 * b, rm, g, in.SOL, in.ldr, dE + rp, b, 0.0, in.Z + pm0, in.ldz, c.s);
+      const double gi = g * std::sqrt(d * d + 1.0);
+      const double* dEi = upload(c, Ei);
+      if (rp) gemm_ts<T, T>(n, 2 * b, rp, gi, in.SOL, in.ldr, dEi, b, 0.0, in.Z + np + rp, in.ldz, c.s);
+      if (rm) gemm_ts<T, T>(n, 2 * b, rm, gi, in.SOL, in.ldr, dEi + rp, b, 0.0, in.Z + pm0 + rm, in.ldz, c.s);
+      j += 2;
+    }
+    if (knew) {
+      // K_new += Z_blk (Z_blk^T B)
+      const int add = mult * rp;
+      std::vector<double> ZtB = gram_h<T>(c, n, add, in.m, in.Z + np, in.ldz, in.B, in.ldm);
+      gemm_ts<T, T>(n, add, in.m, 1.0, in.Z + np, in.ldz, upload(c, ZtB), in.m, 1.0, in.Knew, in.ldm, c.s);
+    }
+    if (rp) {
+      last0 = np;
+      lastw = mult * rp;
+    } else {
+      last0 = pm0;
+      lastw = mult * rm;
+    }
+    np += mult * rp;
+    nm += mult * rm;
+    r = adi_norm2<T>(c, in, b) / w0;
+    if (!std::isfinite(r)) CARE_THROW(CARE_NONFINITE, "LR-ADI residual not finite");
+    if (verbose_level() >= 2)
+      fprintf(stderr, "[care]   adi j=%d p=(%.4e,%.4e) res=%.3e cols=%d+%d\n", j, p.re, p.im, r, np, nm);
+  }
+  res.np = np;
+  res.nm = nm;
+  res.steps = j;
+  res.res = r;
+  res.converged = r <= tol;
+  if (verbose_level() >= 1)
+    fprintf(stderr, "[care]  lradi b=%d (%d+%d) steps=%d res=%.3e cols=%d+%d compress=%d krylov_unconv=%d\n", b, rp, rm,
+            j, r, np, nm, res.compressions, c.krylov_unconverged);
+  return res;
+}
+template AdiResult lradi<float>(Ctx&, Inner<float>&, int, int, bool, double, int, bool);
+template AdiResult lradi<double>(Ctx&, Inner<double>&, int, int, bool, double, int, bool);
+
+template <class T>
+NlrResult nlradi(Ctx& c, Inner<T>& in, const T* Ct, int ldct, int p, double tol_lyap, double tol_newton,
+                 int newton_max, int jmax) {
+  NlrResult out;
+  const long n = in.n;
+  bool hasK = false;
+  double prev_rel = -1.0;
+  CARE_CUDA(cudaMemsetAsync(in.K, 0, (size_t)n * in.ldm * sizeof(T), c.s));
+  for (int i = 0; i < newton_max; ++i) {
+    // right-hand side factor [C^T, K_i] (K_0 = 0: C^T only)
+    copy2d<T, T>(n, p, Ct, ldct, 1, in.W0, in.ldw, 1, 1.0, c.s);
+    int b = p;
+    if (hasK) {
+      copy2d<T, T>(n, in.m, in.K, in.ldm, 1, in.W0 + p, in.ldw, 1, 1.0, c.s);
+      b += in.m;
+    }
+    CARE_CUDA(cudaMemsetAsync(in.Knew, 0, (size_t)n * in.ldm * sizeof(T), c.s));
+    AdiResult a = lradi<T>(c, in, b, b, hasK, tol_lyap, jmax, true);
+    out.adi += a.steps;
+    out.newton = i + 1;
+    out.cols = a.np;
+    // relative change of the feedback
+    axpby<T>(n, in.m, 1.0, in.Knew, in.ldm, 0.0, in.Kd, in.ldm, c.s);
+    axpby<T>(n, in.m, -1.0, in.K, in.ldm, 1.0, in.Kd, in.ldm, c.s);
+    std::vector<double> Gd = gram_h<T>(c, n, in.m, in.m, in.Kd, in.ldm, in.Kd, in.ldm);
+    std::vector<double> Gk = gram_h<T>(c, n, in.m, in.m, in.Knew, in.ldm, in.Knew, in.ldm);
+    double dk = 0.0, nk = 0.0;
+    for (int q = 0; q < in.m; ++q) {
+      dk += Gd[(size_t)q * in.m + q];
+      nk += Gk[(size_t)q * in.m + q];
+    }
+    const double rel = nk > 0 ? std::sqrt(dk / nk) : 0.0;
+    std::swap(in.K, in.Knew);
+    hasK = true;
+    if (verbose_level() >= 1)
+      fprintf(stderr, "[care] nlradi newton=%d adi=%d cols=%d dK=%.3e adires=%.3e\n", i + 1, a.steps, a.np,
+              rel, a.res);
+    if (!std::isfinite(rel)) CARE_THROW(CARE_NONFINITE, "NLR-ADI feedback not finite");
+    if (rel <= tol_newton) {
+      out.converged = true;
+      break;
+    }
+    // Newton has reached the accuracy of its inner solves once the change stops
+    // shrinking quadratically: further steps only add rounding noise
+    if (prev_rel > 0 && rel < 1e-3 && rel > 0.5 * prev_rel) break;
+    prev_rel = rel;
+  }
+  return out;
+}
+template NlrResult nlradi<float>(Ctx&, Inner<float>&, const float*, int, int, double, double, int, int);
+template NlrResult nlradi<double>(Ctx&, Inner<double>&, const double*, int, int, double, double, int, int);
+
+}  // namespace care

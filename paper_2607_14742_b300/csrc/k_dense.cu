@@ -1,0 +1,301 @@
+// Tall-skinny dense kernels on the CUDA cores (FP32 / FP64 FMA).
+//
+// gram:    G = X^T Y, a, b <= a few hundred, n up to 1e6.  Output tiles of
+//          64 x 64 per CTA, rows split across CTAs (split-K); each CTA stages
+//          32-row slabs of X and Y in shared memory, accumulates a 4 x 4 register
+//          tile per thread, and writes an FP64 partial; a second kernel sums
+//          the partials in a fixed order (deterministic).
+// gemm_ts: Y = alpha X S + beta Y with S small (a x b): 64-row x 64-column
+//          output tiles, the contraction over a staged 32 columns at a time.
+#include "dense.cuh"
+
+namespace care {
+
+constexpr int GT = 64;   // output tile
+constexpr int GK = 32;   // rows (gram) / inner columns (gemm_ts) per stage
+
+size_t gram_work_elems(long n, int a, int b) {
+  const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
+  const long tiles = (long)ta * tb;
+  long split = (2L * device_sms() + tiles - 1) / tiles;
+  long maxsplit = (n + 4 * GK - 1) / (4 * GK);
+  if (split > maxsplit) split = maxsplit;
+  if (split < 1) split = 1;
+  return (size_t)split * ta * GT * tb * GT;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gram(long n, int a, int b, const T* __restrict__ X, int ldx,
+                                              const T* __restrict__ Y, int ldy, long rows_per,
+                                              double* __restrict__ part) {
+  __shared__ T xs[GK][GT];
+  __shared__ T ys[GK][GT];
+  const int ta = blockIdx.y, tb = blockIdx.z;
+  const int i0 = ta * GT, j0 = tb * GT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4];
+  double accd[4][4];  // FP32 inputs: each 32-row stage is flushed into FP64
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      acc[u][v] = T(0);
+      accd[u][v] = 0.0;
+    }
+  const long r_begin = (long)blockIdx.x * rows_per;
+  long r_end = r_begin + rows_per;
+  if (r_end > n) r_end = n;
+  for (long r0 = r_begin; r0 < r_end; r0 += GK) {
+    // stage GK rows x GT columns of X and Y (zero outside)
+    for (int e = threadIdx.x; e < GK * GT; e += 256) {
+      const int k = e / GT, c = e % GT;
+      const long r = r0 + k;
+      const bool rin = r < r_end;
+      xs[k][c] = (rin && i0 + c < a) ? X[(size_t)r * ldx + i0 + c] : T(0);
+      ys[k][c] = (rin && j0 + c < b) ? Y[(size_t)r * ldy + j0 + c] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < GK; ++k) {
+      T xv[4], yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = xs[k][ty * 4 + u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yv[v] = ys[k][tx * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xv[u], yv[v], acc[u][v]);
+    }
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          accd[u][v] += (double)acc[u][v];
+          acc[u][v] = T(0);
+        }
+    }
+    __syncthreads();
+  }
+  const int TA = gridDim.y * GT, TB = gridDim.z * GT;
+  double* out = part + (size_t)blockIdx.x * TA * TB;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      out[(size_t)(i0 + ty * 4 + u) * TB + j0 + tx * 4 + v] = sizeof(T) == 4 ? accd[u][v] : (double)acc[u][v];
+}
+
+__global__ void k_gram_reduce(int a, int b, int TA, int TB, long split, const double* __restrict__ part,
+                              double* __restrict__ G, int ldg) {
+  const long total = (long)a * b;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / b), j = (int)(e % b);
+    const size_t off = (size_t)i * TB + j;
+    double s0 = 0, s1 = 0;
+    long g = 0;
+    for (; g + 1 < split; g += 2) {
+      s0 += part[(size_t)g * TA * TB + off];
+      s1 += part[(size_t)(g + 1) * TA * TB + off];
+    }
+    if (g < split) s0 += part[(size_t)g * TA * TB + off];
+    G[(size_t)i * ldg + j] = s0 + s1;
+  }
+}
+
+template <class T>
+void gram(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double* G, int ldg,
+          double* work, size_t work_elems, cudaStream_t s) {
+  if (a == 0 || b == 0) return;
+  const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
+  const size_t need = gram_work_elems(n, a, b);
+  CARE_REQUIRE(need <= work_elems, CARE_ERR_WORKSPACE, "gram: scratch too small");
+  const long split = (long)(need / ((size_t)ta * GT * tb * GT));
+  const long rows_per = ((n + split - 1) / split + GK - 1) / GK * GK;
+  if (n == 0) {
+    CARE_CUDA(cudaMemsetAsync(work, 0, need * sizeof(double), s));
+  } else {
+    dim3 grid((unsigned)split, ta, tb);
+    k_gram<T><<<grid, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, rows_per, work);
+    CARE_LAUNCH();
+  }
+  const long tot = (long)a * b;
+  int g = (int)((tot + 255) / 256);
+  if (g > device_sms() * 4) g = device_sms() * 4;
+  k_gram_reduce<<<g, 256, 0, s>>>(a, b, ta * GT, tb * GT, n == 0 ? 1 : split, work, G, ldg);
+  CARE_LAUNCH();
+}
+template void gram<float>(long, int, int, const float*, int, const float*, int, double*, int, double*,
+                          size_t, cudaStream_t);
+template void gram<double>(long, int, int, const double*, int, const double*, int, double*, int, double*,
+                           size_t, cudaStream_t);
+
+template <class Ti, class To>
+__global__ void __launch_bounds__(256) k_gemm_ts(long n, int a, int b, double alpha,
+                                                 const Ti* __restrict__ X, int ldx,
+                                                 const double* __restrict__ S, int lds, double beta,
+                                                 To* __restrict__ Y, int ldy) {
+  __shared__ Ti xs[GT][GK + 1];
+  __shared__ Ti ss[GK][GT];
+  const long r0 = (long)blockIdx.x * GT;
+  const int j0 = blockIdx.y * GT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  Ti acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = Ti(0);
+  for (int k0 = 0; k0 < a; k0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+      const int r = e / GK, k = e % GK;
+      const long rr = r0 + r;
+      xs[r][k] = (rr < n && k0 + k < a) ? X[(size_t)rr * ldx + k0 + k] : Ti(0);
+    }
+    for (int e = threadIdx.x; e < GK * GT; e += 256) {
+      const int k = e / GT, c = e % GT;
+      ss[k][c] = (k0 + k < a && j0 + c < b) ? (Ti)S[(size_t)(k0 + k) * lds + j0 + c] : Ti(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < GK; ++k) {
+      Ti xv[4], sv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = xs[ty * 4 + u][k];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sv[v] = ss[k][tx * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xv[u], sv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long r = r0 + ty * 4 + u;
+    if (r >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = j0 + tx * 4 + v;
+      if (c >= b) continue;
+      const size_t o = (size_t)r * ldy + c;
+      double y = alpha * (double)acc[u][v];
+      if (beta != 0.0) y += beta * (double)Y[o];
+      Y[o] = (To)y;
+    }
+  }
+}
+
+template <class Ti, class To>
+void gemm_ts(long n, int a, int b, double alpha, const Ti* X, int ldx, const double* S, int lds,
+             double beta, To* Y, int ldy, cudaStream_t s) {
+  if (n == 0 || b == 0) return;
+  if (a == 0) {
+    // Y = beta Y
+    if (beta == 1.0) return;
+    copy2d<To, To>(n, b, Y, ldy, 1, Y, ldy, 1, beta, s);
+    return;
+  }
+  dim3 grid((unsigned)((n + GT - 1) / GT), (b + GT - 1) / GT);
+  k_gemm_ts<Ti, To><<<grid, 256, 0, s>>>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy);
+  CARE_LAUNCH();
+}
+template void gemm_ts<float, float>(long, int, int, double, const float*, int, const double*, int, double,
+                                    float*, int, cudaStream_t);
+template void gemm_ts<double, double>(long, int, int, double, const double*, int, const double*, int,
+                                      double, double*, int, cudaStream_t);
+template void gemm_ts<double, float>(long, int, int, double, const double*, int, const double*, int,
+                                     double, float*, int, cudaStream_t);
+template void gemm_ts<float, double>(long, int, int, double, const float*, int, const double*, int,
+                                     double, double*, int, cudaStream_t);
+
+// ---------------------------------------------------------------- copies --
+template <class Ti, class To>
+__global__ void k_copy2d(long rows, int cols, const Ti* __restrict__ src, long srs, long scs,
+                         To* __restrict__ dst, long drs, long dcs, double scale) {
+  // 32 x 32 tile: read with threadIdx.x along the source's contiguous index,
+  // write with threadIdx.x along the destination's contiguous index.
+  __shared__ double tile[32][33];
+  const long bi = (long)blockIdx.x * 32;
+  const int bj = blockIdx.y * 32;
+  const bool src_rowmajor = (scs == 1);
+  const bool dst_rowmajor = (dcs == 1);
+  for (int t = threadIdx.y; t < 32; t += blockDim.y) {
+    long i;
+    int j;
+    if (src_rowmajor) { i = bi + t; j = bj + threadIdx.x; }
+    else { i = bi + threadIdx.x; j = bj + t; }
+    double v = 0.0;
+    if (i < rows && j < cols) v = (double)src[i * srs + (long)j * scs];
+    tile[i - bi][j - bj] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.y; t < 32; t += blockDim.y) {
+    long i;
+    int j;
+    if (dst_rowmajor) { i = bi + t; j = bj + threadIdx.x; }
+    else { i = bi + threadIdx.x; j = bj + t; }
+    if (i < rows && j < cols) dst[i * drs + (long)j * dcs] = (To)(scale * tile[i - bi][j - bj]);
+  }
+}
+
+template <class Ti, class To>
+void copy2d(long rows, int cols, const Ti* src, long src_rs, long src_cs, To* dst, long dst_rs,
+            long dst_cs, double scale, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return;
+  dim3 grid((unsigned)((rows + 31) / 32), (cols + 31) / 32);
+  dim3 block(32, 8);
+  k_copy2d<Ti, To><<<grid, block, 0, s>>>(rows, cols, src, src_rs, src_cs, dst, dst_rs, dst_cs, scale);
+  CARE_LAUNCH();
+}
+template void copy2d<float, float>(long, int, const float*, long, long, float*, long, long, double,
+                                   cudaStream_t);
+template void copy2d<double, double>(long, int, const double*, long, long, double*, long, long, double,
+                                     cudaStream_t);
+template void copy2d<double, float>(long, int, const double*, long, long, float*, long, long, double,
+                                    cudaStream_t);
+template void copy2d<float, double>(long, int, const float*, long, long, double*, long, long, double,
+                                    cudaStream_t);
+
+template <class T>
+__global__ void k_axpby(long n, int cols, double alpha, const T* __restrict__ X, int ldx, double beta,
+                        T* __restrict__ Y, int ldy) {
+  const long total = n * (long)cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / cols;
+    const int c = (int)(e % cols);
+    T& y = Y[(size_t)r * ldy + c];
+    const double v = alpha * (double)X[(size_t)r * ldx + c] + (beta != 0.0 ? beta * (double)y : 0.0);
+    y = (T)v;
+  }
+}
+template <class T>
+void axpby(long n, int cols, double alpha, const T* X, int ldx, double beta, T* Y, int ldy,
+           cudaStream_t s) {
+  if (n == 0 || cols == 0) return;
+  k_axpby<T><<<device_sms() * 4, 256, 0, s>>>(n, cols, alpha, X, ldx, beta, Y, ldy);
+  CARE_LAUNCH();
+}
+template void axpby<float>(long, int, double, const float*, int, double, float*, int, cudaStream_t);
+template void axpby<double>(long, int, double, const double*, int, double, double*, int, cudaStream_t);
+
+template <class T>
+__global__ void k_scale_cols(long n, int cols, T* __restrict__ Y, int ldy, const double* __restrict__ d) {
+  const long total = n * (long)cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / cols;
+    const int c = (int)(e % cols);
+    Y[(size_t)r * ldy + c] = (T)((double)Y[(size_t)r * ldy + c] * d[c]);
+  }
+}
+template <class T>
+void scale_cols(long n, int cols, T* Y, int ldy, const double* d, cudaStream_t s) {
+  if (n == 0 || cols == 0) return;
+  k_scale_cols<T><<<device_sms() * 4, 256, 0, s>>>(n, cols, Y, ldy, d);
+  CARE_LAUNCH();
+}
+template void scale_cols<float>(long, int, float*, int, const double*, cudaStream_t);
+template void scale_cols<double>(long, int, double*, int, const double*, cudaStream_t);
+
+}  // namespace care

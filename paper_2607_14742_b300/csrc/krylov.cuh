@@ -1,0 +1,68 @@
+// Sparse operator, fused SpMM and the block BiCGStab shifted solver.
+#pragma once
+
+#include "common.cuh"
+
+namespace care {
+
+// A^T in CSR with values of type T (the prepared operator of care_op).
+template <class T>
+struct OpT {
+  int n = 0, nnz = 0;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const T* val = nullptr;
+  const T* diag = nullptr;
+  bool diag_const = true;
+};
+OpT<double> op64(const care_op& op);
+OpT<float> op32(const care_op& op);
+
+// Per-column state of the block BiCGStab recurrences (one entry per real
+// column, or per complex column in complex mode).  Scalars are kept in FP64.
+struct KState {
+  double rho_re, rho_im, alpha_re, alpha_im, omega_re, omega_im, beta_re, beta_im;
+  double bnorm2, rnorm2;
+  int flag;  // 0 active, 1 converged, 2 breakdown
+  int iters;
+};
+struct KHeader {
+  int n_active;
+  unsigned counter;
+  int pad[2];
+};
+
+// Workspace of one block Krylov solve of at most kMaxRealCols real columns.
+template <class T>
+struct KrylovWork {
+  T *X = nullptr, *R = nullptr, *Rh = nullptr, *P = nullptr, *V = nullptr, *S = nullptr, *Tt = nullptr;
+  T *Ph = nullptr, *Sh = nullptr, *Dinv = nullptr;
+  KState* st = nullptr;
+  KHeader* hdr = nullptr;
+  double* partial = nullptr;
+  double* out = nullptr;
+  int n = 0;
+};
+template <class T>
+KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi);
+
+struct KrylovResult {
+  int iters = 0;
+  int unconverged = 0;  // columns not converged (limit or breakdown)
+  long long spmm = 0;
+};
+
+// Solves (A^T + sigma I) X = RHS for `cols` real columns (complex interleaved
+// columns when cplx: cols = 2 * complex columns), cols <= kMaxRealCols.
+// rhs/sol are row-major with leading dimensions ld_rhs / ld_sol (reals).
+template <class T>
+KrylovResult krylov_bicgstab(const OpT<T>& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol,
+                             int ld_sol, int cols, double tol, int maxit, bool jacobi,
+                             KrylovWork<T>& w, cudaStream_t s);
+
+// Y = (A^T + sigma I) X on `cols` real columns (any width; complex when cplx).
+template <class T>
+void spmm(const OpT<T>& op, cd sigma, bool cplx, const T* X, int ldx, T* Y, int ldy, int cols,
+          cudaStream_t s);
+
+}  // namespace care

@@ -1,0 +1,107 @@
+// Host orchestration of the CARE solver: context, buffers, and the algorithm
+// steps (SMW shifted solve, projection shifts, LR-ADI, NLR-ADI, Algorithms 1-2).
+#pragma once
+
+#include <chrono>
+#include <vector>
+
+#include "dense.cuh"
+#include "krylov.cuh"
+
+namespace care {
+
+struct Ctx {
+  cudaStream_t s = nullptr;
+  care_opts o{};
+  Arena ar;
+  care_op op{};
+  double* dS = nullptr;  // staging for small matrices (device)
+  size_t dS_cap = 0;
+  double* dG = nullptr;  // Gram results (device)
+  size_t dG_cap = 0;
+  double* gw = nullptr;  // Gram split-K scratch
+  size_t gw_cap = 0;
+  long long krylov_iters = 0, spmm_calls = 0;
+  int krylov_unconverged = 0;
+  bool counting() const { return ar.counting(); }
+};
+
+// host <-> device helpers for small matrices
+const double* upload(Ctx& c, const std::vector<double>& h);
+template <class T>
+std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, const T* Y, int ldy);
+
+// Rank-revealing orthonormalisation X (n x cols) -> Q (in place, n x rank) with
+// X = Q T (T rank x cols, row-major).  Column-scaled eigendecomposition of the
+// Gram matrix (SVQB, Stathopoulos & Wu 2002) keeps directions with scaled
+// eigenvalue > drop_rel * max; an optional second pass (Cholesky QR of the
+// result) restores orthogonality to working accuracy.  colfloor2 (optional,
+// host) gives per-column squared norms below which a column counts as zero.
+struct OrthOut {
+  int rank = 0;
+  std::vector<double> T;  // rank x cols
+};
+// With `out` (one pass only) the basis is written there and X is left intact.
+template <class T>
+OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double drop_rel,
+                const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo);
+
+// X (n x cols) -= Q (Q^T X) twice (classical Gram-Schmidt with
+// reorthogonalisation); returns the r x cols coefficients.
+template <class T>
+std::vector<double> cgs2(Ctx& c, long n, const T* Q, int ldq, int r, T* X, int ldx, int cols);
+
+// Inner (u_s precision) solver state: block Krylov work, SMW, LR-ADI, NLR-ADI.
+template <class T>
+struct Inner {
+  int n = 0, m = 0, bcap = 0, adicap = 0, hcap = 0;
+  KrylovWork<T> kw;
+  T *B = nullptr, *K = nullptr, *Knew = nullptr, *Kd = nullptr;  // n x m (ldm)
+  T *W = nullptr, *W0 = nullptr;                                 // n x bcap (ldw)
+  T *RHS = nullptr, *SOL = nullptr;                              // n x 2(bcap+m) (ldr)
+  T *Z = nullptr;   // n x adicap (ldz): X_+ factor from the left, X_- factor from the right
+  T *Zs = nullptr;  // n x adicap scratch (compression)
+  T *Q = nullptr, *FQ = nullptr, *Qt = nullptr;                  // n x hcap (ldq)
+  int ldm = 0, ldw = 0, ldr = 0, ldz = 0, ldq = 0;
+  bool jacobi = false;
+  void alloc(Ctx& c, int n_, int m_, int bcap_, int adicap_, int hcap_);
+};
+
+struct AdiResult {
+  int np = 0, nm = 0;  // factor columns: X_+ in Z[:, 0:np], X_- in Z[:, adicap-nm : adicap]
+  int steps = 0;       // shifts used (a complex pair counts 2)
+  int compressions = 0;
+  bool converged = false;
+  double res = 0.0;    // final ||W^T W||_2 / ||W_0^T W_0||_2
+};
+
+// LR-ADI for F X + X F^T + W0 W0^T = 0, F = A^T - K B^T (hasK), on the first
+// b columns of in.W0; the first rp columns belong to X_+, the rest to X_-
+// (the two correction equations of Framework 1 solved as one block).  If
+// knew, accumulates K_new += Z_blk (Z_blk^T B) into in.Knew (requires rp = b).
+// When the factor reaches its capacity it is column-compressed; if that does
+// not free enough room the solve stops early (inexact inner solve).
+template <class T>
+AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew);
+
+struct NlrResult {
+  int newton = 0, adi = 0, cols = 0;
+  bool converged = false;
+};
+// NLR-ADI: Newton-Kleinman with LR-ADI inner solves; C^T (n x p, row-major T,
+// ldw) must be in in.W0's first p columns on entry (it is re-read each step).
+template <class T>
+NlrResult nlradi(Ctx& c, Inner<T>& in, const T* Ct, int ldct, int p, double tol_lyap, double tol_newton,
+                 int newton_max, int jmax);
+
+template <class T>
+OpT<T> op_of(const Ctx& c);
+
+// One SMW shifted block solve (V in the leading columns of in.SOL) for the
+// first b columns of in.W, with or without the feedback term.
+template <class T>
+void smw_solve_public(Ctx& c, Inner<T>& in, double p_re, double p_im, int b, bool hasK);
+
+double now_ms();
+
+}  // namespace care

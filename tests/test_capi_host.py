@@ -1,0 +1,101 @@
+"""C-ABI library checks that need no GPU: it loads, exports every declared symbol,
+and its host small-dense routines agree with LAPACK (via NumPy)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2607_14742_b300 as pb
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "care_b300.h")
+
+
+def declared_functions():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted({n for n in names if n not in ("if", "while", "for", "return", "sizeof")})
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = pb.lib()
+    names = declared_functions()
+    assert "care_solve" in names and "lyap_lradi" in names and "care_residual_factor" in names
+    for name in names:
+        assert hasattr(L, name), name
+        assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
+
+
+def test_status_strings_and_defaults():
+    assert pb.status_string(0) == "CARE_OK"
+    assert pb.status_string(6) == "CARE_STAGNATED"
+    o = pb.default_options()
+    # Section 5 parameter list
+    assert (o.kmax, o.jmax) == (20, 50)
+    assert o.eta_r_rel == 1e-4 and o.eta_s_mult == 10.0
+    assert o.tau_L_lo == 1e-5 and o.tau_L_hi == 1e-12
+    assert o.krylov_tol_lo == 1e-5 and o.krylov_tol_hi == 1e-10
+    assert (o.krylov_maxit_lo, o.krylov_maxit_hi) == (100, 200)
+    assert o.stag_ratio == 0.999
+    assert "sm_103a" in pb.version()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 31, 64, 150])
+def test_host_symeig_matches_lapack(n):
+    rng = np.random.default_rng(n)
+    M = rng.standard_normal((n, n))
+    A = M + M.T
+    w, V = pb.host_symeig(A)
+    wr = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.abs(wr).max())
+    assert np.abs(w - wr).max() <= 1e-13 * scale * n
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-13 * n
+    assert np.abs(A @ V - V * w).max() <= 1e-13 * scale * n
+
+
+def test_host_symeig_degenerate():
+    w, V = pb.host_symeig(np.eye(6))
+    assert np.allclose(w, 1.0) and np.allclose(V.T @ V, np.eye(6))
+    w, _ = pb.host_symeig(np.zeros((3, 3)))
+    assert np.all(w == 0)
+    # clustered spectrum with a rank-2 perturbation
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    d = np.concatenate([np.full(20, 1.0), np.full(18, 1.0 + 1e-12), [5.0, -3.0]])
+    A = (Q * d) @ Q.T
+    w, V = pb.host_symeig(A)
+    assert np.abs(np.sort(d) - w).max() < 1e-13 * 5 * 40
+    assert np.abs(V.T @ V - np.eye(40)).max() < 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 9, 33, 64])
+def test_host_eigvals_matches_lapack(n):
+    rng = np.random.default_rng(100 + n)
+    M = rng.standard_normal((n, n))
+    ev = pb.host_eigvals(M)
+    er = np.linalg.eigvals(M)
+    scale = max(1.0, np.abs(er).max())
+    # same multiset: greedy matching
+    left = list(er)
+    for e in ev:
+        k = int(np.argmin(np.abs(np.array(left) - e)))
+        assert abs(left[k] - e) <= 1e-10 * scale
+        left.pop(k)
+
+
+def test_host_eigvals_structured():
+    # companion-like and rotation blocks (complex pairs), triangular (already Schur)
+    R = np.array([[0.0, -2.0], [2.0, 0.0]])
+    ev = np.sort_complex(pb.host_eigvals(R))
+    assert np.allclose(ev, [-2j, 2j])
+    T = np.triu(np.arange(1.0, 26.0).reshape(5, 5))
+    assert np.allclose(np.sort(pb.host_eigvals(T).real), np.sort(np.diag(T)))
+
+
+def test_workspace_size_grows_with_problem():
+    a = pb.workspace_size(400, 1920, 1, 1, 64, "mixed")
+    b = pb.workspace_size(250000, 1248000, 5, 5, 512, "mixed")
+    c = pb.workspace_size(250000, 1248000, 5, 5, 512, "fp64")
+    assert 0 < a < b < c

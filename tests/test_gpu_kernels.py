@@ -1,0 +1,109 @@
+"""GPU parity of the kernel-level entry points (SpMM, Gram, SMW shifted solve)
+against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import care_inputs as ci
+from oracle import lowrank as ol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_14742_b300 as m
+    m.lib()
+    return m
+
+
+def _ops(pb, prob):
+    A = prob.A
+    dA = pb.CSR.from_arrays(A.n, A.rowptr, A.colind, A.val)
+    return dA, pb.Operator(dA), A.to_scipy()
+
+
+@pytest.mark.parametrize("N,b", [(20, 1), (20, 3), (23, 8), (31, 13), (40, 64), (17, 130)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shift", [0.0, -250.0, complex(-300.0, 900.0)])
+def test_spmm_parity(pb, N, b, dtype, shift):
+    """Y = (A^T + p I) X element by element against the oracle, ragged widths, complex shifts,
+    and widths above one kernel chunk (130 reals)."""
+    prob = ci.config_small_fdm(N)
+    dA, op, As = _ops(pb, prob)
+    cplx = isinstance(shift, complex)
+    if cplx and b > 64:
+        b = 64
+    X = ci.random_block(prob.n, b, 31)
+    if cplx:
+        X = X + 1j * ci.random_block(prob.n, b, 32)
+    ref = ol.shifted_operator_apply(As, shift, X)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    if cplx:
+        Xt = torch.tensor(X, dtype=torch.complex128 if dtype == "f64" else torch.complex64, device="cuda")
+    else:
+        Xt = torch.tensor(X, dtype=tdt, device="cuda")
+    Y = pb.spmm(op, Xt, shift).cpu().numpy().astype(np.complex128 if cplx else np.float64)
+    # rounding bound: |A^T| |X| + |p| |X| with gamma_{k} of the precision (k <= 6 terms)
+    bound = np.abs(As.T) @ np.abs(X) + abs(shift) * np.abs(X)
+    u = U64 if dtype == "f64" else U32
+    # FP32 path also rounds A and X to FP32 (two more roundings per term)
+    k = 8 if dtype == "f64" else 12
+    assert np.all(np.abs(Y - ref) <= k * u * bound + 1e-300)
+
+
+def test_spmm_large_ragged(pb):
+    """n = 250,000 operator (the 500x500 grid) on a 10-column block: sampled rows."""
+    prob = ci.config_fdm2d(500, 1, 1)
+    dA, op, As = _ops(pb, prob)
+    X = ci.random_block(prob.n, 10, 33)
+    Y = pb.spmm(op, torch.tensor(X, dtype=torch.float32, device="cuda"), -1000.0).cpu().numpy()
+    rows = np.random.default_rng(0).choice(prob.n, 2000, replace=False)
+    ref = (As.T[rows] @ X) - 1000.0 * X[rows]
+    bound = np.abs(As.T[rows]) @ np.abs(X) + 1000.0 * np.abs(X[rows])
+    assert np.all(np.abs(Y[rows] - ref) <= 12 * U32 * bound)
+
+
+@pytest.mark.parametrize("n,a,b", [(1, 1, 1), (100, 3, 5), (1000, 64, 64), (5003, 65, 7), (20000, 130, 200)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_gram_parity(pb, n, a, b, dtype):
+    X = ci.random_block(n, a, 41)
+    Y = ci.random_block(n, b, 42)
+    ref = ol.gram(X, Y)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    G = pb.gram(torch.tensor(X, dtype=tdt, device="cuda"), torch.tensor(Y, dtype=tdt, device="cuda")).cpu().numpy()
+    if dtype == "f32":
+        Xr, Yr = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+        ref = ol.gram(Xr, Yr)
+    bound = np.abs(X).T @ np.abs(Y)
+    u = U64 if dtype == "f64" else U32
+    assert np.all(np.abs(G - ref) <= (n + 2) * u * bound + 1e-300)
+
+
+def test_gram_deterministic(pb):
+    X = torch.tensor(ci.random_block(300000, 12, 43), dtype=torch.float32, device="cuda")
+    g1 = pb.gram(X, X)
+    g2 = pb.gram(X, X)
+    assert torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+@pytest.mark.parametrize("shift", [-400.0, complex(-900.0, 1500.0)])
+@pytest.mark.parametrize("feedback", [False, True])
+def test_shifted_solve_parity(pb, prec, tol, shift, feedback):
+    """SMW + block BiCGStab vs the oracle's sparse-LU SMW solve (Section 4)."""
+    prob = ci.config_small_fdm()
+    dA, op, As = _ops(pb, prob)
+    W = ci.random_block(prob.n, 3, 51)
+    K = 1e-2 * ci.random_block(prob.n, 1, 52) if feedback else None
+    B = prob.B if feedback else None
+    ref = ol.smw_solve(ol.ShiftedSolver(As), B, K, shift, W)
+    V, iters = pb.shifted_solve(op, W, shift, B=B, K=K, prec=prec)
+    V = V.cpu().numpy()
+    assert iters > 0
+    assert np.linalg.norm(V - ref) <= tol * np.linalg.norm(ref)
