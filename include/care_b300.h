@@ -63,7 +63,7 @@ typedef enum {
 } care_prec;
 
 typedef enum { CARE_KRYLOV_BICGSTAB = 0 } care_krylov;
-typedef enum { CARE_PRECOND_NONE = 0, CARE_PRECOND_JACOBI = 1 } care_precond;
+typedef enum { CARE_PRECOND_NONE = 0, CARE_PRECOND_JACOBI = 1, CARE_PRECOND_ILU0 = 2 } care_precond;
 
 /* A itself (not A^T) in CSR: int32 row pointers (n+1) and column indices (nnz),
  * FP64 values (nnz); device pointers; column indices need not be sorted. */
@@ -99,6 +99,8 @@ typedef struct {
   int krylov_chunk;      /* max right-hand-side columns per Krylov call (<= 64)      */
   double stag_ratio;     /* refinement stops if ||R_{k+1}|| / ||R_k|| > stag_ratio   */
   int shift_hmin;        /* min. projection basis width for shift generation         */
+  int ilu_sweeps;        /* ILU(0) fixed-point sweeps per shift (CARE_PRECOND_ILU0)  */
+  int tri_sweeps;        /* Jacobi sweeps per triangular factor in the ILU(0) apply  */
   int verbose;           /* 0 silent, 1 per outer step, 2 per ADI step (stderr)      */
 } care_opts;
 
@@ -132,7 +134,11 @@ typedef struct {
   float* val32_t;   /* A^T values rounded to FP32                                    */
   double* diag64;   /* diag(A)                                                       */
   float* diag32;
+  float* rowsum32_t;  /* row sums of A^T (FP64 sums rounded to FP32): the FP32 operator is
+                         applied in the difference form sum_j a_ij (x_j - x_i) + s_i x_i */
+  int max_row_nnz;  /* longest row of A^T                                            */
   int diag_const;   /* 1 if all diagonal entries are equal (Jacobi is then a no-op)  */
+  int full_diag;    /* 1 if every row stores its diagonal entry (required by ILU(0)) */
   double a_fro;     /* ||A||_F                                                       */
 } care_op;
 

@@ -29,6 +29,7 @@ PREC_MIXED_FP32 = 1
 PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED_FP32, "mixed_fp32": PREC_MIXED_FP32}
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
+PRECOND_ILU0 = 2
 HIST_MAX = 32
 
 
@@ -50,7 +51,8 @@ class opts_t(ct.Structure):
                 ("krylov_tol_lo", ct.c_double), ("krylov_tol_hi", ct.c_double),
                 ("krylov_maxit_lo", ct.c_int), ("krylov_maxit_hi", ct.c_int), ("krylov", ct.c_int),
                 ("precond", ct.c_int), ("krylov_chunk", ct.c_int), ("stag_ratio", ct.c_double),
-                ("shift_hmin", ct.c_int), ("verbose", ct.c_int)]
+                ("shift_hmin", ct.c_int), ("ilu_sweeps", ct.c_int), ("tri_sweeps", ct.c_int),
+                ("verbose", ct.c_int)]
 
 
 class info_t(ct.Structure):
@@ -64,7 +66,9 @@ class info_t(ct.Structure):
 class op_t(ct.Structure):
     _fields_ = [("n", ct.c_int), ("nnz", ct.c_int), ("rowptr_t", ct.c_void_p), ("colind_t", ct.c_void_p),
                 ("val64_t", ct.c_void_p), ("val32_t", ct.c_void_p), ("diag64", ct.c_void_p),
-                ("diag32", ct.c_void_p), ("diag_const", ct.c_int), ("a_fro", ct.c_double)]
+                ("diag32", ct.c_void_p), ("rowsum32_t", ct.c_void_p), ("max_row_nnz", ct.c_int),
+                ("diag_const", ct.c_int), ("full_diag", ct.c_int),
+                ("a_fro", ct.c_double)]
 
 
 _lib = None

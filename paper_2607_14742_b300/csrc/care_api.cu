@@ -24,6 +24,7 @@ static size_t op_bytes(int n, int nnz) {
   a.get<float>((size_t)nnz);   // val32_t
   a.get<double>((size_t)n);    // diag64
   a.get<float>((size_t)n);     // diag32
+  a.get<float>((size_t)n);     // rowsum32_t
   a.get<int>((size_t)n + 1);   // cursor / counts
   a.get<double>(4);            // reductions
   return a.off;
@@ -76,7 +77,7 @@ __global__ void k_scatter(int n, const int* rp, const int* ci, const double* v, 
 // sort each row of A^T by column (insertion sort; rows are short), merge
 // duplicate-free; cast values; extract the diagonal
 __global__ void k_finish_rows(int n, const int* rpt, int* cit, double* vt, float* vt32, double* d64,
-                              float* d32) {
+                              float* d32, float* rs32, double* missing, int* maxrow) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const int b = rpt[i], e = rpt[i + 1];
     for (int k = b + 1; k < e; ++k) {
@@ -91,11 +92,19 @@ __global__ void k_finish_rows(int n, const int* rpt, int* cit, double* vt, float
       cit[q + 1] = c;
       vt[q + 1] = v;
     }
-    double dg = 0.0;
+    double dg = 0.0, rs = 0.0;
+    bool has = false;
     for (int k = b; k < e; ++k) {
       vt32[k] = (float)vt[k];
-      if (cit[k] == i) dg += vt[k];
+      rs += vt[k];
+      if (cit[k] == i) {
+        dg += vt[k];
+        has = true;
+      }
     }
+    if (!has) atomicAdd(missing, 1.0);
+    atomicMax(maxrow, e - b);
+    rs32[i] = (float)rs;
     d64[i] = dg;
     d32[i] = (float)dg;
   }
@@ -142,6 +151,7 @@ static void prepare_op(const care_csr* A, void* mem, size_t bytes, cudaStream_t 
   op->val32_t = a.get<float>((size_t)nnz);
   op->diag64 = a.get<double>((size_t)n);
   op->diag32 = a.get<float>((size_t)n);
+  op->rowsum32_t = a.get<float>((size_t)n);
   int* cnt = a.get<int>((size_t)n + 1);
   double* red = a.get<double>(4);
   const int g = device_sms() * 4;
@@ -153,14 +163,20 @@ static void prepare_op(const care_csr* A, void* mem, size_t bytes, cudaStream_t 
   CARE_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)n + 1), s));
   k_scatter<<<g, 256, 0, s>>>(n, A->rowptr, A->colind, A->val, op->rowptr_t, cnt, op->colind_t, op->val64_t);
   CARE_LAUNCH();
+  CARE_CUDA(cudaMemsetAsync(red, 0, sizeof(double) * 4, s));
+  CARE_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
   k_finish_rows<<<g, 256, 0, s>>>(n, op->rowptr_t, op->colind_t, op->val64_t, op->val32_t, op->diag64,
-                                    op->diag32);
+                                    op->diag32, op->rowsum32_t, red + 3, cnt);
   CARE_LAUNCH();
   k_op_stats<<<1, 1024, 0, s>>>(n, nnz, op->val64_t, op->diag64, red);
   CARE_LAUNCH();
   double h[4];
-  CARE_CUDA(cudaMemcpyAsync(h, red, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+  int mr = 0;
+  CARE_CUDA(cudaMemcpyAsync(&mr, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CARE_CUDA(cudaMemcpyAsync(h, red, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
   CARE_CUDA(cudaStreamSynchronize(s));
+  op->full_diag = h[3] == 0.0 ? 1 : 0;
+  op->max_row_nnz = mr;
   op->a_fro = std::sqrt(h[0]);
   op->diag_const = (n == 0 || h[1] == h[2]) ? 1 : 0;
 }
@@ -480,6 +496,7 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
                               int ldc, int p, double tol, double* Zout, int ldz, int r_cap, care_info* info) {
   const double t0 = now_ms();
   const int n = A->n;
+  c.op_nnz = A->nnz;
   const Caps k = caps_for(n, m, p, r_cap, c.o);
   // operator first (its memory leads the workspace)
   void* opmem = c.ar.get<char>(op_bytes(n, A->nnz));
@@ -539,7 +556,7 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     gemm_ts<double, T>(n, r, m, 1.0, S.R.QZ, S.R.ldq, upload(c, KB), m, 0.0, S.in.K, S.in.ldm, c.s);
     t1 = now_ms();
     const int bw = a1.rp + a1.rm;
-    AdiResult ad = lradi<T>(c, S.in, bw, a1.rp, true, tauL, c.o.jmax, false);
+    AdiResult ad = lradi<T>(c, S.in, bw, a1.rp, true, tauL, c.o.jmax, false, true);
     inf.iter_inner += ad.steps;
     CARE_CUDA(cudaStreamSynchronize(c.s));
     inf.ms_phase[2] += now_ms() - t1;
@@ -571,6 +588,7 @@ static care_status lradi_impl(Ctx& c, const care_csr* A, const double* B, int ld
                               int r_cap, care_info* info) {
   const double t0 = now_ms();
   const int n = A->n;
+  c.op_nnz = A->nnz;
   care_opts o2 = c.o;
   o2.adi_cap = std::max(c.o.adi_cap, r_cap);
   const Caps k = caps_for(n, std::max(m, 1), b, 1, o2);
@@ -652,6 +670,7 @@ static care_status shifted_impl(Ctx& c, const care_op* op, const double* B, int 
                                 int m, double pre, double pim, const double* W, int ldw, int b, double* V,
                                 int ldv, int* iters) {
   const long n = op->n;
+  c.op_nnz = op->nnz;
   Inner<T> in;
   alloc_small(c, n, 2 * (b + m) + 64, 4 * (b + m + 8) * (b + m + 8) + 65536);
   in.alloc(c, (int)n, std::max(m, 1), b, 1, 1);
@@ -706,7 +725,7 @@ void care_opts_default(care_opts* o) {
   o->kmax = 20;
   o->jmax = 50;
   o->newton_max = 50;
-  o->adi_cap = 1024;
+  o->adi_cap = 2048;
   o->eta_r_rel = 1e-4;
   o->eta_s_mult = 10.0;
   o->tau_L_lo = 1e-5;
@@ -718,10 +737,12 @@ void care_opts_default(care_opts* o) {
   o->krylov_maxit_lo = 100;
   o->krylov_maxit_hi = 200;
   o->krylov = CARE_KRYLOV_BICGSTAB;
-  o->precond = CARE_PRECOND_JACOBI;
+  o->precond = CARE_PRECOND_ILU0;
   o->krylov_chunk = 64;
   o->stag_ratio = 0.999;
   o->shift_hmin = 4;
+  o->ilu_sweeps = 3;
+  o->tri_sweeps = 2;
   o->verbose = 0;
 }
 

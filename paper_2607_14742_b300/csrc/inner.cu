@@ -113,13 +113,20 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   CARE_REQUIRE(out == nullptr || !second_pass, CARE_ERR_INVALID_ARG, "orth_rr: out needs one pass");
   if (cols == 0) return o;
   std::vector<double> G = gram_h<T>(c, n, cols, cols, X, ldx, X, ldx);
-  // column scaling; columns at or below their floor are dropped
+  // column scaling; columns at or below their floor are dropped.  drop_rel < 0
+  // selects the unscaled mode: pivots are compared with |drop_rel| * max_j G_jj,
+  // i.e. the truncation is relative to the largest column of X (used to cut
+  // factors at the accuracy of the precision that produced them).
+  const bool unscaled = drop_rel < 0.0;
+  double gmax = 0.0;
+  for (int j = 0; j < cols; ++j) gmax = std::max(gmax, G[(size_t)j * cols + j]);
   std::vector<double> d(cols, 0.0);
   for (int j = 0; j < cols; ++j) {
     const double g = G[(size_t)j * cols + j];
     const double fl = colfloor2 ? (*colfloor2)[j] : 0.0;
-    if (g > fl && g > 0.0 && std::isfinite(g)) d[j] = std::sqrt(g);
+    if (g > fl && g > 0.0 && std::isfinite(g)) d[j] = unscaled ? 1.0 : std::sqrt(g);
   }
+  if (unscaled) drop_rel = -drop_rel * gmax;
   std::vector<double> Gs((size_t)cols * cols, 0.0);
   for (int i = 0; i < cols; ++i)
     for (int j = 0; j < cols; ++j)
@@ -217,8 +224,10 @@ template std::vector<double> cgs2<double>(Ctx&, long, const double*, int, int, d
 template <class T>
 void Inner<T>::alloc(Ctx& c, int n_, int m_, int bcap_, int adicap_, int hcap_) {
   n = n_; m = m_; bcap = bcap_; adicap = adicap_; hcap = hcap_;
-  jacobi = c.o.precond == CARE_PRECOND_JACOBI;
-  kw = krylov_alloc<T>(c.ar, n, jacobi);
+  jacobi = c.o.precond != CARE_PRECOND_NONE;
+  kw = krylov_alloc<T>(c.ar, n, jacobi, c.o.precond == CARE_PRECOND_ILU0 ? (long)c.op_nnz : -1L);
+  kw.ilu_sweeps = c.o.ilu_sweeps;
+  kw.tri_sweeps = c.o.tri_sweeps;
   ldm = pad_ld<T>(std::max(m, 1));
   ldw = pad_ld<T>(std::max(bcap, 1));
   ldr = pad_ld<T>(2 * (bcap + m));
@@ -350,7 +359,7 @@ static void smw_solve(Ctx& c, Inner<T>& in, Shift p, int b, bool hasK) {
   for (int c0 = 0; c0 < rc; c0 += chunk) {
     const int w = std::min(chunk, rc - c0);
     KrylovResult kr = krylov_bicgstab<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr,
-                                         w, krylov_tol<T>(c), krylov_maxit<T>(c), in.jacobi, in.kw, c.s);
+                                         w, krylov_tol<T>(c), krylov_maxit<T>(c), c.o.precond, in.kw, c.s);
     c.krylov_iters += kr.iters;
     c.spmm_calls += kr.spmm;
     if (kr.unconverged) c.krylov_unconverged++;
@@ -415,7 +424,11 @@ template <class T>
 static int compress_part(Ctx& c, Inner<T>& in, int col0, int ncols, bool right_aligned) {
   if (ncols == 0) return 0;
   const long n = in.n;
-  const double drop = sizeof(T) == 4 ? 1e-6 : 1e-12;
+  // unscaled truncation at the accuracy of the inner precision u_s: directions
+  // whose residual column norm^2 is below (a few u_s) times the largest column
+  // norm^2 carry less than that fraction of X_+- and are below what the inner
+  // solve determines (the inner backward error is O(u_s), Assumption 2)
+  const double drop = sizeof(T) == 4 ? -2.0e-7 : -1.0e-15;
   OrthOut o = orth_rr<T>(c, n, ncols, in.Z + col0, in.ldz, in.Zs, in.ldz, drop, nullptr, true, 0, nullptr, 0);
   const int q = o.rank;
   if (q == 0) return 0;
@@ -435,7 +448,8 @@ static int compress_part(Ctx& c, Inner<T>& in, int col0, int ncols, bool right_a
 }
 
 template <class T>
-AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew) {
+AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew,
+                bool compress_end) {
   AdiResult res;
   const long n = in.n;
   const int rm = b - rp;
@@ -525,6 +539,11 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
     if (verbose_level() >= 2)
       fprintf(stderr, "[care]   adi j=%d p=(%.4e,%.4e) res=%.3e cols=%d+%d\n", j, p.re, p.im, r, np, nm);
   }
+  if (compress_end && np + nm > 2 * b) {
+    np = compress_part<T>(c, in, 0, np, false);
+    nm = compress_part<T>(c, in, cap - nm, nm, true);
+    res.compressions++;
+  }
   res.np = np;
   res.nm = nm;
   res.steps = j;
@@ -535,8 +554,8 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
             j, r, np, nm, res.compressions, c.krylov_unconverged);
   return res;
 }
-template AdiResult lradi<float>(Ctx&, Inner<float>&, int, int, bool, double, int, bool);
-template AdiResult lradi<double>(Ctx&, Inner<double>&, int, int, bool, double, int, bool);
+template AdiResult lradi<float>(Ctx&, Inner<float>&, int, int, bool, double, int, bool, bool);
+template AdiResult lradi<double>(Ctx&, Inner<double>&, int, int, bool, double, int, bool, bool);
 
 template <class T>
 NlrResult nlradi(Ctx& c, Inner<T>& in, const T* Ct, int ldct, int p, double tol_lyap, double tol_newton,
@@ -555,7 +574,7 @@ NlrResult nlradi(Ctx& c, Inner<T>& in, const T* Ct, int ldct, int p, double tol_
       b += in.m;
     }
     CARE_CUDA(cudaMemsetAsync(in.Knew, 0, (size_t)n * in.ldm * sizeof(T), c.s));
-    AdiResult a = lradi<T>(c, in, b, b, hasK, tol_lyap, jmax, true);
+    AdiResult a = lradi<T>(c, in, b, b, hasK, tol_lyap, jmax, true, false);
     out.adi += a.steps;
     out.newton = i + 1;
     out.cols = a.np;

@@ -14,15 +14,19 @@ namespace care {
 constexpr int GT = 64;   // output tile
 constexpr int GK = 32;   // rows (gram) / inner columns (gemm_ts) per stage
 
-size_t gram_work_elems(long n, int a, int b) {
+// number of row slices of a Gram product: about two CTAs per SM in total,
+// at least 4 staging slabs per CTA
+static long gram_split(long n, int a, int b) {
   const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
   const long tiles = (long)ta * tb;
   long split = (2L * device_sms() + tiles - 1) / tiles;
   long maxsplit = (n + 4 * GK - 1) / (4 * GK);
   if (split > maxsplit) split = maxsplit;
   if (split < 1) split = 1;
-  return (size_t)split * ta * GT * tb * GT;
+  return split;
 }
+
+size_t gram_work_elems(long n, int a, int b) { return (size_t)gram_split(n, a, b) * a * b; }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_gram(long n, int a, int b, const T* __restrict__ X, int ldx,
@@ -78,29 +82,38 @@ __global__ void __launch_bounds__(256) k_gram(long n, int a, int b, const T* __r
     }
     __syncthreads();
   }
-  const int TA = gridDim.y * GT, TB = gridDim.z * GT;
-  double* out = part + (size_t)blockIdx.x * TA * TB;
+  // compact partial layout [split][a][b]: only valid entries are written
+  double* out = part + (size_t)blockIdx.x * a * b;
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty * 4 + u;
+    if (i >= a) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-      out[(size_t)(i0 + ty * 4 + u) * TB + j0 + tx * 4 + v] = sizeof(T) == 4 ? accd[u][v] : (double)acc[u][v];
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + tx * 4 + v;
+      if (j < b) out[(size_t)i * b + j] = sizeof(T) == 4 ? accd[u][v] : (double)acc[u][v];
+    }
+  }
 }
 
-__global__ void k_gram_reduce(int a, int b, int TA, int TB, long split, const double* __restrict__ part,
-                              double* __restrict__ G, int ldg) {
+// one warp per output: lanes sum strided partials, then a fixed xor-shuffle tree
+__global__ void k_gram_reduce(int a, int b, long split, const double* __restrict__ part, double* __restrict__ G,
+                              int ldg) {
   const long total = (long)a * b;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / b), j = (int)(e % b);
-    const size_t off = (size_t)i * TB + j;
-    double s0 = 0, s1 = 0;
-    long g = 0;
-    for (; g + 1 < split; g += 2) {
-      s0 += part[(size_t)g * TA * TB + off];
-      s1 += part[(size_t)(g + 1) * TA * TB + off];
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x / 32);
+  for (long e = (blockIdx.x * (long)blockDim.x + threadIdx.x) / 32; e < total; e += warps) {
+    double s0 = 0.0, s1 = 0.0;
+    long g = lane;
+    for (; g + 32 < split; g += 64) {
+      s0 += part[(size_t)g * total + e];
+      s1 += part[(size_t)(g + 32) * total + e];
     }
-    if (g < split) s0 += part[(size_t)g * TA * TB + off];
-    G[(size_t)i * ldg + j] = s0 + s1;
+    if (g < split) s0 += part[(size_t)g * total + e];
+    double v = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) G[(size_t)(e / b) * ldg + (e % b)] = v;
   }
 }
 
@@ -111,7 +124,7 @@ void gram(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double
   const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
   const size_t need = gram_work_elems(n, a, b);
   CARE_REQUIRE(need <= work_elems, CARE_ERR_WORKSPACE, "gram: scratch too small");
-  const long split = (long)(need / ((size_t)ta * GT * tb * GT));
+  const long split = gram_split(n, a, b);
   const long rows_per = ((n + split - 1) / split + GK - 1) / GK * GK;
   if (n == 0) {
     CARE_CUDA(cudaMemsetAsync(work, 0, need * sizeof(double), s));
@@ -121,9 +134,9 @@ void gram(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double
     CARE_LAUNCH();
   }
   const long tot = (long)a * b;
-  int g = (int)((tot + 255) / 256);
-  if (g > device_sms() * 4) g = device_sms() * 4;
-  k_gram_reduce<<<g, 256, 0, s>>>(a, b, ta * GT, tb * GT, n == 0 ? 1 : split, work, G, ldg);
+  int g = (int)((tot + 7) / 8);  // 8 warps per CTA, one output per warp
+  if (g > device_sms() * 8) g = device_sms() * 8;
+  k_gram_reduce<<<g, 256, 0, s>>>(a, b, n == 0 ? 1 : split, work, G, ldg);
   CARE_LAUNCH();
 }
 template void gram<float>(long, int, int, const float*, int, const float*, int, double*, int, double*,

@@ -23,12 +23,15 @@ OpT<double> op64(const care_op& o) {
   OpT<double> r;
   r.n = o.n; r.nnz = o.nnz; r.rp = o.rowptr_t; r.ci = o.colind_t; r.val = o.val64_t; r.diag = o.diag64;
   r.diag_const = o.diag_const != 0;
+  r.full_diag = o.full_diag != 0 && o.max_row_nnz <= 32;
   return r;
 }
 OpT<float> op32(const care_op& o) {
   OpT<float> r;
   r.n = o.n; r.nnz = o.nnz; r.rp = o.rowptr_t; r.ci = o.colind_t; r.val = o.val32_t; r.diag = o.diag32;
+  r.rowsum = o.rowsum32_t;
   r.diag_const = o.diag_const != 0;
+  r.full_diag = o.full_diag != 0 && o.max_row_nnz <= 32;
   return r;
 }
 
@@ -86,18 +89,39 @@ __device__ bool dot_reduce(const T (&acc)[NDOT][NVPT * (16 / sizeof(T))], int w,
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
+  // last CTA: TPI threads per item sum strided subsets of the G partials, then a
+  // fixed-order tree in shared memory (deterministic for a given grid)
   const int G = gridDim.x;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int g = 0;
-    for (; g + 3 < G; g += 4) {
-      s0 += __ldcg(d.partial + (size_t)(g + 0) * items + it);
-      s1 += __ldcg(d.partial + (size_t)(g + 1) * items + it);
-      s2 += __ldcg(d.partial + (size_t)(g + 2) * items + it);
-      s3 += __ldcg(d.partial + (size_t)(g + 3) * items + it);
+  int TPI = 1;
+  while (TPI * 2 * items <= (int)blockDim.x) TPI *= 2;
+  __shared__ double red[kBlock];
+  {
+    const int t = threadIdx.x;
+    const int item = t / TPI, lane = t % TPI;
+    double s0 = 0.0, s1 = 0.0;
+    if (item < items) {
+      int g = lane;
+      for (; g + TPI < G; g += 2 * TPI) {
+        s0 += __ldcg(d.partial + (size_t)g * items + item);
+        s1 += __ldcg(d.partial + (size_t)(g + TPI) * items + item);
+      }
+      if (g < G) s0 += __ldcg(d.partial + (size_t)g * items + item);
     }
-    for (; g < G; ++g) s0 += __ldcg(d.partial + (size_t)g * items + it);
-    d.out[it] = (s0 + s1) + (s2 + s3);
+    red[t] = s0 + s1;
+    __syncthreads();
+    for (int w = TPI / 2; w > 0; w >>= 1) {
+      if (lane < w) red[t] += red[t + w];
+      __syncthreads();
+    }
+    if (item < items && lane == 0) d.out[item] = red[t];
+  }
+  // items beyond one pass of the block (items > blockDim.x) use one thread each
+  for (int it = blockDim.x; it < items; it += blockDim.x) {
+    const int item = it + threadIdx.x;
+    if (item >= items) continue;
+    double s0 = 0.0;
+    for (int g = 0; g < G; ++g) s0 += __ldcg(d.partial + (size_t)g * items + item);
+    d.out[item] = s0;
   }
   if (threadIdx.x == 0) *d.counter = 0u;
   __threadfence();
@@ -186,6 +210,7 @@ struct SpmmArgs {
   const int* rp;
   const int* ci;
   const T* av;
+  const T* rs;  // row sums: difference form  y_i = sum_j a_ij (x_j - x_i) + (s_i + p) x_i
   const T* X;
   int ldx;
   T* Y;
@@ -211,14 +236,21 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
   for (int q = 0; q < ND; ++q)
 #pragma unroll
     for (int e = 0; e < NS; ++e) acc[q][e] = T(0);
-  const T sre = (T)a.sre, sim = (T)a.sim;
+  const T sim = (T)a.sim;
+  const bool diff = a.rs != nullptr;
   for (long row = it.row; row < a.n; row += it.stride) {
     const int s = __ldg(a.rp + row), e = __ldg(a.rp + row + 1);
-    T y[NVPT][VEC];
+    T y[NVPT][VEC], xi[NVPT][VEC];
 #pragma unroll
-    for (int k = 0; k < NVPT; ++k)
+    for (int k = 0; k < NVPT; ++k) {
+      const int v = it.lane_v + k * TPR;
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) y[k][q] = T(0);
+      for (int q = 0; q < VEC; ++q) {
+        y[k][q] = T(0);
+        xi[k][q] = T(0);
+      }
+      if (v < a.nvec && diff) vload(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
+    }
     for (int j = s; j < e; ++j) {
       const int c = __ldg(a.ci + j);
       const T av = __ldg(a.av + j);
@@ -230,27 +262,28 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
           T x[VEC];
           vload(xr + v * VEC, x);
 #pragma unroll
-          for (int q = 0; q < VEC; ++q) y[k][q] = fma(av, x[q], y[k][q]);
+          for (int q = 0; q < VEC; ++q) y[k][q] = fma(av, x[q] - xi[k][q], y[k][q]);
         }
       }
     }
+    // diagonal term: (s_i + p) in the difference form, p otherwise
+    const T dre = (T)a.sre + (diff ? __ldg(a.rs + row) : T(0));
 #pragma unroll
     for (int k = 0; k < NVPT; ++k) {
       const int v = it.lane_v + k * TPR;
       if (v < a.nvec) {
-        T xi[VEC];
-        vload(a.X + (size_t)row * a.ldx + v * VEC, xi);
+        if (!diff) vload(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
         if constexpr (CPLX) {
 #pragma unroll
           for (int q = 0; q < VEC; q += 2) {
-            const T yr = y[k][q] + sre * xi[q] - sim * xi[q + 1];
-            const T yi = y[k][q + 1] + sre * xi[q + 1] + sim * xi[q];
+            const T yr = y[k][q] + dre * xi[k][q] - sim * xi[k][q + 1];
+            const T yi = y[k][q + 1] + dre * xi[k][q + 1] + sim * xi[k][q];
             y[k][q] = yr;
             y[k][q + 1] = yi;
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < VEC; ++q) y[k][q] = fma(sre, xi[q], y[k][q]);
+          for (int q = 0; q < VEC; ++q) y[k][q] = fma(dre, xi[k][q], y[k][q]);
         }
         vstore(a.Y + (size_t)row * a.ldy + v * VEC, y[k]);
         if constexpr (NDOT > 0) {
@@ -310,7 +343,7 @@ void spmm(const OpT<T>& op, cd sigma, bool cplx, const T* X, int ldx, T* Y, int 
   for (int c0 = 0; c0 < cols; c0 += chunk) {
     const int w = (cols - c0 < chunk) ? cols - c0 : chunk;
     SpmmArgs<T> a{};
-    a.n = op.n; a.rp = op.rp; a.ci = op.ci; a.av = op.val;
+    a.n = op.n; a.rp = op.rp; a.ci = op.ci; a.av = op.val; a.rs = op.rowsum;
     a.X = X + c0; a.ldx = ldx; a.Y = Y + c0; a.ldy = ldy;
     a.nvec = (w + VEC - 1) / VEC;
     a.sre = sigma.re; a.sim = sigma.im;
@@ -338,6 +371,13 @@ struct KArgs {
   KHeader* hdr;
   DotOut dots;
   double tol2;
+  // ILU(0) preconditioner
+  const int* rp;
+  const int* ci;
+  const int* dpos;
+  const T* F;
+  T *Y1, *Y2, *Y3;
+  int tri_sweeps;
 };
 
 // scalar of column slot q of vector v (complex: pairs share one state entry)
@@ -385,7 +425,7 @@ struct ThreadCols {
 };
 
 // init: r = rhs (zero beyond cols), rhat = r, x = p = v = 0; dots <rhat, r>, <r, r>
-template <class T, int TPR, int NVPT, bool CPLX, bool PREC>
+template <class T, int TPR, int NVPT, bool CPLX, int PREC>
 __global__ void __launch_bounds__(kBlock) k_bicg_init(KArgs<T> a) {
   constexpr int VEC = 16 / sizeof(T), NS = NVPT * VEC;
   RowIter<TPR> it;
@@ -421,7 +461,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_init(KArgs<T> a) {
 }
 
 // p = r + beta (p - omega v);  ph = Dinv p
-template <class T, int TPR, int NVPT, bool CPLX, bool PREC>
+template <class T, int TPR, int NVPT, bool CPLX, int PREC>
 __global__ void __launch_bounds__(kBlock) k_bicg_p(KArgs<T> a) {
   constexpr int VEC = 16 / sizeof(T);
   constexpr int NC = CPLX ? VEC / 2 : VEC;
@@ -462,7 +502,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_p(KArgs<T> a) {
         if (act[k][c]) p[q] = r[q] + t2[q];
       }
       vstore(a.P + off, p);
-      if constexpr (PREC) {
+      if constexpr (PREC == 1) {
         T ph[VEC];
         apply_dinv<T, CPLX, VEC>(ph, a.Dinv, row, p);
         vstore(a.Ph + off, ph);
@@ -472,7 +512,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_p(KArgs<T> a) {
 }
 
 // s = r - alpha v;  sh = Dinv s
-template <class T, int TPR, int NVPT, bool CPLX, bool PREC>
+template <class T, int TPR, int NVPT, bool CPLX, int PREC>
 __global__ void __launch_bounds__(kBlock) k_bicg_s(KArgs<T> a) {
   constexpr int VEC = 16 / sizeof(T);
   constexpr int NC = CPLX ? VEC / 2 : VEC;
@@ -504,7 +544,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_s(KArgs<T> a) {
 #pragma unroll
       for (int q = 0; q < VEC; ++q) r[q] = r[q] - t1[q];
       vstore(a.S + off, r);
-      if constexpr (PREC) {
+      if constexpr (PREC == 1) {
         T sh[VEC];
         apply_dinv<T, CPLX, VEC>(sh, a.Dinv, row, r);
         vstore(a.Sh + off, sh);
@@ -514,7 +554,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_s(KArgs<T> a) {
 }
 
 // x += alpha ph + omega sh;  r = s - omega t;  dots <rhat, r>, <r, r>
-template <class T, int TPR, int NVPT, bool CPLX, bool PREC>
+template <class T, int TPR, int NVPT, bool CPLX, int PREC>
 __global__ void __launch_bounds__(kBlock) k_bicg_xr(KArgs<T> a) {
   constexpr int VEC = 16 / sizeof(T), NS = NVPT * VEC;
   constexpr int NC = CPLX ? VEC / 2 : VEC;
@@ -553,7 +593,7 @@ __global__ void __launch_bounds__(kBlock) k_bicg_xr(KArgs<T> a) {
       vload(a.X + off, x);
       vload((PREC ? a.Ph : a.P) + off, ph);
       vload(a.S + off, s);
-      if constexpr (PREC) vload(a.Sh + off, sh);
+      if constexpr (PREC != 0) vload(a.Sh + off, sh);
       else
 #pragma unroll
         for (int q = 0; q < VEC; ++q) sh[q] = s[q];
@@ -618,8 +658,217 @@ __global__ void k_dinv(long n, const T* diag, double sre, double sim, bool cplx,
   }
 }
 
+// ------------------------------------------------------------ ILU(0) ----
+// Incomplete LU of M_p = A^T + p I on the pattern of A^T, computed by
+// fixed-point sweeps (Chow & Patel, SIAM J. Sci. Comput. 37(2), 2015): every
+// entry is updated in parallel from the previous iterate,
+//   i > j: l_ij = (m_ij - sum_{k<j} l_ik u_kj) / u_jj,
+//   i <= j: u_ij =  m_ij - sum_{k<i} l_ik u_kj,
+// with L unit lower and U upper stored in one array F on the pattern.  The
+// triangular solves of the preconditioner are approximated by Jacobi sweeps
+// (Anzt, Chow & Dongarra 2015): y <- r - (L - I) y, x <- D^{-1}(y - (U - D) x).
+// Complex shifts give complex factors (interleaved re, im).
+
+__global__ void k_diagpos(int n, const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ dpos) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    int lo = rp[i], hi = rp[i + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int c = ci[mid];
+      if (c == i) { pos = mid; break; }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    dpos[i] = pos;
+  }
+}
+
+template <class T, bool CPLX>
+__device__ __forceinline__ cd fload(const T* F, int e) {
+  if constexpr (CPLX) return cd{(double)F[2 * e], (double)F[2 * e + 1]};
+  else return cd{(double)F[e], 0.0};
+}
+template <class T, bool CPLX>
+__device__ __forceinline__ void fstore(T* F, int e, cd v) {
+  if constexpr (CPLX) { F[2 * e] = (T)v.re; F[2 * e + 1] = (T)v.im; }
+  else F[e] = (T)v.re;
+}
+
+// m_e = (A^T)_e + p [i == j]
+template <class T, bool CPLX>
+__device__ __forceinline__ cd mval(const T* av, int e, int i, int j, double pre, double pim) {
+  cd m{(double)av[e], 0.0};
+  if (i == j) { m.re += pre; m.im += pim; }
+  return m;
+}
+
+// initial guess: l_ij = m_ij / m_jj, u_ij = m_ij
+template <class T, bool CPLX>
+__global__ void k_ilu_init(int n, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ av,
+                           const int* __restrict__ dpos, double pre, double pim, T* __restrict__ F) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = ci[e];
+      cd m = mval<T, CPLX>(av, e, (int)i, j, pre, pim);
+      if (j < i) {
+        const int dj = dpos[j];
+        const cd mjj = mval<T, CPLX>(av, dj, j, j, pre, pim);
+        m = cdivz(m, mjj);
+      }
+      fstore<T, CPLX>(F, e, m);
+    }
+  }
+}
+
+// one synchronous fixed-point sweep Fnew <- G(Fold)
+template <class T, bool CPLX>
+__global__ void k_ilu_sweep(int n, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ av,
+                            const int* __restrict__ dpos, double pre, double pim, const T* __restrict__ Fo,
+                            T* __restrict__ Fn) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int b = rp[i], e_end = rp[i + 1];
+    for (int e = b; e < e_end; ++e) {
+      const int j = ci[e];
+      const int lim = j < i ? j : (int)i;  // k < min(i, j)
+      cd s = mval<T, CPLX>(av, e, (int)i, j, pre, pim);
+      for (int kk = b; kk < e_end; ++kk) {
+        const int k = ci[kk];
+        if (k >= lim) break;  // columns sorted
+        // find (k, j) in row k
+        int lo = rp[k], hi = rp[k + 1] - 1, pos = -1;
+        while (lo <= hi) {
+          const int mid = (lo + hi) >> 1;
+          const int c = ci[mid];
+          if (c == j) { pos = mid; break; }
+          if (c < j) lo = mid + 1; else hi = mid - 1;
+        }
+        if (pos >= 0) {
+          const cd t = cmul(fload<T, CPLX>(Fo, kk), fload<T, CPLX>(Fo, pos));
+          s.re -= t.re;
+          s.im -= t.im;
+        }
+      }
+      if (j < i) s = cdivz(s, fload<T, CPLX>(Fo, dpos[j]));
+      fstore<T, CPLX>(Fn, e, s);
+    }
+  }
+}
+
+// Dinv[i] = 1 / u_ii
+template <class T, bool CPLX>
+__global__ void k_ilu_dinv(int n, const int* __restrict__ dpos, const T* __restrict__ F, T* __restrict__ dinv) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const cd z = cdivz(cd{1.0, 0.0}, fload<T, CPLX>(F, dpos[i]));
+    if constexpr (CPLX) { dinv[2 * i] = (T)z.re; dinv[2 * i + 1] = (T)z.im; }
+    else dinv[i] = (T)z.re;
+  }
+}
+
+// Jacobi sweep of a triangular factor on an n x w block:
+//   LOWER:  out = r - (L - I) xin          (xin == nullptr: out = r)
+//   UPPER:  out = D^{-1} (r - (U - D) xin)  (xin == nullptr: out = D^{-1} r)
+// SCALE_OUT (LOWER only): also write out2 = D^{-1} out (the first U iterate).
 template <class T>
-KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi) {
+struct TriArgs {
+  long n;
+  const int* rp;
+  const int* ci;
+  const int* dpos;
+  const T* F;
+  const T* dinv;
+  const T* r;
+  const T* xin;
+  T* out;
+  T* out2;
+  int ld;
+  int nvec;
+};
+
+template <class T, int TPR, int NVPT, bool CPLX, bool LOWER, bool SCALE_OUT>
+__global__ void __launch_bounds__(kBlock) k_trisweep(TriArgs<T> a) {
+  constexpr int VEC = 16 / sizeof(T);
+  RowIter<TPR> it;
+  for (long row = it.row; row < a.n; row += it.stride) {
+    const int dp = __ldg(a.dpos + row);
+    const int e0 = LOWER ? __ldg(a.rp + row) : dp + 1;
+    const int e1 = LOWER ? dp : __ldg(a.rp + row + 1);
+    T acc[NVPT][VEC];
+#pragma unroll
+    for (int k = 0; k < NVPT; ++k)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[k][q] = T(0);
+    if (a.xin) {
+      for (int e = e0; e < e1; ++e) {
+        const int c = __ldg(a.ci + e);
+        T fr, fi = T(0);
+        if constexpr (CPLX) { fr = a.F[2 * e]; fi = a.F[2 * e + 1]; }
+        else fr = a.F[e];
+        const T* xr = a.xin + (size_t)c * a.ld;
+#pragma unroll
+        for (int k = 0; k < NVPT; ++k) {
+          const int v = it.lane_v + k * TPR;
+          if (v < a.nvec) {
+            T x[VEC];
+            vload(xr + v * VEC, x);
+            if constexpr (CPLX) {
+#pragma unroll
+              for (int q = 0; q < VEC; q += 2) {
+                acc[k][q] += fr * x[q] - fi * x[q + 1];
+                acc[k][q + 1] += fr * x[q + 1] + fi * x[q];
+              }
+            } else {
+#pragma unroll
+              for (int q = 0; q < VEC; ++q) acc[k][q] = fma(fr, x[q], acc[k][q]);
+            }
+          }
+        }
+      }
+    }
+    T dr = T(1), di = T(0);
+    if constexpr (CPLX) { dr = a.dinv[2 * row]; di = a.dinv[2 * row + 1]; }
+    else dr = a.dinv[row];
+#pragma unroll
+    for (int k = 0; k < NVPT; ++k) {
+      const int v = it.lane_v + k * TPR;
+      if (v >= a.nvec) continue;
+      const size_t off = (size_t)row * a.ld + v * VEC;
+      T r[VEC], o[VEC];
+      vload(a.r + off, r);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) o[q] = r[q] - acc[k][q];
+      if constexpr (!LOWER) {
+        if constexpr (CPLX) {
+#pragma unroll
+          for (int q = 0; q < VEC; q += 2) {
+            const T yr = dr * o[q] - di * o[q + 1], yi = dr * o[q + 1] + di * o[q];
+            o[q] = yr;
+            o[q + 1] = yi;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) o[q] *= dr;
+        }
+      }
+      vstore(a.out + off, o);
+      if constexpr (LOWER && SCALE_OUT) {
+        T o2[VEC];
+        if constexpr (CPLX) {
+#pragma unroll
+          for (int q = 0; q < VEC; q += 2) {
+            o2[q] = dr * o[q] - di * o[q + 1];
+            o2[q + 1] = dr * o[q + 1] + di * o[q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) o2[q] = dr * o[q];
+        }
+        vstore(a.out2 + off, o2);
+      }
+    }
+  }
+}
+
+template <class T>
+KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi, long nnz_ilu) {
   KrylovWork<T> w;
   const size_t blk = (size_t)n * kMaxRealCols;
   w.n = n;
@@ -628,21 +877,61 @@ KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi) {
   if (jacobi) {
     w.Ph = ar.get<T>(blk); w.Sh = ar.get<T>(blk); w.Dinv = ar.get<T>((size_t)2 * n);
   }
+  if (nnz_ilu >= 0) {
+    w.ilu = true;
+    w.F0 = ar.get<T>((size_t)2 * nnz_ilu);
+    w.F1 = ar.get<T>((size_t)2 * nnz_ilu);
+    w.dpos = ar.get<int>((size_t)n);
+    w.Y1 = ar.get<T>(blk); w.Y2 = ar.get<T>(blk); w.Y3 = ar.get<T>(blk);
+  }
   w.st = ar.get<KState>(kMaxRealCols);
   w.hdr = ar.get<KHeader>(1);
   w.partial = ar.get<double>((size_t)device_sms() * 8 * 2 * kMaxRealCols);
   w.out = ar.get<double>(2 * kMaxRealCols);
   return w;
 }
-template KrylovWork<float> krylov_alloc<float>(Arena&, int, bool);
-template KrylovWork<double> krylov_alloc<double>(Arena&, int, bool);
+template KrylovWork<float> krylov_alloc<float>(Arena&, int, bool, long);
+template KrylovWork<double> krylov_alloc<double>(Arena&, int, bool, long);
 
-template <class T, int TPR, int NVPT, bool CPLX, bool PREC>
+// out = P^{-1} r with P = L U the ILU(0) factor: tri_sweeps Jacobi sweeps on L
+// then on U (see the ILU(0) notes above).
+template <class T, int TPR, int NVPT, bool CPLX>
+static void ilu_apply(const KArgs<T>& a, const T* r, T* out, int grid, cudaStream_t s) {
+  TriArgs<T> t{};
+  t.n = a.n; t.rp = a.rp; t.ci = a.ci; t.dpos = a.dpos; t.F = a.F; t.dinv = a.Dinv; t.ld = a.ld; t.nvec = a.nvec;
+  const int sT = a.tri_sweeps;
+  T* yb[2] = {a.Y1, a.Y2};
+  int yi = 0;
+  const T* yprev = r;
+  for (int q = 1; q <= sT; ++q) {
+    t.r = r; t.xin = yprev; t.out = yb[yi];
+    if (q == sT) {
+      t.out2 = a.Y3;
+      k_trisweep<T, TPR, NVPT, CPLX, true, true><<<grid, kBlock, 0, s>>>(t);
+    } else {
+      k_trisweep<T, TPR, NVPT, CPLX, true, false><<<grid, kBlock, 0, s>>>(t);
+    }
+    CARE_LAUNCH();
+    yprev = yb[yi];
+    yi ^= 1;
+  }
+  // y = yprev (yb[yi ^ 1]); first U iterate x0 = D^{-1} y is in Y3
+  const T* xprev = a.Y3;
+  for (int q = 1; q <= sT; ++q) {
+    T* dst = (q == sT) ? out : (xprev == a.Y3 ? yb[yi] : a.Y3);
+    t.r = yprev; t.xin = xprev; t.out = dst; t.out2 = nullptr;
+    k_trisweep<T, TPR, NVPT, CPLX, false, false><<<grid, kBlock, 0, s>>>(t);
+    CARE_LAUNCH();
+    xprev = dst;
+  }
+}
+
+template <class T, int TPR, int NVPT, bool CPLX, int PREC>
 static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, int grid,
                              cudaStream_t s) {
   KrylovResult res;
   SpmmArgs<T> sp{};
-  sp.n = op.n; sp.rp = op.rp; sp.ci = op.ci; sp.av = op.val; sp.ldx = a.ld; sp.ldy = a.ld;
+  sp.n = op.n; sp.rp = op.rp; sp.ci = op.ci; sp.av = op.val; sp.rs = op.rowsum; sp.ldx = a.ld; sp.ldy = a.ld;
   sp.nvec = a.nvec; sp.sre = sigma.re; sp.sim = sigma.im; sp.dots = a.dots; sp.st = a.st;
   sp.hdr = a.hdr; sp.tol2 = a.tol2;
   k_bicg_init<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
@@ -656,11 +945,13 @@ static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, 
   for (it = 0; it < maxit; ++it) {
     k_bicg_p<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
     CARE_LAUNCH();
+    if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.P, a.Ph, grid, s);
     sp.X = PREC ? a.Ph : a.P; sp.Y = a.V; sp.w0 = a.Rh; sp.w1 = nullptr; sp.mode = FIN_ALPHA;
     k_spmm<T, TPR, NVPT, CPLX, 1><<<grid, kBlock, 0, s>>>(sp);
     CARE_LAUNCH();
     k_bicg_s<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
     CARE_LAUNCH();
+    if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.S, a.Sh, grid, s);
     sp.X = PREC ? a.Sh : a.S; sp.Y = a.Tt; sp.w0 = a.S; sp.w1 = nullptr; sp.mode = FIN_OMEGA;
     k_spmm<T, TPR, NVPT, CPLX, 2><<<grid, kBlock, 0, s>>>(sp);
     CARE_LAUNCH();
@@ -680,14 +971,40 @@ static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, 
   return res;
 }
 
+// ILU(0) of M_p = A^T + sigma I into w.F0 / w.F1; returns the final factor.
+template <class T>
+static const T* ilu_setup(const OpT<T>& op, cd sigma, bool cplx, KrylovWork<T>& w, cudaStream_t s) {
+  const int g = device_sms() * 4;
+  k_diagpos<<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, w.dpos);
+  CARE_LAUNCH();
+  T* Fa = w.F0;
+  T* Fb = w.F1;
+  if (cplx) k_ilu_init<T, true><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, op.val, w.dpos, sigma.re, sigma.im, Fa);
+  else k_ilu_init<T, false><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, op.val, w.dpos, sigma.re, sigma.im, Fa);
+  CARE_LAUNCH();
+  for (int q = 0; q < w.ilu_sweeps; ++q) {
+    if (cplx) k_ilu_sweep<T, true><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, op.val, w.dpos, sigma.re, sigma.im, Fa, Fb);
+    else k_ilu_sweep<T, false><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, op.val, w.dpos, sigma.re, sigma.im, Fa, Fb);
+    CARE_LAUNCH();
+    std::swap(Fa, Fb);
+  }
+  if (cplx) k_ilu_dinv<T, true><<<g, kBlock, 0, s>>>(op.n, w.dpos, Fa, w.Dinv);
+  else k_ilu_dinv<T, false><<<g, kBlock, 0, s>>>(op.n, w.dpos, Fa, w.Dinv);
+  CARE_LAUNCH();
+  return Fa;
+}
+
 template <class T>
 KrylovResult krylov_bicgstab(const OpT<T>& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol,
-                             int ld_sol, int cols, double tol, int maxit, bool jacobi,
+                             int ld_sol, int cols, double tol, int maxit, int precond,
                              KrylovWork<T>& w, cudaStream_t s) {
   constexpr int VEC = 16 / sizeof(T);
   CARE_REQUIRE(cols <= kMaxRealCols && cols > 0, CARE_ERR_INVALID_ARG, "krylov: bad width");
   CARE_REQUIRE(!cplx || cols % 2 == 0, CARE_ERR_INVALID_ARG, "krylov: odd complex width");
-  const bool prec = jacobi && !op.diag_const && w.Ph != nullptr;
+  int pmode = 0;
+  if (precond == CARE_PRECOND_ILU0 && w.ilu && op.full_diag) pmode = 2;
+  else if ((precond == CARE_PRECOND_JACOBI || precond == CARE_PRECOND_ILU0) && !op.diag_const && w.Ph != nullptr)
+    pmode = 1;  // ILU(0) needs every diagonal entry and sparse rows; Jacobi otherwise
   KArgs<T> a{};
   a.n = op.n;
   a.ld = pad_ld<T>(cols);
@@ -698,24 +1015,30 @@ KrylovResult krylov_bicgstab(const OpT<T>& op, cd sigma, bool cplx, const T* rhs
   a.st = w.st; a.hdr = w.hdr;
   a.dots = DotOut{w.partial, w.out, &w.hdr->counter};
   a.tol2 = tol * tol;
+  a.rp = op.rp; a.ci = op.ci; a.dpos = w.dpos; a.Y1 = w.Y1; a.Y2 = w.Y2; a.Y3 = w.Y3;
+  a.tri_sweeps = w.tri_sweeps < 1 ? 1 : w.tri_sweeps;
   const int tpr = tpr_for(a.nvec);
   const int nvpt = (a.nvec + 31) / 32;
   const int grid = grid_rows(op.n, tpr);
   CARE_REQUIRE(grid <= device_sms() * 8, CARE_ERR_INVALID_ARG, "krylov: grid exceeds partial buffer");
   // reduction counter and flags start from zero for every solve
   CARE_CUDA(cudaMemsetAsync(w.hdr, 0, sizeof(KHeader), s));
-  if (prec) {
+  if (pmode == 1) {
     k_dinv<T><<<device_sms() * 4, kBlock, 0, s>>>(op.n, op.diag, sigma.re, sigma.im, cplx, w.Dinv);
     CARE_LAUNCH();
+  } else if (pmode == 2) {
+    a.F = ilu_setup<T>(op, sigma, cplx, w, s);
   }
   KrylovResult r;
-#define CARE_BICG_CASE(TP, NV)                                                               \
-  if (tpr == TP && nvpt == NV) {                                                             \
-    if (cplx) r = prec ? run_bicg<T, TP, NV, true, true>(op, sigma, a, maxit, grid, s)       \
-                       : run_bicg<T, TP, NV, true, false>(op, sigma, a, maxit, grid, s);     \
-    else r = prec ? run_bicg<T, TP, NV, false, true>(op, sigma, a, maxit, grid, s)           \
-                  : run_bicg<T, TP, NV, false, false>(op, sigma, a, maxit, grid, s);         \
-    goto done;                                                                               \
+#define CARE_BICG_CASE(TP, NV)                                                                        \
+  if (tpr == TP && nvpt == NV) {                                                                      \
+    if (cplx) r = pmode == 2 ? run_bicg<T, TP, NV, true, 2>(op, sigma, a, maxit, grid, s)             \
+                 : pmode == 1 ? run_bicg<T, TP, NV, true, 1>(op, sigma, a, maxit, grid, s)            \
+                              : run_bicg<T, TP, NV, true, 0>(op, sigma, a, maxit, grid, s);           \
+    else r = pmode == 2 ? run_bicg<T, TP, NV, false, 2>(op, sigma, a, maxit, grid, s)                 \
+            : pmode == 1 ? run_bicg<T, TP, NV, false, 1>(op, sigma, a, maxit, grid, s)                \
+                         : run_bicg<T, TP, NV, false, 0>(op, sigma, a, maxit, grid, s);               \
+    goto done;                                                                                        \
   }
   CARE_BICG_CASE(1, 1) CARE_BICG_CASE(2, 1) CARE_BICG_CASE(4, 1) CARE_BICG_CASE(8, 1)
   CARE_BICG_CASE(16, 1) CARE_BICG_CASE(32, 1) CARE_BICG_CASE(32, 2)
@@ -736,9 +1059,9 @@ done:
   return r;
 }
 template KrylovResult krylov_bicgstab<float>(const OpT<float>&, cd, bool, const float*, int, float*, int,
-                                             int, double, int, bool, KrylovWork<float>&, cudaStream_t);
+                                             int, double, int, int, KrylovWork<float>&, cudaStream_t);
 template KrylovResult krylov_bicgstab<double>(const OpT<double>&, cd, bool, const double*, int, double*,
-                                              int, int, double, int, bool, KrylovWork<double>&,
+                                              int, int, double, int, int, KrylovWork<double>&,
                                               cudaStream_t);
 
 }  // namespace care

@@ -13,7 +13,9 @@ struct OpT {
   const int* ci = nullptr;
   const T* val = nullptr;
   const T* diag = nullptr;
+  const T* rowsum = nullptr;  // set: apply in the difference form (FP32 operator)
   bool diag_const = true;
+  bool full_diag = false;
 };
 OpT<double> op64(const care_op& op);
 OpT<float> op32(const care_op& op);
@@ -37,14 +39,22 @@ template <class T>
 struct KrylovWork {
   T *X = nullptr, *R = nullptr, *Rh = nullptr, *P = nullptr, *V = nullptr, *S = nullptr, *Tt = nullptr;
   T *Ph = nullptr, *Sh = nullptr, *Dinv = nullptr;
+  // ILU(0) factors (ping-pong for the fixed-point sweeps), diagonal positions,
+  // and the temporaries of the triangular Jacobi sweeps
+  bool ilu = false;
+  T *F0 = nullptr, *F1 = nullptr, *Y1 = nullptr, *Y2 = nullptr, *Y3 = nullptr;
+  int* dpos = nullptr;
+  int ilu_sweeps = 3, tri_sweeps = 2;
   KState* st = nullptr;
   KHeader* hdr = nullptr;
   double* partial = nullptr;
   double* out = nullptr;
   int n = 0;
 };
+// nnz_ilu >= 0 also allocates the ILU(0) preconditioner for an operator with
+// that many entries (jacobi must then be true: the factor uses Ph / Sh / Dinv).
 template <class T>
-KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi);
+KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi, long nnz_ilu = -1);
 
 struct KrylovResult {
   int iters = 0;
@@ -52,12 +62,13 @@ struct KrylovResult {
   long long spmm = 0;
 };
 
+// Preconditioner of a solve: 0 none, 1 Jacobi, 2 ILU(0).
 // Solves (A^T + sigma I) X = RHS for `cols` real columns (complex interleaved
 // columns when cplx: cols = 2 * complex columns), cols <= kMaxRealCols.
 // rhs/sol are row-major with leading dimensions ld_rhs / ld_sol (reals).
 template <class T>
 KrylovResult krylov_bicgstab(const OpT<T>& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol,
-                             int ld_sol, int cols, double tol, int maxit, bool jacobi,
+                             int ld_sol, int cols, double tol, int maxit, int precond,
                              KrylovWork<T>& w, cudaStream_t s);
 
 // Y = (A^T + sigma I) X on `cols` real columns (any width; complex when cplx).

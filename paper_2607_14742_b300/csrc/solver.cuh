@@ -15,6 +15,7 @@ struct Ctx {
   care_opts o{};
   Arena ar;
   care_op op{};
+  long op_nnz = 0;  // entries of A (sizes the ILU(0) factors before the operator exists)
   double* dS = nullptr;  // staging for small matrices (device)
   size_t dS_cap = 0;
   double* dG = nullptr;  // Gram results (device)
@@ -81,8 +82,11 @@ struct AdiResult {
 // knew, accumulates K_new += Z_blk (Z_blk^T B) into in.Knew (requires rp = b).
 // When the factor reaches its capacity it is column-compressed; if that does
 // not free enough room the solve stops early (inexact inner solve).
+// compress_end: column-compress both factor groups at the end (inner-precision
+// truncation) before they are handed to Algorithm 2.
 template <class T>
-AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew);
+AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew,
+                bool compress_end = false);
 
 struct NlrResult {
   int newton = 0, adi = 0, cols = 0;

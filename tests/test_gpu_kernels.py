@@ -49,8 +49,10 @@ def test_spmm_parity(pb, N, b, dtype, shift):
     else:
         Xt = torch.tensor(X, dtype=tdt, device="cuda")
     Y = pb.spmm(op, Xt, shift).cpu().numpy().astype(np.complex128 if cplx else np.float64)
-    # rounding bound: |A^T| |X| + |p| |X| with gamma_{k} of the precision (k <= 6 terms)
-    bound = np.abs(As.T) @ np.abs(X) + abs(shift) * np.abs(X)
+    # rounding bound: |A^T| |X| + |p| |X| with gamma_{k} of the precision (k <= 6 terms); the FP32
+    # operator is applied as sum_j a_ij (x_j - x_i) + (s_i + p) x_i, which adds (sum_j |a_ij|) |x_i|
+    rowabs = np.asarray(abs(As.T).sum(axis=1)).ravel()[:, None]
+    bound = np.abs(As.T) @ np.abs(X) + abs(shift) * np.abs(X) + rowabs * np.abs(X)
     u = U64 if dtype == "f64" else U32
     # FP32 path also rounds A and X to FP32 (two more roundings per term)
     k = 8 if dtype == "f64" else 12
@@ -65,7 +67,8 @@ def test_spmm_large_ragged(pb):
     Y = pb.spmm(op, torch.tensor(X, dtype=torch.float32, device="cuda"), -1000.0).cpu().numpy()
     rows = np.random.default_rng(0).choice(prob.n, 2000, replace=False)
     ref = (As.T[rows] @ X) - 1000.0 * X[rows]
-    bound = np.abs(As.T[rows]) @ np.abs(X) + 1000.0 * np.abs(X[rows])
+    rowabs = np.asarray(abs(As.T[rows]).sum(axis=1)).ravel()[:, None]
+    bound = np.abs(As.T[rows]) @ np.abs(X) + 1000.0 * np.abs(X[rows]) + rowabs * np.abs(X[rows])
     assert np.all(np.abs(Y[rows] - ref) <= 12 * U32 * bound)
 
 
@@ -107,3 +110,33 @@ def test_shifted_solve_parity(pb, prec, tol, shift, feedback):
     V = V.cpu().numpy()
     assert iters > 0
     assert np.linalg.norm(V - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("shift", [-150.0, -2000.0, complex(-1500.0, 2500.0)])
+def test_ilu0_preconditioner_parity_and_gain(pb, shift):
+    """ILU(0) (fixed-point factorisation, Jacobi triangular sweeps) gives the same solution
+    as the unpreconditioned solve and needs fewer iterations on the 100x100 operator."""
+    prob = ci.config_fdm2d(100, 2, 2)
+    dA, op, As = _ops(pb, prob)
+    W = ci.random_block(prob.n, 4, 53)
+    ref = ol.smw_solve(ol.ShiftedSolver(As), None, None, shift, W)
+    its = {}
+    for name, pc in (("none", pb.PRECOND_NONE), ("ilu0", pb.PRECOND_ILU0)):
+        o = pb.default_options(precond=pc, krylov_maxit_hi=2000)
+        V, it = pb.shifted_solve(op, W, shift, prec="fp64", opts=o)
+        V = V.cpu().numpy()
+        its[name] = it
+        assert np.linalg.norm(V - ref) <= 1e-8 * np.linalg.norm(ref), name
+    assert its["ilu0"] < 0.6 * its["none"], its
+
+
+def test_spmm_fp32_difference_form_smooth_accuracy(pb):
+    """On a smooth block the FP32 operator keeps FP32 relative accuracy in A^T x (the
+    difference form avoids the ~400x cancellation of the 1/h^2 stencil)."""
+    prob = ci.config_fdm2d(500, 1, 1)
+    dA, op, As = _ops(pb, prob)
+    v, lam = ci.laplacian_mode(500, 2, (1, 1))
+    X = np.stack([v, 2 * v], 1)
+    Y = pb.spmm(op, torch.tensor(X, dtype=torch.float32, device="cuda"), 0.0).cpu().numpy().astype(np.float64)
+    ref = As.T @ X.astype(np.float32).astype(np.float64)
+    assert np.linalg.norm(Y - ref) <= 50 * U32 * np.linalg.norm(ref)
