@@ -294,6 +294,7 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
   // K = Z Z^T B -> coefficients T_Z T_Z^T (Q_Z^T B) in the Q_Z rows
   {
     std::vector<double> TT((size_t)rq * rq, 0.0);
+#pragma omp parallel for if ((long)rq * rq * r > 1000000) schedule(dynamic, 4)
     for (int i = 0; i < rq; ++i)
       for (int k = 0; k < rq; ++k) {
         double s = 0.0;
@@ -309,6 +310,7 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
   }
   // H = tZ tA^T + tA tZ^T - tK tK^T + tC tC^T   (= T M T^T)
   std::vector<double> H((size_t)rt * rt, 0.0);
+#pragma omp parallel for if ((long)rt * rt * (2 * r + m + p) > 1000000) schedule(dynamic, 4)
   for (int i = 0; i < rt; ++i)
     for (int k = i; k < rt; ++k) {
       double s = 0.0;
@@ -389,10 +391,13 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
     for (int j = 0; j < ny; ++j) Gam[(size_t)(r + i) * sc + r + j] = O.T[(size_t)i * ny + j];
   for (int j = 0; j < sc; ++j) Nd[j] = j < r ? 1.0 : sign[j - r];
   std::vector<double> Pm((size_t)rt * rt, 0.0);
+#pragma omp parallel for if ((long)rt * rt * sc > 1000000) schedule(dynamic, 4)
   for (int i = 0; i < rt; ++i)
     for (int k = i; k < rt; ++k) {
       double s = 0.0;
-      for (int j = 0; j < sc; ++j) s += Gam[(size_t)i * sc + j] * Nd[j] * Gam[(size_t)k * sc + j];
+      const double* gi = &Gam[(size_t)i * sc];
+      const double* gk = &Gam[(size_t)k * sc];
+      for (int j = 0; j < sc; ++j) s += gi[j] * Nd[j] * gk[j];
       Pm[(size_t)k * rt + i] = s;
       Pm[(size_t)i * rt + k] = s;
     }

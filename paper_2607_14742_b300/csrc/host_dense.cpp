@@ -40,20 +40,23 @@ inline void givens(double x, double z, double& c, double& s) {
 
 bool host_symeig(int n, const double* A, double* w, double* V) {
   if (n <= 0) return true;
+  // a: working copy (column-major == row-major for the symmetric matrix)
   std::vector<double> a(A, A + (size_t)n * n);
-  // symmetrise (callers pass numerically symmetric matrices)
   for (int j = 0; j < n; ++j)
     for (int i = j + 1; i < n; ++i) {
       const double s = 0.5 * (at(a, n, i, j) + at(a, n, j, i));
       at(a, n, i, j) = s;
       at(a, n, j, i) = s;
     }
-  std::vector<double> Q;
   const bool vec = V != nullptr;
+  // Q is kept row-major (Q[r * n + k]) so that a plane rotation of columns
+  // (k, k+1) touches contiguous memory in every row and rows are independent
+  std::vector<double> Q;
   if (vec) {
     Q.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
   }
+  const bool par = n >= 96;
   // 1. Householder tridiagonalisation: A <- H_k A H_k, Q <- Q H_k
   std::vector<double> v(n), p(n), wv(n);
   for (int k = 0; k + 2 < n; ++k) {
@@ -69,20 +72,19 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
     for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
     if (vn2 == 0.0) continue;
     const double beta = 2.0 / vn2;
-    // p = beta * A22 v
-    for (int i = 0; i < m; ++i) p[i] = 0.0;
-    for (int j = 0; j < m; ++j) {
-      const double vj = v[j];
-      const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
-      for (int i = 0; i < m; ++i) p[i] += col[i] * vj;
+    // p = beta * A22 v  (A22 symmetric: p_i = beta * sum_j a(k+1+j, k+1+i) v_j, column i contiguous)
+#pragma omp parallel for if (par) schedule(static)
+    for (int i = 0; i < m; ++i) {
+      const double* col = &a[(size_t)(k + 1 + i) * n + k + 1];
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j) acc += col[j] * v[j];
+      p[i] = beta * acc;
     }
     double pv = 0.0;
-    for (int i = 0; i < m; ++i) {
-      p[i] *= beta;
-      pv += p[i] * v[i];
-    }
+    for (int i = 0; i < m; ++i) pv += p[i] * v[i];
     const double K = 0.5 * beta * pv;
     for (int i = 0; i < m; ++i) wv[i] = p[i] - K * v[i];
+#pragma omp parallel for if (par) schedule(static)
     for (int j = 0; j < m; ++j) {
       double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
       const double vj = v[j], wj = wv[j];
@@ -95,35 +97,37 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
       at(a, n, k, i) = 0.0;
     }
     if (vec) {
-      // Q[:, k+1:] -= beta (Q[:, k+1:] v) v^T
+      // Q[:, k+1:] -= beta (Q[:, k+1:] v) v^T, row by row
+#pragma omp parallel for if (par) schedule(static)
       for (int r = 0; r < n; ++r) {
+        double* qr = &Q[(size_t)r * n + k + 1];
         double s = 0.0;
-        for (int i = 0; i < m; ++i) s += Q[(size_t)(k + 1 + i) * n + r] * v[i];
+        for (int i = 0; i < m; ++i) s += qr[i] * v[i];
         s *= beta;
-        for (int i = 0; i < m; ++i) Q[(size_t)(k + 1 + i) * n + r] -= s * v[i];
+        for (int i = 0; i < m; ++i) qr[i] -= s * v[i];
       }
     }
   }
   std::vector<double> d(n), e(n, 0.0);
   for (int i = 0; i < n; ++i) d[i] = at(a, n, i, i);
   for (int i = 0; i + 1 < n; ++i) e[i] = at(a, n, i + 1, i);
-  // 2. implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e)
+  // 2. implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
+  //    the rotations of one sweep are recorded and then applied to all rows
+  //    of Q in parallel
   const double eps = 2.220446049250313e-16;
+  std::vector<double> rc(n), rs(n);
   int u = n - 1;
-  int iters = 0;
+  long iters = 0;
   while (u > 0) {
-    // deflate negligible off-diagonals at the bottom
     if (std::fabs(e[u - 1]) <= eps * (std::fabs(d[u - 1]) + std::fabs(d[u]))) {
       e[u - 1] = 0.0;
       --u;
-      iters = 0;
       continue;
     }
     int l = u - 1;
     while (l > 0 && std::fabs(e[l - 1]) > eps * (std::fabs(d[l - 1]) + std::fabs(d[l]))) --l;
     if (l > 0) e[l - 1] = 0.0;
-    if (++iters > 60 * n) return false;
-    // Wilkinson shift from the trailing 2 x 2 block
+    if (++iters > 60L * n) return false;
     const double dd = 0.5 * (d[u - 1] - d[u]);
     const double eu = e[u - 1];
     const double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::hypot(dd, eu);
@@ -133,7 +137,8 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
     for (int k = l; k < u; ++k) {
       double c, s;
       givens(x, z, c, s);
-      // rotate rows/cols k, k+1 of T (symmetric tridiagonal + bulge)
+      rc[k] = c;
+      rs[k] = s;
       if (k > l) e[k - 1] = c * e[k - 1] - s * bulge;
       const double dk = d[k], dk1 = d[k + 1], ek = e[k];
       d[k] = c * c * dk - 2.0 * c * s * ek + s * s * dk1;
@@ -145,14 +150,20 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
         x = e[k];
         z = bulge;
       }
-      if (vec) {
-        double* qk = &Q[(size_t)k * n];
-        double* qk1 = &Q[(size_t)(k + 1) * n];
-        for (int r = 0; r < n; ++r) {
-          const double t1 = qk[r], t2 = qk1[r];
-          qk[r] = c * t1 - s * t2;
-          qk1[r] = s * t1 + c * t2;
+    }
+    if (vec) {
+      const bool par2 = par && (u - l) >= 16;
+#pragma omp parallel for if (par2) schedule(static)
+      for (int r = 0; r < n; ++r) {
+        double* qr = &Q[(size_t)r * n];
+        double t1 = qr[l];
+        for (int k = l; k < u; ++k) {
+          const double c = rc[k], s = rs[k];
+          const double t2 = qr[k + 1];
+          qr[k] = c * t1 - s * t2;
+          t1 = s * t1 + c * t2;
         }
+        qr[u] = t1;
       }
     }
   }
@@ -160,10 +171,11 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int x1, int x2) { return d[x1] < d[x2]; });
-  for (int i = 0; i < n; ++i) {
-    w[i] = d[idx[i]];
-    if (vec)
-      for (int r = 0; r < n; ++r) V[(size_t)i * n + r] = Q[(size_t)idx[i] * n + r];
+  for (int i = 0; i < n; ++i) w[i] = d[idx[i]];
+  if (vec) {
+#pragma omp parallel for if (par) schedule(static)
+    for (int i = 0; i < n; ++i)
+      for (int r = 0; r < n; ++r) V[(size_t)i * n + r] = Q[(size_t)r * n + idx[i]];
   }
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(w[i])) return false;

@@ -94,10 +94,12 @@ static int pivoted_cholesky(int c, const std::vector<double>& G, double tol, int
     double* rk = &R[(size_t)r * c];
     const double rkk = std::sqrt(d[jp]);
     rk[jp] = rkk;
+    const double* Rd = R.data();
+#pragma omp parallel for if ((long)c * r > 200000) schedule(static)
     for (int i = 0; i < c; ++i) {
       if (used[i]) continue;
       double s = G[(size_t)jp * c + i];
-      for (int l = 0; l < r; ++l) s -= R[(size_t)l * c + jp] * R[(size_t)l * c + i];
+      for (int l = 0; l < r; ++l) s -= Rd[(size_t)l * c + jp] * Rd[(size_t)l * c + i];
       rk[i] = s / rkk;
       d[i] -= rk[i] * rk[i];
     }
@@ -194,10 +196,13 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   gemm_ts<T, T>(n, r1, r1, 1.0, buf, ldb, upload(c, Rinv), r1, 0.0, X, ldx, c.s);
   o.rank = r1;
   o.T.assign((size_t)r1 * cols, 0.0);
+#pragma omp parallel for if ((long)r1 * r1 * cols > 1000000) schedule(dynamic, 4)
   for (int i = 0; i < r1; ++i)
     for (int k = i; k < r1; ++k) {
       const double rik = R[(size_t)k * r1 + i];
-      for (int j = 0; j < cols; ++j) o.T[(size_t)i * cols + j] += rik * T1[(size_t)k * cols + j];
+      double* oi = &o.T[(size_t)i * cols];
+      const double* tk = &T1[(size_t)k * cols];
+      for (int j = 0; j < cols; ++j) oi[j] += rik * tk[j];
     }
   return o;
 }
@@ -433,11 +438,15 @@ static int compress_part(Ctx& c, Inner<T>& in, int col0, int ncols, bool right_a
   const int q = o.rank;
   if (q == 0) return 0;
   std::vector<double> TT((size_t)q * q, 0.0), R((size_t)q * q);
+#pragma omp parallel for if ((long)q * q * ncols > 1000000) schedule(dynamic, 4)
   for (int i = 0; i < q; ++i)
-    for (int k = 0; k < q; ++k) {
+    for (int k = 0; k <= i; ++k) {
       double acc = 0.0;
-      for (int j = 0; j < ncols; ++j) acc += o.T[(size_t)i * ncols + j] * o.T[(size_t)k * ncols + j];
+      const double* ti = &o.T[(size_t)i * ncols];
+      const double* tk = &o.T[(size_t)k * ncols];
+      for (int j = 0; j < ncols; ++j) acc += ti[j] * tk[j];
       TT[(size_t)i * q + k] = acc;
+      TT[(size_t)k * q + i] = acc;
     }
   CARE_REQUIRE(host_cholesky_upper(q, TT.data(), R.data()), CARE_ERR_SMALL_DENSE, "compression Cholesky");
   // column-major upper R == row-major R^T = L

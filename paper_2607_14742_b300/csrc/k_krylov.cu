@@ -251,7 +251,31 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
       }
       if (v < a.nvec && diff) vload(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
     }
-    for (int j = s; j < e; ++j) {
+    // four independent gathers in flight per thread (stencil rows have 5-7 entries)
+    int j = s;
+    for (; j + 3 < e; j += 4) {
+      int c[4];
+      T av[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __ldg(a.ci + j + u);
+        av[u] = __ldg(a.av + j + u);
+      }
+#pragma unroll
+      for (int k = 0; k < NVPT; ++k) {
+        const int v = it.lane_v + k * TPR;
+        if (v < a.nvec) {
+          T x[4][VEC];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) vload(a.X + (size_t)c[u] * a.ldx + v * VEC, x[u]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) y[k][q] = fma(av[u], x[u][q] - xi[k][q], y[k][q]);
+        }
+      }
+    }
+    for (; j < e; ++j) {
       const int c = __ldg(a.ci + j);
       const T av = __ldg(a.av + j);
       const T* xr = a.X + (size_t)c * a.ldx;
