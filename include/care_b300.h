@@ -185,6 +185,30 @@ size_t care_gram_work_size(int n, int a, int b);
 care_status care_gram(int dtype, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy,
                       double* G, int ldg, void* work, size_t work_bytes, care_stream_t s);
 
+/* Allocation-free variant of care_gram, for callers that cannot allocate device
+ * memory at call time: for example a control loop with hard deadlines that
+ * reserved all of its memory at start-up, or a plug-in whose host framework's
+ * allocator owns the device memory.  The paper has no counterpart to this
+ * entry point.  It computes the same G = X^T Y (same layouts, same precision
+ * rules) without a workspace argument: its split-K scratch is a fixed
+ * file-scope device array of CARE_GRAM_NOALLOC_SCRATCH_DOUBLES doubles (8 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - a * b must not exceed CARE_GRAM_NOALLOC_SCRATCH_DOUBLES, else
+ *    CARE_ERR_INVALID_ARG; long row ranges are handled with fewer, longer
+ *    row slices, so results may differ from care_gram in the last bits.
+ *  - The first call on a device looks up the scratch's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one scratch array and it keeps the last call's
+ *    contents; every entry a call reads is written by that call first.  Calls
+ *    that overlap on the GPU (different streams, or different host threads
+ *    without ordering) race on the scratch and give wrong results.
+ *  - Asynchronous on s. */
+#define CARE_GRAM_NOALLOC_SCRATCH_DOUBLES 1048576
+care_status care_gram_noalloc(int dtype, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy,
+                              double* G, int ldg, care_stream_t s);
+
 /* Shifted block solve with feedback (Section 4, SMW formula):
  *   V = ((A - B K^T)^T + p I)^{-1} W,  i.e.  (A_k + p I)^{-T} W,  A_k = A - B K^T,
  * for an n x b block W; B, K FP64 column-major n x m (K may be NULL: no

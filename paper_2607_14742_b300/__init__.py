@@ -93,6 +93,7 @@ def lib() -> ct.CDLL:
         "care_spmm": (i, [P(op_t), i, i, d, d, vp, i, i, vp, i, vp]),
         "care_gram_work_size": (sz, [i, i, i]),
         "care_gram": (i, [i, i, i, i, vp, i, vp, i, vp, i, vp, sz, vp]),
+        "care_gram_noalloc": (i, [i, i, i, i, vp, i, vp, i, vp, i, vp]),
         "care_shifted_solve_workspace_size": (i, [P(op_t), i, i, i, P(opts_t), P(sz)]),
         "care_shifted_solve": (i, [P(op_t), vp, i, vp, i, i, d, d, vp, i, i, i, P(opts_t), vp, i, vp, sz, vp,
                                    P(i)]),
@@ -350,6 +351,21 @@ def gram(X: torch.Tensor, Y: torch.Tensor):
     ws = torch.empty(max(lib().care_gram_work_size(n, a, b), 8), dtype=torch.uint8, device=X.device)
     _check(lib().care_gram(0 if X.dtype == torch.float64 else 1, n, a, b, _ptr(X), X.stride(0), _ptr(Y),
                            Y.stride(0), _ptr(G), b, _ptr(ws), ws.numel(), _stream()), "care_gram")
+    return G
+
+
+GRAM_NOALLOC_SCRATCH_DOUBLES = 1048576
+
+
+def gram_noalloc(X: torch.Tensor, Y: torch.Tensor, out: torch.Tensor | None = None):
+    """G = X^T Y through the allocation-free entry point (no workspace; the library's
+    fixed device scratch).  `out` (float64 a x b) may be preallocated by the caller."""
+    assert X.dtype == Y.dtype and X.shape[0] == Y.shape[0]
+    n, a = X.shape
+    b = Y.shape[1]
+    G = out if out is not None else torch.empty(a, b, dtype=torch.float64, device=X.device)
+    _check(lib().care_gram_noalloc(0 if X.dtype == torch.float64 else 1, n, a, b, _ptr(X), X.stride(0), _ptr(Y),
+                                   Y.stride(0), _ptr(G), G.stride(0), _stream()), "care_gram_noalloc")
     return G
 
 

@@ -817,6 +817,18 @@ care_status care_gram(int dtype, int n, int a, int b, const void* X, int ldx, co
   });
 }
 
+care_status care_gram_noalloc(int dtype, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy,
+                              double* G, int ldg, care_stream_t s) {
+  if (n < 0 || a < 0 || b < 0 || (dtype != 0 && dtype != 1) || ldx < a || ldy < b || ldg < b) return CARE_ERR_INVALID_ARG;
+  if ((long)a * b > CARE_GRAM_NOALLOC_SCRATCH_DOUBLES) return CARE_ERR_INVALID_ARG;
+  if (a > 0 && b > 0 && (!G || (n > 0 && (!X || !Y)))) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    if (dtype == 0) gram_noalloc<double>(n, a, b, (const double*)X, ldx, (const double*)Y, ldy, G, ldg, (cudaStream_t)s);
+    else gram_noalloc<float>(n, a, b, (const float*)X, ldx, (const float*)Y, ldy, G, ldg, (cudaStream_t)s);
+    return CARE_OK;
+  });
+}
+
 care_status care_shifted_solve_workspace_size(const care_op* op, int m, int b, care_prec prec, const care_opts* opts,
                                               size_t* bytes) {
   if (!op || !bytes || m < 0 || b <= 0) return CARE_ERR_INVALID_ARG;

@@ -12,6 +12,12 @@ template <class T>
 void gram(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double* G, int ldg,
           double* work, size_t work_elems, cudaStream_t s);
 
+// Same product with the split-K scratch in a fixed file-scope device array
+// (no allocation, no workspace argument); a * b <= CARE_GRAM_NOALLOC_SCRATCH_DOUBLES.
+template <class T>
+void gram_noalloc(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double* G, int ldg,
+                  cudaStream_t s);
+
 // Y (n x b, row-major To, ldy) = alpha X S + beta Y,  X row-major Ti (n x a, ldx),
 // S device FP64 row-major (a x b, lds).
 template <class Ti, class To>

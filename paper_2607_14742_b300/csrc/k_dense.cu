@@ -311,4 +311,63 @@ void scale_cols(long n, int cols, T* Y, int ldy, const double* d, cudaStream_t s
 template void scale_cols<float>(long, int, float*, int, const double*, cudaStream_t);
 template void scale_cols<double>(long, int, double*, int, const double*, cudaStream_t);
 
+// ------------------------------------------------- allocation-free Gram ----
+// Scratch for care_gram_noalloc: a fixed file-scope device array, so the entry
+// point never allocates.  Every device that loads the library holds it until
+// the process exits.  Host code must not pass the symbol itself to a kernel
+// (in host code it names a host-side stand-in); its device address is looked
+// up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_gram_noalloc_scratch[CARE_GRAM_NOALLOC_SCRATCH_DOUBLES];
+
+}  // namespace care
+
+#include <mutex>
+
+namespace care {
+
+static double* gram_noalloc_scratch_ptr(int dev) {
+  static std::mutex mu;
+  static double* ptrs[64] = {nullptr};
+  CARE_REQUIRE(dev >= 0 && dev < 64, CARE_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    CARE_CUDA(cudaGetSymbolAddress(&p, g_gram_noalloc_scratch));
+    ptrs[dev] = static_cast<double*>(p);
+  }
+  return ptrs[dev];
+}
+
+template <class T>
+void gram_noalloc(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double* G, int ldg,
+                  cudaStream_t s) {
+  if (a == 0 || b == 0) return;
+  const long cap = CARE_GRAM_NOALLOC_SCRATCH_DOUBLES;
+  CARE_REQUIRE((long)a * b <= cap, CARE_ERR_INVALID_ARG,
+               "gram_noalloc: a*b exceeds the fixed scratch (CARE_GRAM_NOALLOC_SCRATCH_DOUBLES)");
+  int dev = 0;
+  CARE_CUDA(cudaGetDevice(&dev));
+  double* work = gram_noalloc_scratch_ptr(dev);
+  const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
+  long split = gram_split(n, a, b);
+  if (split * a * b > cap) split = cap / ((long)a * b);  // fewer, longer row slices
+  if (split < 1) split = 1;
+  const long rows_per = ((n + split - 1) / split + GK - 1) / GK * GK;
+  if (n == 0) {
+    CARE_CUDA(cudaMemsetAsync(work, 0, (size_t)a * b * sizeof(double), s));
+  } else {
+    dim3 grid((unsigned)split, ta, tb);
+    k_gram<T><<<grid, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, rows_per, work);
+    CARE_LAUNCH();
+  }
+  const long tot = (long)a * b;
+  int g = (int)((tot + 7) / 8);
+  if (g > device_sms() * 8) g = device_sms() * 8;
+  k_gram_reduce<<<g, 256, 0, s>>>(a, b, n == 0 ? 1 : split, work, G, ldg);
+  CARE_LAUNCH();
+}
+template void gram_noalloc<float>(long, int, int, const float*, int, const float*, int, double*, int, cudaStream_t);
+template void gram_noalloc<double>(long, int, int, const double*, int, const double*, int, double*, int,
+                                   cudaStream_t);
+
 }  // namespace care
