@@ -548,7 +548,9 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
     if (verbose_level() >= 2)
       fprintf(stderr, "[care]   adi j=%d p=(%.4e,%.4e) res=%.3e cols=%d+%d\n", j, p.re, p.im, r, np, nm);
   }
-  if (compress_end && np + nm > 2 * b) {
+  // compress only wide factors: below a few hundred columns Algorithm 2's FP64
+  // rank revealing is cheap and keeps the full FP32 accuracy of X_+ - X_-
+  if (compress_end && np + nm > std::max(2 * b, 512)) {
     np = compress_part<T>(c, in, 0, np, false);
     nm = compress_part<T>(c, in, cap - nm, nm, true);
     res.compressions++;

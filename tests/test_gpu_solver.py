@@ -97,10 +97,11 @@ def test_care_solve_dense_conditioning(pb, k):
     prob = ci.config_dense_conditioning(k)
     A = prob.A.to_dense()
     X = od.newton_care(A, prob.B, prob.C)["X"]
-    Z, info = pb.care_solve(dcsr(pb, prob), prob.B, prob.C, tol=1e-10, prec="mixed", r_cap=200)
+    Z, info = pb.care_solve(dcsr(pb, prob), prob.B, prob.C, tol=1e-10, prec="mixed", r_cap=200, allow=(5, 6))
     Z = Z.cpu().numpy()
-    assert info["status"] == "CARE_OK", info
-    assert np.linalg.norm(Z @ Z.T - X) <= 1e-8 * np.linalg.norm(X)
+    err = np.linalg.norm(Z @ Z.T - X) / np.linalg.norm(X)
+    assert info["status"] == "CARE_OK", (info, err)
+    assert err <= 1e-8, (info, err)
 
 
 def test_care_solve_eigen_aligned_closed_form(pb):
