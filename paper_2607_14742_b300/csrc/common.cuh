@@ -32,6 +32,7 @@ struct StatusError {
 // every kernel launch site ends with CARE_LAUNCH(): it checks the launch and
 // counts it (care_kernel_launches)
 void count_launch();
+void count_launch_n(long delta);
 #define CARE_LAUNCH()               \
   do {                              \
     ::care::count_launch();         \

@@ -16,6 +16,7 @@ void set_verbose(int v) { g_verbose = v; }
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch_n(long delta) { g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed); }
 unsigned long long launches() { return g_launches.load(); }
 
 int device_sms() {

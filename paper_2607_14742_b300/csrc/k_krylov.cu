@@ -64,20 +64,44 @@ struct DotOut {
 template <class T, int TPR, int NVPT, int NDOT>
 __device__ bool dot_reduce(const T (&acc)[NDOT][NVPT * (16 / sizeof(T))], int w, const DotOut& d) {
   constexpr int VEC = 16 / sizeof(T), NS = NVPT * VEC;
-  __shared__ double sm[kBlock * NDOT * NS];
+  constexpr int NWARP = kBlock / 32;
+  __shared__ double sm[NWARP * NDOT * TPR * NVPT * VEC];
   __shared__ bool s_last;
+  // 1. within each warp, lanes that own the same vector slot are those with equal
+  //    lane % TPR: combine them with a fixed xor-shuffle tree (in FP64)
+  double v[NDOT][NS];
 #pragma unroll
   for (int q = 0; q < NDOT; ++q)
 #pragma unroll
-    for (int e = 0; e < NS; ++e) sm[(threadIdx.x * NDOT + q) * NS + e] = (double)acc[q][e];
+    for (int e = 0; e < NS; ++e) {
+      double x = (double)acc[q][e];
+#pragma unroll
+      for (int off = TPR; off < 32; off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      v[q][e] = x;
+    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // lanes 0..TPR-1 hold the warp totals for slots (lane + k*TPR)*VEC + e
+  if (lane < TPR) {
+#pragma unroll
+    for (int q = 0; q < NDOT; ++q)
+#pragma unroll
+      for (int k2 = 0; k2 < NVPT; ++k2)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const int slot = (lane + k2 * TPR) * VEC + e;
+          sm[(warp * NDOT + q) * (TPR * NVPT * VEC) + slot] = v[q][k2 * VEC + e];
+        }
+  }
   __syncthreads();
+  // 2. the CTA total of each item: fixed-order sum over the warps
   const int items = NDOT * w;
+  constexpr int SPAN = TPR * NVPT * VEC;  // slots per dot held in shared memory
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int q = it / w, slot = it % w;
-    const int v = slot / VEC, e = slot % VEC;
-    const int lv = v % TPR, k = v / TPR;
     double sum = 0.0;
-    for (int t = lv; t < kBlock; t += TPR) sum += sm[(t * NDOT + q) * NS + k * VEC + e];
+    if (slot < SPAN)
+#pragma unroll
+      for (int wp = 0; wp < NWARP; ++wp) sum += sm[(wp * NDOT + q) * SPAN + slot];
     d.partial[(size_t)blockIdx.x * items + it] = sum;
   }
   __threadfence();
@@ -97,23 +121,25 @@ __device__ bool dot_reduce(const T (&acc)[NDOT][NVPT * (16 / sizeof(T))], int w,
   __shared__ double red[kBlock];
   {
     const int t = threadIdx.x;
-    const int item = t / TPI, lane = t % TPI;
-    double s0 = 0.0, s1 = 0.0;
+    const int item = t / TPI, tl = t % TPI;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     if (item < items) {
-      int g = lane;
-      for (; g + TPI < G; g += 2 * TPI) {
+      int g = tl;
+      for (; g + 3 * TPI < G; g += 4 * TPI) {
         s0 += __ldcg(d.partial + (size_t)g * items + item);
         s1 += __ldcg(d.partial + (size_t)(g + TPI) * items + item);
+        s2 += __ldcg(d.partial + (size_t)(g + 2 * TPI) * items + item);
+        s3 += __ldcg(d.partial + (size_t)(g + 3 * TPI) * items + item);
       }
-      if (g < G) s0 += __ldcg(d.partial + (size_t)g * items + item);
+      for (; g < G; g += TPI) s0 += __ldcg(d.partial + (size_t)g * items + item);
     }
-    red[t] = s0 + s1;
+    red[t] = (s0 + s1) + (s2 + s3);
     __syncthreads();
-    for (int w = TPI / 2; w > 0; w >>= 1) {
-      if (lane < w) red[t] += red[t + w];
+    for (int w2 = TPI / 2; w2 > 0; w2 >>= 1) {
+      if (tl < w2) red[t] += red[t + w2];
       __syncthreads();
     }
-    if (item < items && lane == 0) d.out[item] = red[t];
+    if (item < items && tl == 0) d.out[item] = red[t];
   }
   // items beyond one pass of the block (items > blockDim.x) use one thread each
   for (int it = blockDim.x; it < items; it += blockDim.x) {
@@ -821,27 +847,41 @@ __global__ void __launch_bounds__(kBlock) k_trisweep(TriArgs<T> a) {
 #pragma unroll
       for (int q = 0; q < VEC; ++q) acc[k][q] = T(0);
     if (a.xin) {
-      for (int e = e0; e < e1; ++e) {
-        const int c = __ldg(a.ci + e);
-        T fr, fi = T(0);
-        if constexpr (CPLX) { fr = a.F[2 * e]; fi = a.F[2 * e + 1]; }
-        else fr = a.F[e];
-        const T* xr = a.xin + (size_t)c * a.ld;
+      // triangles of stencil rows hold <= 3 entries: predicated chunks of 4
+      for (int e = e0; e < e1; e += 4) {
+        int c[4];
+        T fr[4], fi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool in = e + u < e1;
+          c[u] = in ? __ldg(a.ci + e + u) : (int)row;
+          if constexpr (CPLX) {
+            fr[u] = in ? a.F[2 * (e + u)] : T(0);
+            fi[u] = in ? a.F[2 * (e + u) + 1] : T(0);
+          } else {
+            fr[u] = in ? a.F[e + u] : T(0);
+            fi[u] = T(0);
+          }
+        }
 #pragma unroll
         for (int k = 0; k < NVPT; ++k) {
           const int v = it.lane_v + k * TPR;
           if (v < a.nvec) {
-            T x[VEC];
-            vload(xr + v * VEC, x);
-            if constexpr (CPLX) {
+            T x[4][VEC];
 #pragma unroll
-              for (int q = 0; q < VEC; q += 2) {
-                acc[k][q] += fr * x[q] - fi * x[q + 1];
-                acc[k][q + 1] += fr * x[q + 1] + fi * x[q];
+            for (int u = 0; u < 4; ++u) vload(a.xin + (size_t)c[u] * a.ld + v * VEC, x[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if constexpr (CPLX) {
+#pragma unroll
+                for (int q = 0; q < VEC; q += 2) {
+                  acc[k][q] += fr[u] * x[u][q] - fi[u] * x[u][q + 1];
+                  acc[k][q + 1] += fr[u] * x[u][q + 1] + fi[u] * x[u][q];
+                }
+              } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) acc[k][q] = fma(fr[u], x[u][q], acc[k][q]);
               }
-            } else {
-#pragma unroll
-              for (int q = 0; q < VEC; ++q) acc[k][q] = fma(fr, x[q], acc[k][q]);
             }
           }
         }
@@ -950,6 +990,44 @@ static void ilu_apply(const KArgs<T>& a, const T* r, T* out, int grid, cudaStrea
   }
 }
 
+// One BiCGStab iteration: p-update, [ILU apply], SpMM + <rhat, v>, s-update,
+// [ILU apply], SpMM + <s, t>, <t, t>, x/r-update + <rhat, r>, <r, r>.
+template <class T, int TPR, int NVPT, bool CPLX, int PREC>
+static void bicg_iteration(const KArgs<T>& a, SpmmArgs<T>& sp, int grid, cudaStream_t s) {
+  k_bicg_p<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
+  CARE_LAUNCH();
+  if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.P, a.Ph, grid, s);
+  sp.X = PREC ? a.Ph : a.P; sp.Y = a.V; sp.w0 = a.Rh; sp.w1 = nullptr; sp.mode = FIN_ALPHA;
+  k_spmm<T, TPR, NVPT, CPLX, 1><<<grid, kBlock, 0, s>>>(sp);
+  CARE_LAUNCH();
+  k_bicg_s<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
+  CARE_LAUNCH();
+  if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.S, a.Sh, grid, s);
+  sp.X = PREC ? a.Sh : a.S; sp.Y = a.Tt; sp.w0 = a.S; sp.w1 = nullptr; sp.mode = FIN_OMEGA;
+  k_spmm<T, TPR, NVPT, CPLX, 2><<<grid, kBlock, 0, s>>>(sp);
+  CARE_LAUNCH();
+  k_bicg_xr<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
+  CARE_LAUNCH();
+}
+
+// Per-thread, per-device capture stream and fork/join events (created once).
+struct CaptureRes {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+static CaptureRes& capture_res() {
+  thread_local CaptureRes r[64];
+  int dev = 0;
+  CARE_CUDA(cudaGetDevice(&dev));
+  CaptureRes& c = r[dev & 63];
+  if (!c.cs) {
+    CARE_CUDA(cudaStreamCreateWithFlags(&c.cs, cudaStreamNonBlocking));
+    CARE_CUDA(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
+    CARE_CUDA(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
+  }
+  return c;
+}
+
 template <class T, int TPR, int NVPT, bool CPLX, int PREC>
 static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, int grid,
                              cudaStream_t s) {
@@ -960,36 +1038,69 @@ static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, 
   sp.hdr = a.hdr; sp.tol2 = a.tol2;
   k_bicg_init<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
   CARE_LAUNCH();
-  const int poll = 4;
+  constexpr int poll = 4;
   KHeader h{};
   int it = 0;
   CARE_CUDA(cudaMemcpyAsync(&h, a.hdr, sizeof(KHeader), cudaMemcpyDeviceToHost, s));
   CARE_CUDA(cudaStreamSynchronize(s));
   if (h.n_active == 0) return res;
-  for (it = 0; it < maxit; ++it) {
-    k_bicg_p<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
-    CARE_LAUNCH();
-    if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.P, a.Ph, grid, s);
-    sp.X = PREC ? a.Ph : a.P; sp.Y = a.V; sp.w0 = a.Rh; sp.w1 = nullptr; sp.mode = FIN_ALPHA;
-    k_spmm<T, TPR, NVPT, CPLX, 1><<<grid, kBlock, 0, s>>>(sp);
-    CARE_LAUNCH();
-    k_bicg_s<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
-    CARE_LAUNCH();
-    if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.S, a.Sh, grid, s);
-    sp.X = PREC ? a.Sh : a.S; sp.Y = a.Tt; sp.w0 = a.S; sp.w1 = nullptr; sp.mode = FIN_OMEGA;
-    k_spmm<T, TPR, NVPT, CPLX, 2><<<grid, kBlock, 0, s>>>(sp);
-    CARE_LAUNCH();
-    k_bicg_xr<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
-    CARE_LAUNCH();
-    res.spmm += 2;
-    if ((it + 1) % poll == 0 || it + 1 == maxit) {
-      CARE_CUDA(cudaMemcpyAsync(&h, a.hdr, sizeof(KHeader), cudaMemcpyDeviceToHost, s));
-      CARE_CUDA(cudaStreamSynchronize(s));
-      if (h.n_active == 0) {
-        ++it;
-        break;
+  // Capture `poll` iterations once and replay the graph; the executable graph is
+  // kept per thread and updated in place when only kernel parameters change.
+  const long per_iter = 5 + (PREC == 2 ? 4L * a.tri_sweeps : 0);
+  thread_local cudaGraphExec_t exec_cache[64] = {nullptr};
+  int dev = 0;
+  CARE_CUDA(cudaGetDevice(&dev));
+  cudaGraphExec_t& exec = exec_cache[dev & 63];
+  CaptureRes& cr = capture_res();
+  bool graphs = maxit >= poll;
+  if (graphs) {
+    cudaGraph_t g = nullptr;
+    CARE_CUDA(cudaStreamBeginCapture(cr.cs, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < poll; ++q) bicg_iteration<T, TPR, NVPT, CPLX, PREC>(a, sp, grid, cr.cs);
+    CARE_CUDA(cudaStreamEndCapture(cr.cs, &g));
+    count_launch_n(-per_iter * poll);  // captured, not executed
+    bool ok = false;
+    if (exec) {
+      cudaGraphExecUpdateResultInfo info{};
+      ok = cudaGraphExecUpdate(exec, g, &info) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
       }
     }
+    if (!ok) CARE_CUDA(cudaGraphInstantiate(&exec, g, 0));
+    cudaGraphDestroy(g);
+    // fork onto the capture stream after the caller's stream
+    CARE_CUDA(cudaEventRecord(cr.ev[0], s));
+    CARE_CUDA(cudaStreamWaitEvent(cr.cs, cr.ev[0], 0));
+  }
+  while (it < maxit) {
+    if (graphs && it + poll <= maxit) {
+      CARE_CUDA(cudaGraphLaunch(exec, cr.cs));
+      count_launch_n(per_iter * poll);
+      it += poll;
+      res.spmm += 2 * poll;
+      CARE_CUDA(cudaMemcpyAsync(&h, a.hdr, sizeof(KHeader), cudaMemcpyDeviceToHost, cr.cs));
+      CARE_CUDA(cudaStreamSynchronize(cr.cs));
+    } else {
+      cudaStream_t ss = graphs ? cr.cs : s;
+      bicg_iteration<T, TPR, NVPT, CPLX, PREC>(a, sp, grid, ss);
+      ++it;
+      res.spmm += 2;
+      if (it % poll == 0 || it == maxit) {
+        CARE_CUDA(cudaMemcpyAsync(&h, a.hdr, sizeof(KHeader), cudaMemcpyDeviceToHost, ss));
+        CARE_CUDA(cudaStreamSynchronize(ss));
+      } else {
+        continue;
+      }
+    }
+    if (h.n_active == 0) break;
+  }
+  if (graphs) {
+    // join back: the caller's stream waits for the capture stream
+    CARE_CUDA(cudaEventRecord(cr.ev[1], cr.cs));
+    CARE_CUDA(cudaStreamWaitEvent(s, cr.ev[1], 0));
   }
   res.iters = it;
   return res;
