@@ -248,6 +248,28 @@ care_status care_solve(const care_csr* A, const double* B, int ldb, int m, const
                        int p, double tol, care_prec prec, const care_opts* opts, double* Z, int ldz,
                        int r_cap, void* work, size_t work_bytes, care_stream_t s, care_info* info);
 
+/* Batched Framework 1 for `count` independent CAREs of uneven sizes (no paper
+ * counterpart; the paper solves one CARE at a time).  Instance i has A[i], B[i]
+ * (n_i x m[i], ldb[i]), C[i] (p[i] x n_i, ldc[i]) and output Z[i] (n_i x r_cap[i],
+ * ldz[i]), all as for care_solve; tol, prec, opts are shared.  Instances are
+ * ordered by estimated cost n_i (m_i + p_i) (largest first) and taken from a
+ * shared queue by `workers` host threads, each with its own CUDA stream and its
+ * own slice of `work`, so that instances overlap on the GPU.  Each instance is
+ * solved exactly as care_solve would (same kernels, same order of operations):
+ * results are bitwise identical to individual calls.  The caller's stream s
+ * waits for all workers before the call returns.  info (host, may be NULL) is
+ * an array of count entries.  Returns CARE_OK if every instance converged,
+ * otherwise the first non-OK status in instance order (all entries of info are
+ * filled either way). */
+care_status care_workspace_size_batched(int count, const care_csr* const* A, const int* m, const int* p,
+                                        const int* r_cap, care_prec prec, const care_opts* opts, int workers,
+                                        size_t* bytes);
+care_status care_solve_batched(int count, const care_csr* const* A, const double* const* B, const int* ldb,
+                               const int* m, const double* const* C, const int* ldc, const int* p, double tol,
+                               care_prec prec, const care_opts* opts, double* const* Z, const int* ldz,
+                               const int* r_cap, int workers, void* work, size_t work_bytes, care_stream_t s,
+                               care_info* info);
+
 /* LR-ADI (Section 4) for  (A - B K^T)^T X + X (A - B K^T) + W W^T = 0,  X ~ Z Z^T.
  * B, K: FP64 column-major n x m (both NULL or m = 0: no feedback).  W: FP64
  * column-major n x b.  Runs in the inner precision of prec with tolerance tol on

@@ -102,6 +102,8 @@ def lib() -> ct.CDLL:
         "lyap_lradi": (i, [P(csr_t), vp, i, vp, i, i, vp, i, i, d, i, P(opts_t), vp, i, i, vp, sz, vp, P(info_t)]),
         "care_residual_factor": (i, [P(csr_t), vp, i, i, vp, i, i, vp, i, i, d, vp, i, P(i), vp, i, P(i), i, P(d),
                                      vp, sz, vp]),
+        "care_workspace_size_batched": (i, [i, vp, vp, vp, vp, i, P(opts_t), i, P(sz)]),
+        "care_solve_batched": (i, [i, vp, vp, vp, vp, vp, vp, vp, d, i, P(opts_t), vp, vp, vp, i, vp, sz, vp, vp]),
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_host_symeig": (i, [i, vp, vp, vp]),
         "care_host_eigvals": (i, [i, vp, vp, vp]),
@@ -241,6 +243,46 @@ def care_solve(A: CSR, B, C, tol=1e-10, prec="mixed", r_cap=512, opts=None, work
                       r_cap, _ptr(ws), ws.numel(), _stream(), ct.byref(inf))
     _check(st, "care_solve", ok=tuple(allow) + (0,))
     return Zc[:inf.rank].t(), _info_dict(inf)
+
+
+def care_solve_batched(problems, tol=1e-10, prec="mixed", r_cap=256, opts=None, workers=4, allow=(0,)):
+    """Solve independent CAREs together (care_solve_batched).  problems: list of
+    (A: CSR, B, C).  Returns (list of Z, list of info dicts, status)."""
+    L = lib()
+    o = opts or default_options()
+    pc = PREC[prec] if isinstance(prec, str) else prec
+    cnt = len(problems)
+    keep = []
+    csrs = (csr_t * cnt)()
+    Ap = (ct.POINTER(csr_t) * cnt)()
+    Bp, Cp, Zp = (ct.c_void_p * cnt)(), (ct.c_void_p * cnt)(), (ct.c_void_p * cnt)()
+    ldb, ldc, ldz = (ct.c_int * cnt)(), (ct.c_int * cnt)(), (ct.c_int * cnt)()
+    ms, ps, rc = (ct.c_int * cnt)(), (ct.c_int * cnt)(), (ct.c_int * cnt)()
+    Zs = []
+    dev = problems[0][0].val.device if cnt else "cuda"
+    for i, (A, B, C) in enumerate(problems):
+        Bc, lb = _colmajor(B, A.val.device)
+        Cc, lc = _colmajor(C, A.val.device)
+        keep += [Bc, Cc]
+        csrs[i] = A.c()
+        Ap[i] = ct.pointer(csrs[i])
+        Bp[i], Cp[i] = Bc.data_ptr(), Cc.data_ptr()
+        ldb[i], ldc[i] = lb, Cc.shape[1]
+        ms[i], ps[i] = Bc.shape[0], Cc.shape[1]
+        rc[i] = r_cap
+        Zc = torch.empty(r_cap, A.n, dtype=torch.float64, device=A.val.device)
+        Zs.append(Zc)
+        Zp[i], ldz[i] = Zc.data_ptr(), A.n
+    need = ct.c_size_t(0)
+    _check(L.care_workspace_size_batched(cnt, Ap, ms, ps, rc, pc, ct.byref(o), workers, ct.byref(need)),
+           "care_workspace_size_batched")
+    ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=dev)
+    infos = (info_t * cnt)()
+    st = L.care_solve_batched(cnt, Ap, Bp, ldb, ms, Cp, ldc, ps, float(tol), pc, ct.byref(o), Zp, ldz, rc, workers,
+                              _ptr(ws), ws.numel(), _stream(), infos)
+    _check(st, "care_solve_batched", ok=tuple(allow) + (0,))
+    out_info = [_info_dict(infos[i]) for i in range(cnt)]
+    return [Zs[i][:infos[i].rank].t() for i in range(cnt)], out_info, st
 
 
 def lyap_lradi(A: CSR, W, B=None, K=None, tol=1e-10, prec="fp64", r_cap=1024, opts=None, allow=(0,)):

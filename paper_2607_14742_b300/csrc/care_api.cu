@@ -2,8 +2,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <functional>
 #include <string>
+#include <thread>
+
+#include <omp.h>
 
 #include "solver.cuh"
 
@@ -901,6 +905,101 @@ care_status care_solve(const care_csr* A, const double* B, int ldb, int m, const
   });
   if (info) info->status = st;
   return st;
+}
+
+// ---- batched solve -------------------------------------------------------
+static size_t solve_ws_bytes(const care_csr* A, int m, int p, int r_cap, care_prec prec, const care_opts* opts) {
+  size_t b = 0;
+  if (care_workspace_size(A->n, A->nnz, m, p, r_cap, prec, opts, &b) != CARE_OK) return 0;
+  return (b + 4095) & ~size_t(4095);
+}
+
+care_status care_workspace_size_batched(int count, const care_csr* const* A, const int* m, const int* p,
+                                        const int* r_cap, care_prec prec, const care_opts* opts, int workers,
+                                        size_t* bytes) {
+  if (count < 0 || workers <= 0 || !bytes || (count > 0 && (!A || !m || !p || !r_cap))) return CARE_ERR_INVALID_ARG;
+  size_t mx = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!A[i]) return CARE_ERR_INVALID_ARG;
+    const size_t b = solve_ws_bytes(A[i], m[i], p[i], r_cap[i], prec, opts);
+    if (b == 0) return CARE_ERR_INVALID_ARG;
+    mx = std::max(mx, b);
+  }
+  const int w = std::max(1, std::min(workers, count));
+  *bytes = mx * (size_t)w;
+  return CARE_OK;
+}
+
+care_status care_solve_batched(int count, const care_csr* const* A, const double* const* B, const int* ldb,
+                               const int* m, const double* const* C, const int* ldc, const int* p, double tol,
+                               care_prec prec, const care_opts* opts, double* const* Z, const int* ldz,
+                               const int* r_cap, int workers, void* work, size_t work_bytes, care_stream_t s,
+                               care_info* info) {
+  if (count < 0 || workers <= 0) return CARE_ERR_INVALID_ARG;
+  if (count == 0) return CARE_OK;
+  if (!A || !B || !ldb || !m || !C || !ldc || !p || !Z || !ldz || !r_cap || !work) return CARE_ERR_INVALID_ARG;
+  size_t need = 0;
+  care_status st = care_workspace_size_batched(count, A, m, p, r_cap, prec, opts, workers, &need);
+  if (st != CARE_OK) return st;
+  if (work_bytes < need) return CARE_ERR_WORKSPACE;
+  const int W = std::max(1, std::min(workers, count));
+  const size_t slice = need / W;
+  // longest-processing-time order by estimated cost n (m + p)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (double)A[x]->n * (m[x] + p[x]) > (double)A[y]->n * (m[y] + p[y]);
+  });
+  std::vector<care_status> status(count, CARE_OK);
+  std::vector<care_info> infos(count);
+  std::atomic<int> next{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CARE_ERR_CUDA;
+  // workers start after the caller's stream has reached this point
+  cudaEvent_t start_ev = nullptr;
+  if (cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) != cudaSuccess) return CARE_ERR_CUDA;
+  if (cudaEventRecord(start_ev, (cudaStream_t)s) != cudaSuccess) {
+    cudaEventDestroy(start_ev);
+    return CARE_ERR_CUDA;
+  }
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  std::vector<cudaStream_t> streams(W, nullptr);
+  std::vector<cudaEvent_t> done(W, nullptr);
+  bool setup_ok = true;
+  for (int w = 0; w < W; ++w) {
+    setup_ok &= cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) == cudaSuccess;
+    setup_ok &= cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming) == cudaSuccess;
+    if (setup_ok) setup_ok &= cudaStreamWaitEvent(streams[w], start_ev, 0) == cudaSuccess;
+  }
+  if (setup_ok) {
+    std::vector<std::thread> pool;
+    for (int w = 0; w < W; ++w) {
+      pool.emplace_back([&, w] {
+        cudaSetDevice(dev);
+        omp_set_num_threads(std::max(1, hw / W));  // share the host cores between workers
+        char* base = static_cast<char*>(work) + slice * w;
+        for (int k = next.fetch_add(1); k < count; k = next.fetch_add(1)) {
+          const int i = order[k];
+          status[i] = care_solve(A[i], B[i], ldb[i], m[i], C[i], ldc[i], p[i], tol, prec, opts, Z[i], ldz[i],
+                                 r_cap[i], base, slice, (care_stream_t)streams[w], &infos[i]);
+        }
+        cudaEventRecord(done[w], streams[w]);
+      });
+    }
+    for (auto& t : pool) t.join();
+    for (int w = 0; w < W; ++w) cudaStreamWaitEvent((cudaStream_t)s, done[w], 0);
+  }
+  for (int w = 0; w < W; ++w) {
+    if (streams[w]) cudaStreamDestroy(streams[w]);
+    if (done[w]) cudaEventDestroy(done[w]);
+  }
+  cudaEventDestroy(start_ev);
+  if (!setup_ok) return CARE_ERR_CUDA;
+  if (info)
+    for (int i = 0; i < count; ++i) info[i] = infos[i];
+  for (int i = 0; i < count; ++i)
+    if (status[i] != CARE_OK) return status[i];
+  return CARE_OK;
 }
 
 care_status lyap_lradi(const care_csr* A, const double* B, int ldb, const double* K, int ldk, int m, const double* W,

@@ -116,3 +116,15 @@ def test_care_solve_eigen_aligned_closed_form(pb):
     Zx = pr.meta["V"] * np.sqrt(x)
     assert info["status"] == "CARE_OK", info
     assert od.lowrank_diff_fro(Z, Zx) <= 1e-9 * od.lowrank_fro(Zx)
+
+
+def test_care_solve_eigen_aligned_3d_full_size(pb):
+    """P3 at the 3D workload's size: Laplacian on a 100^3 grid (n = 1e6, nnz = 6.94e6) with B, C
+    along three analytic modes; the exact X* is known at this size."""
+    pr = ci.eigen_aligned_problem(100, 3, [(1, 1, 1), (2, 1, 3), (1, 4, 2)], [0.6, 1.2, 0.4], [1.5, 0.7, 2.5])
+    Z, info = pb.care_solve(dcsr(pb, pr), pr.B, pr.C, tol=1e-10, prec="mixed", r_cap=64)
+    Z = Z.cpu().numpy()
+    x = od.scalar_care(pr.meta["lams"], pr.meta["beta"], pr.meta["gamma"])
+    Zx = pr.meta["V"] * np.sqrt(x)
+    assert info["status"] == "CARE_OK", info
+    assert od.lowrank_diff_fro(Z, Zx) <= 1e-8 * od.lowrank_fro(Zx)
