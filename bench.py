@@ -186,6 +186,11 @@ def main():
     C = torch.tensor(prob.C, device=dev)
     ws = pb.Workspace()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # shifted-solve configuration chosen by the library's autotuner (outside the timed region)
+    t_tune = time.perf_counter()
+    tuned, tune_ms = pb.autotune(pb.Operator(A), MP, 2 * MP, prec="mixed")
+    t_tune = time.perf_counter() - t_tune
+    tuned64, _ = pb.autotune(pb.Operator(A), MP, 2 * MP, prec="fp64")
 
     def barrier():
         if world > 1:
@@ -193,7 +198,10 @@ def main():
         torch.cuda.synchronize()
 
     def solve(prec):
-        return pb.care_solve(A, B, C, tol=TOL, prec=prec, r_cap=R_CAP, workspace=ws)
+        return pb.care_solve(A, B, C, tol=TOL, prec=prec, r_cap=R_CAP, workspace=ws,
+                             opts=pb.default_options(krylov_chunk=(tuned if prec == "mixed" else tuned64).krylov_chunk,
+                                                     tri_sweeps=(tuned if prec == "mixed" else tuned64).tri_sweeps,
+                                                     precond=(tuned if prec == "mixed" else tuned64).precond))
 
     for _ in range(args.warmup):
         Z, info = solve("mixed")
@@ -257,7 +265,9 @@ def main():
                     hA[2].to(dev, non_blocking=True))
         dB = hB.to(dev, non_blocking=True)
         dC = hC.to(dev, non_blocking=True)
-        Ze, ie = pb.care_solve(dA, dB, dC, tol=TOL, prec="mixed", r_cap=R_CAP, workspace=ws)
+        Ze, ie = pb.care_solve(dA, dB, dC, tol=TOL, prec="mixed", r_cap=R_CAP, workspace=ws,
+                               opts=pb.default_options(krylov_chunk=tuned.krylov_chunk, tri_sweeps=tuned.tri_sweeps,
+                                                       precond=tuned.precond))
         Zh = Ze.cpu()
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
@@ -275,6 +285,8 @@ def main():
         "ms_phase": {"nlradi": info["ms_phase"][0], "alg1": info["ms_phase"][1], "inner_lradi": info["ms_phase"][2],
                      "alg2": info["ms_phase"][3]},
         "fp64_path": fp64,
+        "autotune": {"krylov_chunk": tuned.krylov_chunk, "tri_sweeps": tuned.tri_sweeps, "precond": tuned.precond,
+                     "best_ms": tune_ms, "seconds": t_tune},
         "e2e": {"value": statistics.mean(e2e_t), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches // max(1, args.steps),
         "roofline": spmm["roofline"],

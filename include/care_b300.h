@@ -225,6 +225,20 @@ care_status care_shifted_solve(const care_op* op, const double* B, int ldb, cons
                                care_prec prec, const care_opts* opts, double* V, int ldv,
                                void* work, size_t work_bytes, care_stream_t s, int* iters);
 
+/* Autotuner for the shifted solves (no paper counterpart).  Times SMW + block
+ * Krylov solves of a b-column right-hand side (deterministic pseudo-random
+ * entries) at a mid-spectrum shift p = -0.05 max|a_ii| over the candidate
+ * configurations  krylov_chunk in {16, 32, 64} columns, tri_sweeps in {1, 2, 3}
+ * (ILU(0) triangular Jacobi sweeps), precond in {ILU0, NONE}, and 4 or 8 CTAs
+ * per SM for the row-block kernels; keeps the fastest configuration whose
+ * solve converged.  On return opts->krylov_chunk, tri_sweeps and precond hold
+ * the choice, the CTAs-per-SM choice is applied process-wide, and *best_ms
+ * (host, may be NULL) the best time.  work: device scratch of
+ * care_autotune_workspace_size bytes.  Synchronises s. */
+care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_prec prec, size_t* bytes);
+care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_opts* opts, void* work,
+                          size_t work_bytes, care_stream_t s, double* best_ms);
+
 /* ---- solver entry points ------------------------------------------------ */
 
 /* Workspace for care_solve / lyap_lradi / care_residual_factor on an n x n

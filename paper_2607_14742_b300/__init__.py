@@ -104,6 +104,8 @@ def lib() -> ct.CDLL:
                                      vp, sz, vp]),
         "care_workspace_size_batched": (i, [i, vp, vp, vp, vp, i, P(opts_t), i, P(sz)]),
         "care_solve_batched": (i, [i, vp, vp, vp, vp, vp, vp, vp, d, i, P(opts_t), vp, vp, vp, i, vp, sz, vp, vp]),
+        "care_autotune_workspace_size": (i, [P(op_t), i, i, i, P(sz)]),
+        "care_autotune": (i, [P(op_t), i, i, i, P(opts_t), vp, sz, vp, P(d)]),
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_host_symeig": (i, [i, vp, vp, vp]),
         "care_host_eigvals": (i, [i, vp, vp, vp]),
@@ -382,6 +384,20 @@ def spmm(op: Operator, X: torch.Tensor, shift=0.0, out: torch.Tensor | None = No
     if cplx:
         Y = torch.view_as_complex(Y.reshape(X.shape[0], b, 2).contiguous())
     return Y
+
+
+def autotune(op: Operator, m: int, b: int, prec="mixed", opts=None):
+    """care_autotune: returns (tuned options, best shifted-solve time in ms)."""
+    L = lib()
+    o = opts or default_options()
+    pc = PREC[prec] if isinstance(prec, str) else prec
+    sz = ct.c_size_t(0)
+    _check(L.care_autotune_workspace_size(ct.byref(op.op), m, b, pc, ct.byref(sz)), "care_autotune_workspace_size")
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=op.A.val.device)
+    best = ct.c_double(0)
+    _check(L.care_autotune(ct.byref(op.op), m, b, pc, ct.byref(o), _ptr(ws), ws.numel(), _stream(), ct.byref(best)),
+           "care_autotune")
+    return o, best.value
 
 
 def gram(X: torch.Tensor, Y: torch.Tensor):

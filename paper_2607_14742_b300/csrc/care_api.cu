@@ -326,7 +326,9 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
       H[(size_t)i * rt + k] = s;
     }
   std::vector<double> lam(rt), V((size_t)rt * rt);
+  const double th = now_ms();
   CARE_REQUIRE(host_symeig(rt, H.data(), lam.data(), V.data()), CARE_ERR_SMALL_DENSE, "symeig (H)");
+  c.ms_host += now_ms() - th;
   double ss = 0.0, lmax = 0.0;
   for (double l : lam) {
     ss += l * l;
@@ -406,7 +408,9 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
       Pm[(size_t)i * rt + k] = s;
     }
   std::vector<double> sig(rt), Th((size_t)rt * rt);
+  const double th = now_ms();
   CARE_REQUIRE(host_symeig(rt, Pm.data(), sig.data(), Th.data()), CARE_ERR_SMALL_DENSE, "symeig (P)");
+  c.ms_host += now_ms() - th;
   double smax = 0.0;
   for (double v : sig) smax = std::max(smax, std::fabs(v));
   const double eta = eta_mult * kU64 * smax;
@@ -546,7 +550,8 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     if (inf.nhist < CARE_HIST_MAX) inf.res_hist[inf.nhist++] = rel;
     inf.iter_outer = it;
     if (verbose_level() >= 1)
-      fprintf(stderr, "[care] refine k=%d rank=%d res=%.3e rp=%d rm=%d\n", it, S.R.r, rel, a1.rp, a1.rm);
+      fprintf(stderr, "[care] refine k=%d rank=%d res=%.3e rp=%d rm=%d  (gram %.0f ms, host eig %.0f ms so far)\n", it,
+              S.R.r, rel, a1.rp, a1.rm, c.ms_gram, c.ms_host);
     if (rel <= tol) {
       st = CARE_OK;
       break;
@@ -862,6 +867,101 @@ care_status care_shifted_solve(const care_op* op, const double* B, int ldb, cons
       return shifted_impl<double>(c, op, B, ldb, K, ldk, K ? m : 0, pre, pim, W, ldw, b, V, ldv, iters);
     return shifted_impl<float>(c, op, B, ldb, K, ldk, K ? m : 0, pre, pim, W, ldw, b, V, ldv, iters);
   });
+}
+
+// deterministic pseudo-random right-hand side for the autotuner (SplitMix64 hash of the index)
+__global__ void k_fill_hash(long count, double* x) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x1220ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+}
+
+care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_prec prec, size_t* bytes) {
+  if (!op || !bytes || b <= 0 || m < 0) return CARE_ERR_INVALID_ARG;
+  care_opts o;
+  care_opts_default(&o);
+  o.precond = CARE_PRECOND_ILU0;
+  size_t s1 = 0;
+  care_status st = care_shifted_solve_workspace_size(op, std::max(m, 1), b, prec, &o, &s1);
+  if (st != CARE_OK) return st;
+  // + right-hand side (n x b FP64) + solution (n x b complex FP64)
+  *bytes = s1 + (size_t)op->n * b * 8 * 3 + 4096;
+  return CARE_OK;
+}
+
+care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_opts* opts, void* work,
+                          size_t work_bytes, care_stream_t s, double* best_ms) {
+  if (!op || !opts || !work || b <= 0) return CARE_ERR_INVALID_ARG;
+  size_t need = 0;
+  care_status st = care_autotune_workspace_size(op, m, b, prec, &need);
+  if (st != CARE_OK) return st;
+  if (work_bytes < need) return CARE_ERR_WORKSPACE;
+  const long n = op->n;
+  char* base = static_cast<char*>(work);
+  double* W = reinterpret_cast<double*>(base);
+  double* V = W + (size_t)n * b;
+  void* sw = base + (((size_t)n * b * 8 * 3 + 4095) & ~size_t(4095));
+  const size_t sw_bytes = work_bytes - (((size_t)n * b * 8 * 3 + 4095) & ~size_t(4095));
+  cudaStream_t cs = (cudaStream_t)s;
+  k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * b, W);
+  if (cudaGetLastError() != cudaSuccess) return CARE_ERR_CUDA;
+  // mid-spectrum shift from the largest diagonal magnitude
+  std::vector<double> d(n);
+  if (cudaMemcpyAsync(d.data(), op->diag64, sizeof(double) * n, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaStreamSynchronize(cs) != cudaSuccess)
+    return CARE_ERR_CUDA;
+  double dmax = 0.0;
+  for (double v : d) dmax = std::max(dmax, std::fabs(v));
+  const double p = -0.05 * (dmax > 0 ? dmax : 1.0);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int prev_ctas = tuned_ctas_per_sm();
+  double best = 1e300;
+  care_opts bestopt = *opts;
+  int best_ctas = prev_ctas;
+  const int chunks[3] = {16, 32, 64}, sweeps[3] = {1, 2, 3}, ctas[2] = {4, 8};
+  for (int ci = 0; ci < 2; ++ci)
+    for (int pc = 0; pc < 2; ++pc)
+      for (int ki = 0; ki < 3; ++ki)
+        for (int si = 0; si < (pc == 0 ? 3 : 1); ++si) {
+          care_opts o = *opts;
+          o.precond = pc == 0 ? CARE_PRECOND_ILU0 : CARE_PRECOND_NONE;
+          o.krylov_chunk = chunks[ki];
+          o.tri_sweeps = sweeps[si];
+          set_tuned_ctas_per_sm(ctas[ci]);
+          int iters = 0;
+          // one untimed run (graph capture, caches), one timed run
+          care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw, sw_bytes, s, &iters);
+          cudaEventRecord(e0, cs);
+          care_status r = care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw,
+                                             sw_bytes, s, &iters);
+          cudaEventRecord(e1, cs);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (r == CARE_OK && ms < best) {
+            best = ms;
+            bestopt = o;
+            best_ctas = ctas[ci];
+          }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best >= 1e300) {
+    set_tuned_ctas_per_sm(prev_ctas);
+    return CARE_INNER_FAILED;
+  }
+  opts->precond = bestopt.precond;
+  opts->krylov_chunk = bestopt.krylov_chunk;
+  opts->tri_sweeps = bestopt.tri_sweeps;
+  set_tuned_ctas_per_sm(best_ctas);
+  if (best_ms) *best_ms = best;
+  return CARE_OK;
 }
 
 care_status care_workspace_size(int n, int nnz, int m, int p, int r_cap, care_prec prec, const care_opts* opts,

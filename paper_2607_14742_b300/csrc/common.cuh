@@ -143,7 +143,12 @@ inline int tpr_for(int nvec) {
 constexpr int kBlock = 256;    // threads per CTA of the row-block kernels
 constexpr int kMaxRealCols = 128;  // widest row-block handled by the fused kernels
 
-inline int grid_rows(long rows, int tpr, int ctas_per_sm = 8) {
+// CTAs per SM of the row-block kernels (set by care_autotune; default 8)
+int tuned_ctas_per_sm();
+void set_tuned_ctas_per_sm(int v);
+
+inline int grid_rows(long rows, int tpr, int ctas_per_sm = 0) {
+  if (ctas_per_sm <= 0) ctas_per_sm = tuned_ctas_per_sm();
   long rows_per_cta = (kBlock / 32) * (32 / tpr);
   long need = (rows + rows_per_cta - 1) / rows_per_cta;
   long cap = (long)device_sms() * ctas_per_sm;

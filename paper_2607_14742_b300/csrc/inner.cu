@@ -14,6 +14,10 @@ static int g_verbose = 0;
 int verbose_level() { return g_verbose; }
 void set_verbose(int v) { g_verbose = v; }
 
+static std::atomic<int> g_ctas_per_sm{8};
+int tuned_ctas_per_sm() { return g_ctas_per_sm.load(std::memory_order_relaxed); }
+void set_tuned_ctas_per_sm(int v) { g_ctas_per_sm.store(v < 1 ? 1 : (v > 8 ? 8 : v)); }
+
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launch_n(long delta) { g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed); }
@@ -59,9 +63,11 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   std::vector<double> h((size_t)a * b, 0.0);
   if (a == 0 || b == 0) return h;
   CARE_REQUIRE((size_t)a * b <= c.dG_cap, CARE_ERR_WORKSPACE, "gram output staging too small");
+  const double t0 = verbose_level() >= 1 ? (cudaStreamSynchronize(c.s), now_ms()) : 0.0;
   gram<T>(n, a, b, X, ldx, Y, ldy, c.dG, b, c.gw, c.gw_cap, c.s);
   CARE_CUDA(cudaMemcpyAsync(h.data(), c.dG, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   CARE_CUDA(cudaStreamSynchronize(c.s));
+  if (verbose_level() >= 1) c.ms_gram += now_ms() - t0;
   return h;
 }
 template std::vector<double> gram_h<float>(Ctx&, long, int, int, const float*, int, const float*, int);

@@ -23,6 +23,7 @@ struct Ctx {
   double* gw = nullptr;  // Gram split-K scratch
   size_t gw_cap = 0;
   long long krylov_iters = 0, spmm_calls = 0;
+  double ms_gram = 0.0, ms_host = 0.0;  // Gram kernels (synchronised) and host small-dense time
   int krylov_unconverged = 0;
   bool counting() const { return ar.counting(); }
 };

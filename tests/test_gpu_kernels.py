@@ -140,3 +140,18 @@ def test_spmm_fp32_difference_form_smooth_accuracy(pb):
     Y = pb.spmm(op, torch.tensor(X, dtype=torch.float32, device="cuda"), 0.0).cpu().numpy().astype(np.float64)
     ref = As.T @ X.astype(np.float32).astype(np.float64)
     assert np.linalg.norm(Y - ref) <= 50 * U32 * np.linalg.norm(ref)
+
+
+def test_autotune_picks_valid_config_and_keeps_parity(pb):
+    """The autotuner returns one of its candidate configurations, and a shifted solve with
+    the tuned options still matches the oracle."""
+    prob = ci.config_fdm2d(100, 2, 2)
+    dA, op, As = _ops(pb, prob)
+    o, best_ms = pb.autotune(op, 2, 4, prec="fp64")
+    assert best_ms > 0
+    assert o.krylov_chunk in (16, 32, 64) and o.tri_sweeps in (1, 2, 3)
+    assert o.precond in (pb.PRECOND_NONE, pb.PRECOND_ILU0)
+    W = ci.random_block(prob.n, 4, 54)
+    ref = ol.smw_solve(ol.ShiftedSolver(As), None, None, -500.0, W)
+    V, _ = pb.shifted_solve(op, W, -500.0, prec="fp64", opts=o)
+    assert np.linalg.norm(V.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
