@@ -161,7 +161,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) solve")
+    ap.add_argument("--only", default="all", choices=["all", "spmm", "gram"],
+                    help="spmm / gram: only the SpMM or Gram microbenchmark cases (the profiling cases "
+                         "for k_spmm and k_gram)")
+    ap.add_argument("--summarize-launches", metavar="CSV",
+                    help="summarise an ncu --csv launch list (gpu__time_duration.sum) per kernel and exit")
     args = ap.parse_args()
+    if args.summarize_launches:
+        return summarize_launches(args.summarize_launches)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -181,6 +189,12 @@ def main():
     dev = torch.device("cuda", local)
 
     prob = ci.config_fdm2d(GRID, MP, MP)
+    if args.only == "spmm":
+        print(json.dumps(spmm_roofline(pb, torch, prob, dev)))
+        return
+    if args.only == "gram":
+        print(json.dumps(gram_cases(pb, torch, dev)))
+        return
     A = pb.CSR.from_arrays(prob.n, prob.A.rowptr, prob.A.colind, prob.A.val, device=dev)
     B = torch.tensor(prob.B, device=dev)
     C = torch.tensor(prob.C, device=dev)
@@ -212,6 +226,8 @@ def main():
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
     barrier()
+    # the timed steps sit in an NVTX range so that a profiler can be restricted to them
+    torch.cuda.nvtx.range_push("bench_timed")
     with clocks:
         for _ in range(args.steps):
             flush.fill_(1.0)
@@ -224,6 +240,7 @@ def main():
             barrier()
             ts.append(e0.elapsed_time(e1) / 1e3)
             infos.append(info)
+    torch.cuda.nvtx.range_pop()
     launches = pb.kernel_launches() - launches0
     t = max(ts) if False else statistics.mean(ts)
     if world > 1:
@@ -257,7 +274,7 @@ def main():
     h2d = sum(x.numel() * x.element_size() for x in hA + [hB, hC])
     e2e_t = []
     d2h = 0
-    for _ in range(max(1, args.steps)):
+    for _ in range(0 if args.no_e2e else max(1, args.steps)):
         flush.fill_(1.0)
         barrier()
         t0 = time.perf_counter()
@@ -287,9 +304,10 @@ def main():
         "fp64_path": fp64,
         "autotune": {"krylov_chunk": tuned.krylov_chunk, "tri_sweeps": tuned.tri_sweeps, "precond": tuned.precond,
                      "best_ms": tune_ms, "seconds": t_tune},
-        "e2e": {"value": statistics.mean(e2e_t), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": statistics.mean(e2e_t), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                if e2e_t else None),
         "gpu_launches": launches // max(1, args.steps),
-        "roofline": spmm["roofline"],
+        "roofline": gram_roofline(info, t),
         "spmm": spmm,
         "clocks": clocks.summary(),
         "peaks_source": "MEASURED_PEAKS.json" if pk else "fallback 6400 GB/s",
@@ -303,6 +321,107 @@ def main():
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def summarize_launches(path):
+    """Per-kernel launches, total device time and share from an ncu launch list
+    (``ncu --metrics gpu__time_duration.sum --csv --log-file PATH``); prints a
+    markdown table.  ncu serialises launches and runs them cold, so the shares,
+    not the absolute times, are what carry over to the timed run."""
+    import csv
+    import re
+    with open(path, newline="") as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    rd = csv.reader(lines)
+    head = next(rd)
+    ik, im, iu, iv = (head.index(k) for k in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value"))
+    scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
+
+    def short(name):
+        # drop "void " and the trailing (argument list)
+        name = re.sub(r"^void ", "", name)
+        if name.endswith(")"):
+            depth = 0
+            for i in range(len(name) - 1, -1, -1):
+                depth += name[i] == ")"
+                depth -= name[i] == "("
+                if depth == 0:
+                    return name[:i]
+        return name
+
+    agg = {}
+    nrows = 0
+    for r in rd:
+        if len(r) <= iv or r[im] != "gpu__time_duration.sum":
+            continue
+        name = short(r[ik])
+        us = float(r[iv].replace(",", "")) * scale.get(r[iu], 1.0)
+        c, t = agg.get(name, (0, 0.0))
+        agg[name] = (c + 1, t + us)
+        nrows += 1
+    total = sum(t for _, t in agg.values())
+    print(f"{nrows} launches, {total / 1e3:.1f} ms summed device time\n")
+    print("| kernel | launches | total ms | share | mean us |")
+    print("|---|---:|---:|---:|---:|")
+    for name, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        print(f"| `{name}` | {c} | {t / 1e3:.1f} | {100 * t / total:.1f}% | {t / c:.1f} |")
+    fam = {}
+    for name, (c, t) in agg.items():
+        k = name.split("<")[0]
+        fc, ft = fam.get(k, (0, 0.0))
+        fam[k] = (fc + c, ft + t)
+    print("\n| kernel family | launches | total ms | share |")
+    print("|---|---:|---:|---:|")
+    for k, (c, t) in sorted(fam.items(), key=lambda kv: -kv[1][1]):
+        print(f"| `{k}` | {c} | {t / 1e3:.1f} | {100 * t / total:.1f}% |")
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal B300 FP64 (CUDA cores): ~2 FMA/clk/SM x 148 SMs x 2.03 GHz x 2
+
+
+def gram_roofline(info, step_s):
+    """Roofline of the dominant kernel family of the mixed solve, the FP64 Gram
+    products X^T Y of Algorithms 1-2 (k_gram<double> + its split-K reduction):
+    algorithmic FLOP (2 n a b; n a (a+1) for X^T X) over their device time, both
+    accumulated by the library with CUDA events on the solve's stream during the
+    timed step.  Bound by the FP64 FMA pipe of the CUDA cores."""
+    ms = info["gram_ms"][0]
+    gf = info["gram_gflop"][0]
+    ach = gf / ms if ms > 0 else 0.0  # GFLOP / ms = TFLOP/s
+    return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_gram<double> + k_gram_reduce: FP64 X^T Y of Algorithms 1-2 (n=250000, widths up to "
+                      "~2600 columns), measured live in the timed step with CUDA events on its stream",
+            "launches": info["gram_calls"][0], "device_s": ms / 1e3, "share_of_step": ms / 1e3 / step_s,
+            "peak_note": "nominal FP64 rate (no measured FP64 peak); FP32 Gram products of the inner solves: "
+                         f"{info['gram_gflop'][1] / max(info['gram_ms'][1], 1e-9):.2f} TFLOP/s over "
+                         f"{info['gram_ms'][1] / 1e3:.2f} s"}
+
+
+def gram_cases(pb, torch, dev):
+    """Gram microbenchmark (CUDA events on the launching stream, inputs > L2)."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, dt, n, a, b in (("f64_sym_n250000_a512", torch.float64, 250000, 512, None),
+                              ("f64_n250000_256x512", torch.float64, 250000, 256, 512),
+                              ("f32_sym_n250000_a1024", torch.float32, 250000, 1024, None)):
+        X = torch.randn(n, a, dtype=dt, device=dev)
+        Y = X if b is None else torch.randn(n, b, dtype=dt, device=dev)
+        flop = n * a * (a + 1) if b is None else 2 * n * a * b
+        ms = []
+        for it in range(7):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.gram(X, Y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= 2:
+                ms.append(e0.elapsed_time(e1))
+        m = statistics.median(ms)
+        out[name] = {"ms": m, "gflop": flop / 1e9, "TFLOPs": flop / m / 1e9}
+        del X, Y
+    return out
 
 
 def spmm_roofline(pb, torch, prob, dev):
@@ -352,7 +471,10 @@ def spmm_roofline(pb, torch, prob, dev):
     main = cases["fdm3d_100_b32_f32"]
     out["cases"] = cases
     out["roofline"] = {"bound": "hbm", "achieved": main["GBs"], "peak": peak, "unit": "GB/s",
-                       "frac": main["GBs"] / peak, "traffic": None,
+                       "frac": main["GBs"] / peak, "traffic": 289.7e6,
+                       "traffic_note": "dram read+write bytes per launch from ncu --set full of this case "
+                                       "(bench.py --only spmm): 191.5 MB read, 98.1 MB written; about 30 MB "
+                                       "of Y is still in L2 when the kernel ends",
                        "kernel": "k_spmm: Y = (A^T + pI) X, CSR, 7-point 100^3 operator (n=1e6, nnz=6.94e6), "
                                  "32 FP32 columns, difference form, L2 flushed; measured on the launching stream"}
     return out

@@ -102,6 +102,13 @@ typedef struct {
   int ilu_sweeps;        /* ILU(0) fixed-point sweeps per shift (CARE_PRECOND_ILU0)  */
   int tri_sweeps;        /* Jacobi sweeps per triangular factor in the ILU(0) apply  */
   int verbose;           /* 0 silent, 1 per outer step, 2 per ADI step (stderr)      */
+  int inner_compress;    /* FP32 inner solves only.  0 (default): the +/- correction  */
+                         /* factors go to Algorithm 2 as computed, compressed in u_s */
+                         /* only when their capacity is reached; 1: also compress    */
+                         /* them at the end of the solve when wider than             */
+                         /* max(2b, 512) (cheaper Algorithm 2, but a u_s truncation  */
+                         /* relative to ||X_+-|| slows the refinement).  FP64 inner  */
+                         /* factors are always compressed (at FP64 accuracy).        */
 } care_opts;
 
 #define CARE_HIST_MAX 32
@@ -122,6 +129,10 @@ typedef struct {
   double res_paper;       /* final Res of Section 5                                   */
   double ms_phase[4];     /* wall ms: NLR-ADI, Algorithm 1, inner LR-ADI, Algorithm 2 */
   double ms_total;        /* wall ms of the call                                      */
+  double gram_ms[2];      /* device ms (CUDA events on the call's stream) of the Gram */
+                          /* products X^T Y, [0] FP64 and [1] FP32 inputs            */
+  double gram_gflop[2];   /* their algorithmic GFLOP: 2 n a b, or n a (a+1) for X^T X */
+  long long gram_calls[2];/* their number                                             */
 } care_info;
 
 /* Prepared operator: A^T in CSR (FP64 and FP32 values) plus its diagonal, laid

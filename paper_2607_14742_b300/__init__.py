@@ -52,7 +52,7 @@ class opts_t(ct.Structure):
                 ("krylov_maxit_lo", ct.c_int), ("krylov_maxit_hi", ct.c_int), ("krylov", ct.c_int),
                 ("precond", ct.c_int), ("krylov_chunk", ct.c_int), ("stag_ratio", ct.c_double),
                 ("shift_hmin", ct.c_int), ("ilu_sweeps", ct.c_int), ("tri_sweeps", ct.c_int),
-                ("verbose", ct.c_int)]
+                ("verbose", ct.c_int), ("inner_compress", ct.c_int)]
 
 
 class info_t(ct.Structure):
@@ -60,7 +60,8 @@ class info_t(ct.Structure):
                 ("iter_outer", ct.c_int), ("iter_inner", ct.c_int), ("krylov_iters", ct.c_longlong),
                 ("spmm_calls", ct.c_longlong), ("krylov_unconverged", ct.c_int), ("nhist", ct.c_int),
                 ("res_hist", ct.c_double * HIST_MAX), ("res_rel_CtC", ct.c_double), ("res_paper", ct.c_double),
-                ("ms_phase", ct.c_double * 4), ("ms_total", ct.c_double)]
+                ("ms_phase", ct.c_double * 4), ("ms_total", ct.c_double),
+                ("gram_ms", ct.c_double * 2), ("gram_gflop", ct.c_double * 2), ("gram_calls", ct.c_longlong * 2)]
 
 
 class op_t(ct.Structure):
@@ -193,7 +194,8 @@ def _info_dict(inf: info_t) -> dict:
                 krylov_iters=inf.krylov_iters, spmm_calls=inf.spmm_calls,
                 krylov_unconverged=inf.krylov_unconverged, res_hist=list(inf.res_hist[:inf.nhist]),
                 res_rel_CtC=inf.res_rel_CtC, res_paper=inf.res_paper, ms_phase=list(inf.ms_phase),
-                ms_total=inf.ms_total)
+                ms_total=inf.ms_total, gram_ms=list(inf.gram_ms), gram_gflop=list(inf.gram_gflop),
+                gram_calls=list(inf.gram_calls))
 
 
 class Workspace:

@@ -228,7 +228,9 @@ static void alloc_small(Ctx& c, long n, int maxc, int smallcap) {
   c.dG_cap = (size_t)smallcap;
   c.dG = c.ar.get<double>(c.dG_cap);
   const long tiles = (long)((maxc + 63) / 64) * ((maxc + 63) / 64);
-  c.gw_cap = (size_t)(2L * device_sms() + tiles + 2) * 64 * 64;
+  // room for the split-K partials of any product up to maxc x maxc (at least
+  // one slice of the widest one, up to 128 MB for the narrower ones)
+  c.gw_cap = std::max((size_t)(2L * device_sms() + tiles + 2) * 64 * 64, (size_t)1 << 24);
   c.gw = c.ar.get<double>(c.gw_cap);
 }
 
@@ -570,7 +572,11 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     gemm_ts<double, T>(n, r, m, 1.0, S.R.QZ, S.R.ldq, upload(c, KB), m, 0.0, S.in.K, S.in.ldm, c.s);
     t1 = now_ms();
     const int bw = a1.rp + a1.rm;
-    AdiResult ad = lradi<T>(c, S.in, bw, a1.rp, true, tauL, c.o.jmax, false, true);
+    // FP64 inner factors are compressed at FP64 accuracy (harmless before Algorithm 2's own
+    // truncation at 10u); FP32 ones only if asked, since a u_s truncation relative to
+    // ||X_+-|| can exceed the correction X_+ - X_- itself
+    const bool cmp = sizeof(T) == 8 || c.o.inner_compress != 0;
+    AdiResult ad = lradi<T>(c, S.in, bw, a1.rp, true, tauL, c.o.jmax, false, cmp);
     inf.iter_inner += ad.steps;
     CARE_CUDA(cudaStreamSynchronize(c.s));
     inf.ms_phase[2] += now_ms() - t1;
@@ -592,6 +598,11 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.spmm_calls = c.spmm_calls;
   inf.krylov_unconverged = c.krylov_unconverged;
   inf.ms_total = now_ms() - t0;
+  for (int q = 0; q < 2; ++q) {
+    inf.gram_ms[q] = c.gram_ms[q];
+    inf.gram_gflop[q] = c.gram_gflop[q];
+    inf.gram_calls[q] = c.gram_calls[q];
+  }
   if (info) *info = inf;
   return st;
 }
@@ -632,6 +643,11 @@ static care_status lradi_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.res_rel_CtC = a.res;
   inf.status = a.converged ? CARE_OK : CARE_NOT_CONVERGED;
   inf.ms_total = now_ms() - t0;
+  for (int q = 0; q < 2; ++q) {
+    inf.gram_ms[q] = c.gram_ms[q];
+    inf.gram_gflop[q] = c.gram_gflop[q];
+    inf.gram_calls[q] = c.gram_calls[q];
+  }
   if (info) *info = inf;
   return (care_status)inf.status;
 }
@@ -758,6 +774,7 @@ void care_opts_default(care_opts* o) {
   o->ilu_sweeps = 3;
   o->tri_sweeps = 2;
   o->verbose = 0;
+  o->inner_compress = 0;
 }
 
 const char* care_status_string(int s) {

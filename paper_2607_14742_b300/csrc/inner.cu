@@ -64,9 +64,22 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   if (a == 0 || b == 0) return h;
   CARE_REQUIRE((size_t)a * b <= c.dG_cap, CARE_ERR_WORKSPACE, "gram output staging too small");
   const double t0 = verbose_level() >= 1 ? (cudaStreamSynchronize(c.s), now_ms()) : 0.0;
+  if (!c.ge0) {
+    CARE_CUDA(cudaEventCreate(&c.ge0));
+    CARE_CUDA(cudaEventCreate(&c.ge1));
+  }
+  CARE_CUDA(cudaEventRecord(c.ge0, c.s));
   gram<T>(n, a, b, X, ldx, Y, ldy, c.dG, b, c.gw, c.gw_cap, c.s);
+  CARE_CUDA(cudaEventRecord(c.ge1, c.s));
   CARE_CUDA(cudaMemcpyAsync(h.data(), c.dG, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   CARE_CUDA(cudaStreamSynchronize(c.s));
+  float ms = 0.f;
+  CARE_CUDA(cudaEventElapsedTime(&ms, c.ge0, c.ge1));
+  const int k = sizeof(T) == 8 ? 0 : 1;
+  const bool sym = a == b && (const void*)X == (const void*)Y && ldx == ldy;
+  c.gram_ms[k] += ms;
+  c.gram_gflop[k] += (sym ? (double)n * a * (a + 1) : 2.0 * n * a * b) * 1e-9;
+  c.gram_calls[k] += 1;
   if (verbose_level() >= 1) c.ms_gram += now_ms() - t0;
   return h;
 }

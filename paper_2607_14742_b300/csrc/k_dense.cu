@@ -1,10 +1,11 @@
 // Tall-skinny dense kernels on the CUDA cores (FP32 / FP64 FMA).
 //
-// gram:    G = X^T Y, a, b <= a few hundred, n up to 1e6.  Output tiles of
-//          64 x 64 per CTA, rows split across CTAs (split-K); each CTA stages
-//          32-row slabs of X and Y in shared memory, accumulates a 4 x 4 register
-//          tile per thread, and writes an FP64 partial; a second kernel sums
-//          the partials in a fixed order (deterministic).
+// gram:    G = X^T Y, a, b up to a few thousand, n up to 1e6.  Output tiles
+//          of 64 x 64 per CTA, rows split across CTAs (split-K, the split chosen
+//          to balance the CTAs over the SMs); each CTA stages 32-row slabs of X
+//          and Y in shared memory, accumulates a 4 x 4 register tile per thread,
+//          and writes an FP64 partial; a second kernel sums the partials in a
+//          fixed order (deterministic).  X^T X computes only the upper tiles.
 // gemm_ts: Y = alpha X S + beta Y with S small (a x b): 64-row x 64-column
 //          output tiles, the contraction over a staged 32 columns at a time.
 #include "dense.cuh"
@@ -14,31 +15,59 @@ namespace care {
 constexpr int GT = 64;   // output tile
 constexpr int GK = 32;   // rows (gram) / inner columns (gemm_ts) per stage
 
-// number of row slices of a Gram product: about two CTAs per SM in total,
-// at least 4 staging slabs per CTA
-static long gram_split(long n, int a, int b) {
-  const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
-  const long tiles = (long)ta * tb;
-  long split = (2L * device_sms() + tiles - 1) / tiles;
-  long maxsplit = (n + 4 * GK - 1) / (4 * GK);
-  if (split > maxsplit) split = maxsplit;
-  if (split < 1) split = 1;
-  return split;
+// Row slices (split-K) of a Gram product.  Each CTA owns one 64 x 64 output
+// tile and one slice of rows; the CUDA-core FMA pipe is the bound, so the
+// time goes with the CTAs queued on the busiest SM times the rows per CTA:
+// ceil(tiles * split / SMs) / split, minimised over split (ties to the
+// smaller split) with at least 4 staging slabs per CTA and split * a * b
+// partials within cap_elems.  A symmetric product (X^T X) has only the
+// ta (ta + 1) / 2 tiles on and above the diagonal.
+constexpr size_t GRAM_SCRATCH_TARGET = size_t(1) << 24;  // doubles (128 MB)
+
+static long gram_split(long n, int a, int b, bool sym, size_t cap_elems) {
+  const long ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
+  const long tiles = sym ? ta * (ta + 1) / 2 : ta * tb;
+  const long sms = device_sms();
+  long smax = (n + 4 * GK - 1) / (4 * GK);
+  const long by_cap = (long)(std::min(cap_elems, GRAM_SCRATCH_TARGET) / ((size_t)a * b));
+  smax = std::min(smax, std::min(by_cap, 8 * sms));
+  if (smax < 1) return 1;
+  long best = 1;
+  double best_cost = (double)((tiles + sms - 1) / sms);
+  for (long sp = 2; sp <= smax; ++sp) {
+    const double cost = (double)((tiles * sp + sms - 1) / sms) / (double)sp;
+    if (cost < best_cost * 0.995) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
 }
 
-size_t gram_work_elems(long n, int a, int b) { return (size_t)gram_split(n, a, b) * a * b; }
+size_t gram_work_elems(long n, int a, int b) {
+  long split = gram_split(n, a, b, false, GRAM_SCRATCH_TARGET);
+  if (a == b) split = std::max(split, gram_split(n, a, b, true, GRAM_SCRATCH_TARGET));
+  return (size_t)split * a * b;
+}
+
+// X^T Y is computed as a symmetric product when Y is X itself
+template <class T>
+static bool gram_is_sym(int a, int b, const T* X, int ldx, const T* Y, int ldy) {
+  return a == b && X == Y && ldx == ldy;
+}
 
 template <class T>
 __global__ void __launch_bounds__(256) k_gram(long n, int a, int b, const T* __restrict__ X, int ldx,
                                               const T* __restrict__ Y, int ldy, long rows_per,
-                                              double* __restrict__ part) {
+                                              double* __restrict__ part, bool sym) {
   __shared__ T xs[GK][GT];
   __shared__ T ys[GK][GT];
   const int ta = blockIdx.y, tb = blockIdx.z;
+  if (sym && tb < ta) return;  // strictly lower tile of a symmetric product (whole CTA)
   const int i0 = ta * GT, j0 = tb * GT;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   T acc[4][4];
-  double accd[4][4];  // FP32 inputs: each 32-row stage is flushed into FP64
+  double accd[4][4];  // FP32 inputs: FP64 accumulation of 32-row FP32 partial sums
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -72,6 +101,8 @@ __global__ void __launch_bounds__(256) k_gram(long n, int a, int b, const T* __r
         for (int v = 0; v < 4; ++v) acc[u][v] = fma(xv[u], yv[v], acc[u][v]);
     }
     if constexpr (sizeof(T) == 4) {
+      // each 32-row FP32 partial sum is flushed into FP64 (keeps the FP32
+      // rounding to 32-term sums; the inner solves are sensitive to it)
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -96,24 +127,27 @@ __global__ void __launch_bounds__(256) k_gram(long n, int a, int b, const T* __r
   }
 }
 
-// one warp per output: lanes sum strided partials, then a fixed xor-shuffle tree
+// one warp per output: lanes sum strided partials, then a fixed xor-shuffle tree;
+// a symmetric product reads the strictly lower tiles from their mirror image
 __global__ void k_gram_reduce(int a, int b, long split, const double* __restrict__ part, double* __restrict__ G,
-                              int ldg) {
+                              int ldg, bool sym) {
   const long total = (long)a * b;
   const int lane = threadIdx.x & 31;
   const long warps = (long)gridDim.x * (blockDim.x / 32);
   for (long e = (blockIdx.x * (long)blockDim.x + threadIdx.x) / 32; e < total; e += warps) {
+    const int i = (int)(e / b), j = (int)(e % b);
+    const long src = (sym && j / GT < i / GT) ? (long)j * b + i : e;
     double s0 = 0.0, s1 = 0.0;
     long g = lane;
     for (; g + 32 < split; g += 64) {
-      s0 += part[(size_t)g * total + e];
-      s1 += part[(size_t)(g + 32) * total + e];
+      s0 += part[(size_t)g * total + src];
+      s1 += part[(size_t)(g + 32) * total + src];
     }
-    if (g < split) s0 += part[(size_t)g * total + e];
+    if (g < split) s0 += part[(size_t)g * total + src];
     double v = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) G[(size_t)(e / b) * ldg + (e % b)] = v;
+    if (lane == 0) G[(size_t)i * ldg + j] = v;
   }
 }
 
@@ -122,21 +156,22 @@ void gram(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, double
           double* work, size_t work_elems, cudaStream_t s) {
   if (a == 0 || b == 0) return;
   const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
-  const size_t need = gram_work_elems(n, a, b);
-  CARE_REQUIRE(need <= work_elems, CARE_ERR_WORKSPACE, "gram: scratch too small");
-  const long split = gram_split(n, a, b);
+  const bool sym = gram_is_sym(a, b, X, ldx, Y, ldy);
+  CARE_REQUIRE((size_t)a * b <= work_elems, CARE_ERR_WORKSPACE, "gram: scratch too small");
+  const long split = gram_split(n, a, b, sym, work_elems);
+  const size_t need = (size_t)split * a * b;
   const long rows_per = ((n + split - 1) / split + GK - 1) / GK * GK;
   if (n == 0) {
     CARE_CUDA(cudaMemsetAsync(work, 0, need * sizeof(double), s));
   } else {
     dim3 grid((unsigned)split, ta, tb);
-    k_gram<T><<<grid, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, rows_per, work);
+    k_gram<T><<<grid, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, rows_per, work, sym);
     CARE_LAUNCH();
   }
   const long tot = (long)a * b;
   int g = (int)((tot + 7) / 8);  // 8 warps per CTA, one output per warp
   if (g > device_sms() * 8) g = device_sms() * 8;
-  k_gram_reduce<<<g, 256, 0, s>>>(a, b, n == 0 ? 1 : split, work, G, ldg);
+  k_gram_reduce<<<g, 256, 0, s>>>(a, b, n == 0 ? 1 : split, work, G, ldg, sym);
   CARE_LAUNCH();
 }
 template void gram<float>(long, int, int, const float*, int, const float*, int, double*, int, double*,
@@ -349,21 +384,20 @@ void gram_noalloc(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy
   CARE_CUDA(cudaGetDevice(&dev));
   double* work = gram_noalloc_scratch_ptr(dev);
   const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
-  long split = gram_split(n, a, b);
-  if (split * a * b > cap) split = cap / ((long)a * b);  // fewer, longer row slices
-  if (split < 1) split = 1;
+  const bool sym = gram_is_sym(a, b, X, ldx, Y, ldy);
+  const long split = gram_split(n, a, b, sym, (size_t)cap);
   const long rows_per = ((n + split - 1) / split + GK - 1) / GK * GK;
   if (n == 0) {
     CARE_CUDA(cudaMemsetAsync(work, 0, (size_t)a * b * sizeof(double), s));
   } else {
     dim3 grid((unsigned)split, ta, tb);
-    k_gram<T><<<grid, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, rows_per, work);
+    k_gram<T><<<grid, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, rows_per, work, sym);
     CARE_LAUNCH();
   }
   const long tot = (long)a * b;
   int g = (int)((tot + 7) / 8);
   if (g > device_sms() * 8) g = device_sms() * 8;
-  k_gram_reduce<<<g, 256, 0, s>>>(a, b, n == 0 ? 1 : split, work, G, ldg);
+  k_gram_reduce<<<g, 256, 0, s>>>(a, b, n == 0 ? 1 : split, work, G, ldg, sym);
   CARE_LAUNCH();
 }
 template void gram_noalloc<float>(long, int, int, const float*, int, const float*, int, double*, int, cudaStream_t);

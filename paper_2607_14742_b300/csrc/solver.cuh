@@ -24,8 +24,20 @@ struct Ctx {
   size_t gw_cap = 0;
   long long krylov_iters = 0, spmm_calls = 0;
   double ms_gram = 0.0, ms_host = 0.0;  // Gram kernels (synchronised) and host small-dense time
+  // device time (CUDA events on s) and algorithmic GFLOP of the Gram products,
+  // [0] FP64 inputs, [1] FP32 inputs
+  double gram_ms[2] = {0.0, 0.0}, gram_gflop[2] = {0.0, 0.0};
+  long long gram_calls[2] = {0, 0};
+  cudaEvent_t ge0 = nullptr, ge1 = nullptr;
   int krylov_unconverged = 0;
   bool counting() const { return ar.counting(); }
+  Ctx() = default;
+  Ctx(const Ctx&) = delete;
+  Ctx& operator=(const Ctx&) = delete;
+  ~Ctx() {
+    if (ge0) cudaEventDestroy(ge0);
+    if (ge1) cudaEventDestroy(ge1);
+  }
 };
 
 // host <-> device helpers for small matrices

@@ -88,6 +88,26 @@ def test_gram_parity(pb, n, a, b, dtype):
     assert np.all(np.abs(G - ref) <= (n + 2) * u * bound + 1e-300)
 
 
+@pytest.mark.parametrize("n,a", [(100, 1), (1000, 64), (5003, 65), (20000, 130), (3000, 257)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_gram_symmetric_path(pb, n, a, dtype):
+    """X^T X with Y the same buffer computes only the tiles on and above the diagonal and
+    mirrors them: exactly symmetric, and like the general product on a copy (whose
+    split-K slicing, hence summation order, may differ) within the rounding bound of the
+    oracle's product."""
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    X = torch.tensor(ci.random_block(n, a, 44), dtype=tdt, device="cuda")
+    Gs = pb.gram(X, X).cpu().numpy()
+    Gg = pb.gram(X, X.clone()).cpu().numpy()
+    assert np.array_equal(Gs, Gs.T)
+    Xh = X.double().cpu().numpy()
+    u = U64 if dtype == "f64" else U32
+    bound = (n + 2) * u * (np.abs(Xh).T @ np.abs(Xh))
+    ref = ol.gram(Xh, Xh)
+    assert np.all(np.abs(Gs - ref) <= bound)
+    assert np.all(np.abs(Gg - ref) <= bound)
+
+
 def test_gram_deterministic(pb):
     X = torch.tensor(ci.random_block(300000, 12, 43), dtype=torch.float32, device="cuda")
     g1 = pb.gram(X, X)
