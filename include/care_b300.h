@@ -326,9 +326,15 @@ unsigned long long care_kernel_launches(void);
 
 /* Symmetric eigendecomposition of the column-major n x n matrix A (host):
  * eigenvalues ascending in w, orthonormal eigenvectors in V (column-major,
- * may be NULL).  Householder tridiagonalisation + implicit QL with Wilkinson
+ * may be NULL).  Householder tridiagonalisation + implicit QR with Wilkinson
  * shifts.  Returns CARE_OK or CARE_ERR_SMALL_DENSE. */
 care_status care_host_symeig(int n, const double* A, double* w, double* V);
+
+/* The same, with eigenvectors only for the eigenvalues w <= lo or w >= hi (the
+ * other columns of V are set to zero); all eigenvalues are returned.  This is
+ * the form Algorithms 1-2 use, which keep the eigenpairs beyond their
+ * truncation thresholds (eta_r, eta_s).  V must not be NULL. */
+care_status care_host_symeig_outside(int n, const double* A, double* w, double* V, double lo, double hi);
 
 /* Eigenvalues of a real column-major n x n matrix (host): Hessenberg reduction
  * and Francis double-shift QR; real parts in wr, imaginary parts in wi. */

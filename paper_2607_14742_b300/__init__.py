@@ -109,6 +109,7 @@ def lib() -> ct.CDLL:
         "care_autotune": (i, [P(op_t), i, i, i, P(opts_t), vp, sz, vp, P(d)]),
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_host_symeig": (i, [i, vp, vp, vp]),
+        "care_host_symeig_outside": (i, [i, vp, vp, vp, d, d]),
         "care_host_eigvals": (i, [i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -468,6 +469,19 @@ def host_symeig(A):
     w = np.zeros(n)
     V = np.zeros((n, n), order="F")
     _check(lib().care_host_symeig(n, A.ctypes.data, w.ctypes.data, V.ctypes.data), "care_host_symeig")
+    return w, V
+
+
+def host_symeig_outside(A, lo, hi):
+    """Host symmetric eigendecomposition with eigenvectors only for w <= lo or w >= hi
+    (library routine): returns (w ascending, V with zero columns elsewhere)."""
+    import numpy as np
+    A = np.asfortranarray(np.asarray(A, dtype=np.float64))
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.ones((n, n), order="F")
+    _check(lib().care_host_symeig_outside(n, A.ctypes.data, w.ctypes.data, V.ctypes.data, float(lo), float(hi)),
+           "care_host_symeig_outside")
     return w, V
 
 

@@ -327,9 +327,16 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
       H[(size_t)k * rt + i] = s;
       H[(size_t)i * rt + k] = s;
     }
-  std::vector<double> lam(rt), V((size_t)rt * rt);
+  // eigenvectors only for the eigenvalues kept by the truncation at +-eta_r
+  // (none when only ||R||_F is wanted)
+  std::vector<double> lam(rt), V(Cout ? (size_t)rt * rt : 0);
   const double th = now_ms();
-  CARE_REQUIRE(host_symeig(rt, H.data(), lam.data(), V.data()), CARE_ERR_SMALL_DENSE, "symeig (H)");
+  auto kept_r = [eta_rel](double l, double lmx) {
+    const double e = eta_rel * lmx;
+    return e > 0 ? (l >= e || l <= -e) : l != 0.0;
+  };
+  CARE_REQUIRE(host_symeig_select(rt, H.data(), lam.data(), Cout ? V.data() : nullptr, kept_r),
+               CARE_ERR_SMALL_DENSE, "symeig (H)");
   c.ms_host += now_ms() - th;
   double ss = 0.0, lmax = 0.0;
   for (double l : lam) {
@@ -409,9 +416,12 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
       Pm[(size_t)k * rt + i] = s;
       Pm[(size_t)i * rt + k] = s;
     }
+  // eigenvectors only for the eigenvalues kept by the truncation at eta_s
   std::vector<double> sig(rt), Th((size_t)rt * rt);
   const double th = now_ms();
-  CARE_REQUIRE(host_symeig(rt, Pm.data(), sig.data(), Th.data()), CARE_ERR_SMALL_DENSE, "symeig (P)");
+  auto kept_s = [eta_mult](double sg, double smx) { return sg >= eta_mult * kU64 * smx && sg > 0.0; };
+  CARE_REQUIRE(host_symeig_select(rt, Pm.data(), sig.data(), Th.data(), kept_s), CARE_ERR_SMALL_DENSE,
+               "symeig (P)");
   c.ms_host += now_ms() - th;
   double smax = 0.0;
   for (double v : sig) smax = std::max(smax, std::fabs(v));
@@ -1156,6 +1166,13 @@ unsigned long long care_kernel_launches(void) { return care::launches(); }
 care_status care_host_symeig(int n, const double* A, double* w, double* V) {
   if (n < 0 || (n > 0 && (!A || !w))) return CARE_ERR_INVALID_ARG;
   return host_symeig(n, A, w, V) ? CARE_OK : CARE_ERR_SMALL_DENSE;
+}
+
+care_status care_host_symeig_outside(int n, const double* A, double* w, double* V, double lo, double hi) {
+  if (n < 0 || (n > 0 && (!A || !w || !V))) return CARE_ERR_INVALID_ARG;
+  return host_symeig_select(n, A, w, V, [lo, hi](double l, double) { return l <= lo || l >= hi; })
+             ? CARE_OK
+             : CARE_ERR_SMALL_DENSE;
 }
 
 care_status care_host_eigvals(int n, const double* A, double* wr, double* wi) {

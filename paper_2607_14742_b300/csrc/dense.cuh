@@ -2,6 +2,8 @@
 // conversions, and the host small-dense routines.
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace care {
@@ -43,6 +45,10 @@ void scale_cols(long n, int cols, T* Y, int ldy, const double* d, cudaStream_t s
 // ---- host small dense (column-major) ---------------------------------------
 // symmetric eigendecomposition, ascending eigenvalues; V may be null
 bool host_symeig(int n, const double* A, double* w, double* V);
+// the same with only the eigenvectors t for which want(w[t], max_i |w[i]|) holds
+// (the other columns of V are zero); all eigenvalues are returned
+bool host_symeig_select(int n, const double* A, double* w, double* V,
+                        const std::function<bool(double, double)>& want);
 // eigenvalues of a general real matrix
 bool host_eigvals(int n, const double* A, double* wr, double* wi);
 // upper Cholesky factor of SPD G = R^T R (column-major); false if not SPD

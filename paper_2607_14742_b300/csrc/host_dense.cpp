@@ -3,12 +3,16 @@
 // Textbook algorithms (Golub & Van Loan, Matrix Computations, 4th ed.):
 //   symmetric eigenproblem: Householder tridiagonalisation (Alg. 8.3.1) and the
 //     implicit symmetric QR step with Wilkinson shift (Alg. 8.3.2) with
-//     deflation, rotations accumulated into the eigenvector matrix;
+//     deflation; the requested eigenvectors are formed afterwards from the
+//     recorded rotations and the stored reflectors;
 //   nonsymmetric eigenvalues: Householder Hessenberg reduction (Alg. 7.4.2) and
 //     the Francis double-shift QR step (Alg. 7.5.1) with deflation;
 //   Cholesky (Alg. 4.2.2) and LU with partial pivoting (Alg. 3.4.1).
 // All matrices are column-major.
 #include <algorithm>
+#if defined(__SSE2__)
+#include <immintrin.h>
+#endif
 #include <cmath>
 #include <vector>
 
@@ -38,7 +42,78 @@ inline void givens(double x, double z, double& c, double& s) {
 
 }  // namespace
 
-bool host_symeig(int n, const double* A, double* w, double* V) {
+// Eigenvectors.  With Q_T = G_1 G_2 ... G_N the product of the QR-step
+// rotations and H_k the tridiagonalisation reflectors, eigenvector t is
+// V(:, t) = H_0 H_1 ... H_{n-3} G_1 ... G_N e_j (j its tridiagonal index).
+// Only the requested eigenvectors are formed: the rotations are recorded
+// during the QR phase and applied afterwards, last to first, to blocks of
+// SYM_BLK unit vectors (a block of n x 16 values stays in L2 while the
+// rotations stream past), then the reflectors are applied to the same block.
+namespace {
+constexpr int SYM_BLK = 16;
+
+struct Sweep {
+  int l, u;
+  size_t off;  // first rotation of the sweep in rc / rs
+};
+
+// y <- G_1 ... G_N y for a block stored as yb[k * 16 + jj] (16 independent
+// vectors): sweeps and their rotations in reverse order; rotation k of a sweep
+// maps (y_k, y_k+1) to (c y_k + s y_k+1, -s y_k + c y_k+1).
+void apply_rotations_reverse(double* yb, const std::vector<Sweep>& sw, const std::vector<double>& rc,
+                             const std::vector<double>& rs) {
+  static_assert(SYM_BLK == 16, "register blocking assumes 16 vectors");
+  for (size_t q = sw.size(); q-- > 0;) {
+    const Sweep& w = sw[q];
+    if (w.u <= w.l) continue;
+    const double* cc = &rc[w.off];
+    const double* ss = &rs[w.off];
+#if defined(__AVX2__) && defined(__FMA__)
+    double* x = yb + (size_t)w.u * SYM_BLK;
+    __m256d t0 = _mm256_loadu_pd(x), t1 = _mm256_loadu_pd(x + 4), t2 = _mm256_loadu_pd(x + 8),
+            t3 = _mm256_loadu_pd(x + 12);
+    for (int k = w.u - 1; k >= w.l; --k) {
+      x -= SYM_BLK;  // x = y_k, x + 16 = y_k+1
+      const __m256d c = _mm256_set1_pd(cc[k - w.l]), s = _mm256_set1_pd(ss[k - w.l]);
+      const __m256d a0 = _mm256_loadu_pd(x), a1 = _mm256_loadu_pd(x + 4), a2 = _mm256_loadu_pd(x + 8),
+                    a3 = _mm256_loadu_pd(x + 12);
+      // y_k+1 = c t - s a;  t = c a + s t
+      _mm256_storeu_pd(x + SYM_BLK, _mm256_fmsub_pd(c, t0, _mm256_mul_pd(s, a0)));
+      _mm256_storeu_pd(x + SYM_BLK + 4, _mm256_fmsub_pd(c, t1, _mm256_mul_pd(s, a1)));
+      _mm256_storeu_pd(x + SYM_BLK + 8, _mm256_fmsub_pd(c, t2, _mm256_mul_pd(s, a2)));
+      _mm256_storeu_pd(x + SYM_BLK + 12, _mm256_fmsub_pd(c, t3, _mm256_mul_pd(s, a3)));
+      t0 = _mm256_fmadd_pd(s, t0, _mm256_mul_pd(c, a0));
+      t1 = _mm256_fmadd_pd(s, t1, _mm256_mul_pd(c, a1));
+      t2 = _mm256_fmadd_pd(s, t2, _mm256_mul_pd(c, a2));
+      t3 = _mm256_fmadd_pd(s, t3, _mm256_mul_pd(c, a3));
+    }
+    _mm256_storeu_pd(x, t0);
+    _mm256_storeu_pd(x + 4, t1);
+    _mm256_storeu_pd(x + 8, t2);
+    _mm256_storeu_pd(x + 12, t3);
+#else
+    double t[SYM_BLK];
+    for (int jj = 0; jj < SYM_BLK; ++jj) t[jj] = yb[(size_t)w.u * SYM_BLK + jj];
+    for (int k = w.u - 1; k >= w.l; --k) {
+      const double c = cc[k - w.l], sn = ss[k - w.l];
+      double* yk = yb + (size_t)k * SYM_BLK;
+      double* yk1 = yk + SYM_BLK;
+      for (int jj = 0; jj < SYM_BLK; ++jj) {
+        const double a = yk[jj];
+        yk1[jj] = c * t[jj] - sn * a;
+        t[jj] = c * a + sn * t[jj];
+      }
+    }
+    for (int jj = 0; jj < SYM_BLK; ++jj) yb[(size_t)w.l * SYM_BLK + jj] = t[jj];
+#endif
+  }
+}
+}  // namespace
+
+bool host_symeig(int n, const double* A, double* w, double* V) { return host_symeig_select(n, A, w, V, nullptr); }
+
+bool host_symeig_select(int n, const double* A, double* w, double* V,
+                        const std::function<bool(double, double)>& want) {
   if (n <= 0) return true;
   // a: working copy (column-major == row-major for the symmetric matrix)
   std::vector<double> a(A, A + (size_t)n * n);
@@ -49,18 +124,22 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
       at(a, n, j, i) = s;
     }
   const bool vec = V != nullptr;
-  // Q is kept row-major (Q[r * n + k]) so that a plane rotation of columns
-  // (k, k+1) touches contiguous memory in every row and rows are independent
-  std::vector<double> Q;
-  if (vec) {
-    Q.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
-  }
   const bool par = n >= 96;
-  // 1. Householder tridiagonalisation: A <- H_k A H_k, Q <- Q H_k
+  // 1. Householder tridiagonalisation A <- H_k A H_k, H_k = I - beta_k v_k v_k^T with
+  //    v_k supported on k+1..n-1; the reflectors are kept for the eigenvectors
+  std::vector<double> hv, hbeta;
+  std::vector<size_t> hoff;
+  if (vec) {
+    hv.resize((size_t)n * (n - 1) / 2 + 1);
+    hbeta.assign(n, 0.0);
+    hoff.assign(n, 0);
+  }
   std::vector<double> v(n), p(n), wv(n);
+  size_t voff = 0;
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
+    if (vec) hoff[k] = voff;
+    voff += m;
     double xnorm = 0.0;
     for (int i = 0; i < m; ++i) xnorm = std::hypot(xnorm, at(a, n, k + 1 + i, k));
     if (xnorm == 0.0) continue;
@@ -97,25 +176,19 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
       at(a, n, k, i) = 0.0;
     }
     if (vec) {
-      // Q[:, k+1:] -= beta (Q[:, k+1:] v) v^T, row by row
-#pragma omp parallel for if (par) schedule(static)
-      for (int r = 0; r < n; ++r) {
-        double* qr = &Q[(size_t)r * n + k + 1];
-        double s = 0.0;
-        for (int i = 0; i < m; ++i) s += qr[i] * v[i];
-        s *= beta;
-        for (int i = 0; i < m; ++i) qr[i] -= s * v[i];
-      }
+      std::copy(v.begin(), v.begin() + m, hv.begin() + hoff[k]);
+      hbeta[k] = beta;
     }
   }
   std::vector<double> d(n), e(n, 0.0);
   for (int i = 0; i < n; ++i) d[i] = at(a, n, i, i);
   for (int i = 0; i + 1 < n; ++i) e[i] = at(a, n, i + 1, i);
-  // 2. implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e);
-  //    the rotations of one sweep are recorded and then applied to all rows
-  //    of Q in parallel
+  std::vector<double>().swap(a);
+  // 2. implicit symmetric QR with Wilkinson shift on the tridiagonal (d, e); the
+  //    rotations are recorded for the eigenvectors
+  std::vector<Sweep> sweeps;
+  std::vector<double> rc, rs;
   const double eps = 2.220446049250313e-16;
-  std::vector<double> rc(n), rs(n);
   int u = n - 1;
   long iters = 0;
   while (u > 0) {
@@ -134,11 +207,14 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
     const double mu = d[u] - (den != 0.0 ? eu * eu / den : 0.0);
     double x = d[l] - mu, z = e[l];
     double bulge = 0.0;
+    if (vec) sweeps.push_back(Sweep{l, u, rc.size()});
     for (int k = l; k < u; ++k) {
       double c, s;
       givens(x, z, c, s);
-      rc[k] = c;
-      rs[k] = s;
+      if (vec) {
+        rc.push_back(c);
+        rs.push_back(s);
+      }
       if (k > l) e[k - 1] = c * e[k - 1] - s * bulge;
       const double dk = d[k], dk1 = d[k + 1], ek = e[k];
       d[k] = c * c * dk - 2.0 * c * s * ek + s * s * dk1;
@@ -151,34 +227,71 @@ bool host_symeig(int n, const double* A, double* w, double* V) {
         z = bulge;
       }
     }
-    if (vec) {
-      const bool par2 = par && (u - l) >= 16;
-#pragma omp parallel for if (par2) schedule(static)
-      for (int r = 0; r < n; ++r) {
-        double* qr = &Q[(size_t)r * n];
-        double t1 = qr[l];
-        for (int k = l; k < u; ++k) {
-          const double c = rc[k], s = rs[k];
-          const double t2 = qr[k + 1];
-          qr[k] = c * t1 - s * t2;
-          t1 = s * t1 + c * t2;
-        }
-        qr[u] = t1;
-      }
-    }
   }
   // 3. sort ascending
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int x1, int x2) { return d[x1] < d[x2]; });
-  for (int i = 0; i < n; ++i) w[i] = d[idx[i]];
-  if (vec) {
-#pragma omp parallel for if (par) schedule(static)
-    for (int i = 0; i < n; ++i)
-      for (int r = 0; r < n; ++r) V[(size_t)i * n + r] = Q[(size_t)r * n + idx[i]];
-  }
-  for (int i = 0; i < n; ++i)
+  double wmax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    w[i] = d[idx[i]];
     if (!std::isfinite(w[i])) return false;
+    wmax = std::max(wmax, std::fabs(w[i]));
+  }
+  if (!vec) return true;
+  // 4. the requested eigenvectors, SYM_BLK at a time; the other columns are zero
+  std::vector<int> sel;
+  for (int t = 0; t < n; ++t) {
+    if (!want || want(w[t], wmax))
+      sel.push_back(t);
+    else
+      std::fill(V + (size_t)t * n, V + (size_t)(t + 1) * n, 0.0);
+  }
+  const int nsel = (int)sel.size();
+  const int nbk = (nsel + SYM_BLK - 1) / SYM_BLK;
+#pragma omp parallel for if (par && nbk > 1) schedule(dynamic, 1)
+  for (int bk = 0; bk < nbk; ++bk) {
+#if defined(__SSE2__)
+    // eigenvector entries decay exponentially along the tridiagonal; subnormal
+    // values (below 2.2e-308, far under the accuracy of any entry) are flushed
+    // to zero in this thread while the block is formed, then the mode is
+    // restored (subnormal operands cost microcode assists on x86)
+    const unsigned int csr = _mm_getcsr();
+    _mm_setcsr(csr | 0x8040u);  // FTZ | DAZ
+#endif
+    const int j0 = bk * SYM_BLK;
+    const int jn = std::min(SYM_BLK, nsel - j0);
+    std::vector<double> yb((size_t)n * SYM_BLK, 0.0);
+    for (int jj = 0; jj < jn; ++jj) yb[(size_t)idx[sel[j0 + jj]] * SYM_BLK + jj] = 1.0;
+    apply_rotations_reverse(yb.data(), sweeps, rc, rs);
+    for (int k = n - 3; k >= 0; --k) {
+      const double beta = hbeta[k];
+      if (beta == 0.0) continue;
+      const int m = n - k - 1;
+      const double* vk = &hv[hoff[k]];
+      double dot[SYM_BLK] = {};
+      for (int i = 0; i < m; ++i) {
+        const double vi = vk[i];
+        const double* row = &yb[(size_t)(k + 1 + i) * SYM_BLK];
+#pragma omp simd
+        for (int jj = 0; jj < SYM_BLK; ++jj) dot[jj] += vi * row[jj];
+      }
+      for (int jj = 0; jj < SYM_BLK; ++jj) dot[jj] *= beta;
+      for (int i = 0; i < m; ++i) {
+        const double vi = vk[i];
+        double* row = &yb[(size_t)(k + 1 + i) * SYM_BLK];
+#pragma omp simd
+        for (int jj = 0; jj < SYM_BLK; ++jj) row[jj] -= vi * dot[jj];
+      }
+    }
+    for (int jj = 0; jj < jn; ++jj) {
+      double* out = V + (size_t)sel[j0 + jj] * n;
+      for (int i = 0; i < n; ++i) out[i] = yb[(size_t)i * SYM_BLK + jj];
+    }
+#if defined(__SSE2__)
+    _mm_setcsr(csr);
+#endif
+  }
   return true;
 }
 

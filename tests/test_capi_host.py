@@ -42,7 +42,7 @@ def test_status_strings_and_defaults():
     assert "sm_103a" in pb.version()
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 7, 31, 64, 150])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 31, 64, 150, 517])
 def test_host_symeig_matches_lapack(n):
     rng = np.random.default_rng(n)
     M = rng.standard_normal((n, n))
@@ -53,6 +53,33 @@ def test_host_symeig_matches_lapack(n):
     assert np.abs(w - wr).max() <= 1e-13 * scale * n
     assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-13 * n
     assert np.abs(A @ V - V * w).max() <= 1e-13 * scale * n
+
+
+@pytest.mark.parametrize("n", [5, 37, 150, 333])
+def test_host_symeig_outside_selects_the_same_eigenpairs(n):
+    """Eigenvectors formed only for eigenvalues outside (lo, hi), as Algorithms 1-2 request
+    them: the same eigenvalues as the full decomposition, the selected columns agree with the
+    full eigenvectors up to sign, the others are zero (sizes cover several 16-column blocks
+    and a ragged last block)."""
+    rng = np.random.default_rng(100 + n)
+    M = rng.standard_normal((n, n))
+    A = M + M.T
+    w, V = pb.host_symeig(A)
+    lo, hi = np.quantile(w, 0.2), np.quantile(w, 0.7)
+    ws, Vs = pb.host_symeig_outside(A, lo, hi)
+    assert np.array_equal(ws, w)
+    keep = (w <= lo) | (w >= hi)
+    assert np.all(Vs[:, ~keep] == 0.0)
+    sgn = np.sign(np.sum(V[:, keep] * Vs[:, keep], axis=0))
+    assert np.all(sgn != 0)
+    assert np.abs(Vs[:, keep] - V[:, keep] * sgn).max() <= 1e-12
+    scale = max(1.0, np.abs(w).max())
+    assert np.abs(A @ Vs[:, keep] - Vs[:, keep] * w[keep]).max() <= 1e-13 * scale * n
+    # nothing selected / everything selected
+    w0, V0 = pb.host_symeig_outside(A, -np.inf, np.inf)
+    assert np.array_equal(w0, w) and np.all(V0 == 0.0)
+    w1, V1 = pb.host_symeig_outside(A, np.inf, -np.inf)
+    assert np.abs(np.abs(np.sum(V1 * V, axis=0)) - 1.0).max() <= 1e-12
 
 
 def test_host_symeig_degenerate():
