@@ -336,6 +336,28 @@ care_status care_host_symeig(int n, const double* A, double* w, double* V);
  * truncation thresholds (eta_r, eta_s).  V must not be NULL. */
 care_status care_host_symeig_outside(int n, const double* A, double* w, double* V, double lo, double hi);
 
+/* Upper Cholesky factor of the SPD column-major n x n matrix G = R^T R (R
+ * column-major, lower part zero).  CARE_ERR_SMALL_DENSE if G is not SPD. */
+care_status care_host_cholesky_upper(int n, const double* G, double* R);
+
+/* Rank-revealing Cholesky with complete (diagonal) pivoting of the positive
+ * semidefinite row-major c x c matrix G: stops when the largest remaining
+ * pivot is <= tol or after max_rank (> 0) pivots.  Writes the rank to *rank,
+ * the pivot order to piv[0 .. rank) and R (rank x c, row-major, original
+ * column order, rows beyond the rank zero; R must hold c x c) with
+ * G ~= R^T R.  The orthonormalisations of Algorithms 1-2 are built on it. */
+care_status care_host_pivoted_cholesky(int c, const double* G, double tol, int max_rank, int* piv, double* R,
+                                       int* rank);
+
+/* Inverse of the upper triangular row-major r x r matrix U (Ui row-major). */
+care_status care_host_upper_inverse(int r, const double* U, double* Ui);
+
+/* C = A diag(d) B^T for row-major A (m x k, lda), B (n x k, ldb), C (m x n,
+ * ldc); d may be NULL (identity).  sym != 0: B is A, m == n, and C is formed
+ * from its upper part and mirrored (exactly symmetric). */
+care_status care_host_gemm_nt(int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                              const double* d, double* C, int ldc, int sym);
+
 /* Eigenvalues of a real column-major n x n matrix (host): Hessenberg reduction
  * and Francis double-shift QR; real parts in wr, imaginary parts in wi. */
 care_status care_host_eigvals(int n, const double* A, double* wr, double* wi);

@@ -110,6 +110,10 @@ def lib() -> ct.CDLL:
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_host_symeig": (i, [i, vp, vp, vp]),
         "care_host_symeig_outside": (i, [i, vp, vp, vp, d, d]),
+        "care_host_cholesky_upper": (i, [i, vp, vp]),
+        "care_host_pivoted_cholesky": (i, [i, vp, d, i, vp, vp, P(i)]),
+        "care_host_upper_inverse": (i, [i, vp, vp]),
+        "care_host_gemm_nt": (i, [i, i, i, vp, i, vp, i, vp, vp, i, i]),
         "care_host_eigvals": (i, [i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -483,6 +487,55 @@ def host_symeig_outside(A, lo, hi):
     _check(lib().care_host_symeig_outside(n, A.ctypes.data, w.ctypes.data, V.ctypes.data, float(lo), float(hi)),
            "care_host_symeig_outside")
     return w, V
+
+
+def host_cholesky_upper(G):
+    """Upper Cholesky factor R (G = R^T R) of an SPD matrix (library routine)."""
+    import numpy as np
+    G = np.asfortranarray(np.asarray(G, dtype=np.float64))
+    n = G.shape[0]
+    R = np.zeros((n, n), order="F")
+    _check(lib().care_host_cholesky_upper(n, G.ctypes.data, R.ctypes.data), "care_host_cholesky_upper")
+    return R
+
+
+def host_pivoted_cholesky(G, tol, max_rank=0):
+    """Rank-revealing pivoted Cholesky (library routine): returns (piv, R) with
+    G ~= R^T R, R rank x c in the original column order."""
+    import numpy as np
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float64))
+    c = G.shape[0]
+    piv = np.zeros(max(c, 1), dtype=np.int32)
+    R = np.zeros((c, c))
+    rank = ct.c_int(0)
+    _check(lib().care_host_pivoted_cholesky(c, G.ctypes.data, float(tol), int(max_rank), piv.ctypes.data,
+                                            R.ctypes.data, ct.byref(rank)), "care_host_pivoted_cholesky")
+    return piv[:rank.value], R[:rank.value]
+
+
+def host_upper_inverse(U):
+    """Inverse of an upper triangular matrix (library routine)."""
+    import numpy as np
+    U = np.ascontiguousarray(np.asarray(U, dtype=np.float64))
+    r = U.shape[0]
+    Ui = np.zeros((r, r))
+    _check(lib().care_host_upper_inverse(r, U.ctypes.data, Ui.ctypes.data), "care_host_upper_inverse")
+    return Ui
+
+
+def host_gemm_nt(A, B, d=None, sym=False):
+    """C = A diag(d) B^T for row-major blocks (library routine); sym: B is A."""
+    import numpy as np
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    B = A if sym else np.ascontiguousarray(np.asarray(B, dtype=np.float64))
+    m, k = A.shape
+    n = B.shape[0]
+    C = np.full((m, n), np.nan)
+    dd = None if d is None else np.ascontiguousarray(np.asarray(d, dtype=np.float64))
+    _check(lib().care_host_gemm_nt(m, n, k, A.ctypes.data, max(k, 1), B.ctypes.data, max(k, 1),
+                                   None if dd is None else dd.ctypes.data, C.ctypes.data, max(n, 1), int(sym)),
+           "care_host_gemm_nt")
+    return C
 
 
 def host_eigvals(A):

@@ -300,13 +300,7 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
   // K = Z Z^T B -> coefficients T_Z T_Z^T (Q_Z^T B) in the Q_Z rows
   {
     std::vector<double> TT((size_t)rq * rq, 0.0);
-#pragma omp parallel for if ((long)rq * rq * r > 1000000) schedule(dynamic, 4)
-    for (int i = 0; i < rq; ++i)
-      for (int k = 0; k < rq; ++k) {
-        double s = 0.0;
-        for (int j = 0; j < r; ++j) s += TZ[(size_t)i * r + j] * TZ[(size_t)k * r + j];
-        TT[(size_t)i * rq + k] = s;
-      }
+    host_gemm_nt(rq, rq, r, TZ.data(), r, TZ.data(), r, nullptr, TT.data(), rq, true);
     for (int i = 0; i < rq; ++i)
       for (int j = 0; j < m; ++j) {
         double s = 0.0;
@@ -315,13 +309,12 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
       }
   }
   // H = tZ tA^T + tA tZ^T - tK tK^T + tC tC^T   (= T M T^T)
-  std::vector<double> H((size_t)rt * rt, 0.0);
-#pragma omp parallel for if ((long)rt * rt * (2 * r + m + p) > 1000000) schedule(dynamic, 4)
+  std::vector<double> H((size_t)rt * rt, 0.0), ZA((size_t)rt * rt, 0.0);
+  if (r) host_gemm_nt(rt, rt, r, tZ.data(), r, tA.data(), r, nullptr, ZA.data(), rt, false);
+#pragma omp parallel for if ((long)rt * rt * (m + p) > 1000000) schedule(dynamic, 4)
   for (int i = 0; i < rt; ++i)
     for (int k = i; k < rt; ++k) {
-      double s = 0.0;
-      for (int j = 0; j < r; ++j)
-        s += tZ[(size_t)i * r + j] * tA[(size_t)k * r + j] + tA[(size_t)i * r + j] * tZ[(size_t)k * r + j];
+      double s = ZA[(size_t)i * rt + k] + ZA[(size_t)k * rt + i];
       for (int j = 0; j < m; ++j) s -= tK[(size_t)i * m + j] * tK[(size_t)k * m + j];
       for (int j = 0; j < p; ++j) s += tC[(size_t)i * p + j] * tC[(size_t)k * p + j];
       H[(size_t)k * rt + i] = s;
@@ -406,16 +399,7 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
     for (int j = 0; j < ny; ++j) Gam[(size_t)(r + i) * sc + r + j] = O.T[(size_t)i * ny + j];
   for (int j = 0; j < sc; ++j) Nd[j] = j < r ? 1.0 : sign[j - r];
   std::vector<double> Pm((size_t)rt * rt, 0.0);
-#pragma omp parallel for if ((long)rt * rt * sc > 1000000) schedule(dynamic, 4)
-  for (int i = 0; i < rt; ++i)
-    for (int k = i; k < rt; ++k) {
-      double s = 0.0;
-      const double* gi = &Gam[(size_t)i * sc];
-      const double* gk = &Gam[(size_t)k * sc];
-      for (int j = 0; j < sc; ++j) s += gi[j] * Nd[j] * gk[j];
-      Pm[(size_t)k * rt + i] = s;
-      Pm[(size_t)i * rt + k] = s;
-    }
+  host_gemm_nt(rt, rt, sc, Gam.data(), sc, Gam.data(), sc, Nd.data(), Pm.data(), rt, true);
   // eigenvectors only for the eigenvalues kept by the truncation at eta_s
   std::vector<double> sig(rt), Th((size_t)rt * rt);
   const double th = now_ms();
@@ -1166,6 +1150,43 @@ unsigned long long care_kernel_launches(void) { return care::launches(); }
 care_status care_host_symeig(int n, const double* A, double* w, double* V) {
   if (n < 0 || (n > 0 && (!A || !w))) return CARE_ERR_INVALID_ARG;
   return host_symeig(n, A, w, V) ? CARE_OK : CARE_ERR_SMALL_DENSE;
+}
+
+care_status care_host_cholesky_upper(int n, const double* G, double* R) {
+  if (n < 0 || (n > 0 && (!G || !R))) return CARE_ERR_INVALID_ARG;
+  return host_cholesky_upper(n, G, R) ? CARE_OK : CARE_ERR_SMALL_DENSE;
+}
+
+care_status care_host_pivoted_cholesky(int c, const double* G, double tol, int max_rank, int* piv, double* R,
+                                       int* rank) {
+  if (c < 0 || !rank || (c > 0 && (!G || !piv || !R))) return CARE_ERR_INVALID_ARG;
+  std::vector<int> pv;
+  std::vector<double> Rv;
+  const int r = c ? host_pivoted_cholesky(c, G, tol, max_rank, pv, Rv) : 0;
+  std::fill(R, R + (size_t)c * c, 0.0);
+  std::copy(Rv.begin(), Rv.end(), R);
+  std::copy(pv.begin(), pv.end(), piv);
+  *rank = r;
+  return CARE_OK;
+}
+
+care_status care_host_upper_inverse(int r, const double* U, double* Ui) {
+  if (r < 0 || (r > 0 && (!U || !Ui))) return CARE_ERR_INVALID_ARG;
+  host_upper_inverse(r, U, Ui);
+  return CARE_OK;
+}
+
+care_status care_host_gemm_nt(int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                              const double* d, double* C, int ldc, int sym) {
+  if (m < 0 || n < 0 || k < 0 || (sym && (m != n || A != B || lda != ldb)) || ldc < n ||
+      (m > 0 && k > 0 && (!A || lda < k)) || (n > 0 && k > 0 && (!B || ldb < k)) || (m > 0 && n > 0 && !C))
+    return CARE_ERR_INVALID_ARG;
+  if (k == 0) {
+    for (int i = 0; i < m; ++i) std::fill(C + (size_t)i * ldc, C + (size_t)i * ldc + n, 0.0);
+    return CARE_OK;
+  }
+  host_gemm_nt(m, n, k, A, lda, B, ldb, d, C, ldc, sym != 0);
+  return CARE_OK;
 }
 
 care_status care_host_symeig_outside(int n, const double* A, double* w, double* V, double lo, double hi) {

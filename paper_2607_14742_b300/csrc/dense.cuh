@@ -53,6 +53,18 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
 bool host_eigvals(int n, const double* A, double* wr, double* wi);
 // upper Cholesky factor of SPD G = R^T R (column-major); false if not SPD
 bool host_cholesky_upper(int n, const double* G, double* R);
+// rank-revealing Cholesky with complete (diagonal) pivoting of the positive
+// semidefinite c x c matrix G (row-major), stopping when the largest remaining
+// pivot is <= tol or after max_rank (> 0) pivots; returns the rank r, the pivot
+// order and R (r x c, row-major, original column order) with G ~= R^T R
+int host_pivoted_cholesky(int c, const double* G, double tol, int max_rank, std::vector<int>& piv,
+                          std::vector<double>& R);
+// inverse of an upper triangular r x r matrix (row-major in and out)
+void host_upper_inverse(int r, const double* U, double* Ui);
+// C = A diag(dk) B^T (dk may be null) for row-major A (m x k), B (n x k), C (m x n);
+// sym: B is A and only the upper part is computed, then mirrored
+void host_gemm_nt(int m, int n, int k, const double* A, int lda, const double* B, int ldb, const double* dk,
+                  double* C, int ldc, bool sym);
 // complex LU solve A X = B (A n x n col-major, B n x k col-major), in place on B
 bool host_lu_solve_complex(int n, std::vector<cd> A, cd* B, int k);
 

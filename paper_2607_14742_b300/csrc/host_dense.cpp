@@ -7,7 +7,9 @@
 //     recorded rotations and the stored reflectors;
 //   nonsymmetric eigenvalues: Householder Hessenberg reduction (Alg. 7.4.2) and
 //     the Francis double-shift QR step (Alg. 7.5.1) with deflation;
-//   Cholesky (Alg. 4.2.2) and LU with partial pivoting (Alg. 3.4.1).
+//   Cholesky (Alg. 4.2.2, also with complete diagonal pivoting) and LU with
+//   partial pivoting (Alg. 3.4.1); triangular inverse by back substitution;
+//   products A diag(d) B^T of row-major blocks.
 // All matrices are column-major.
 #include <algorithm>
 #if defined(__SSE2__)
@@ -440,22 +442,148 @@ bool host_eigvals(int n, const double* A, double* wr, double* wi) {
   return true;
 }
 
+// dot product of contiguous vectors (vectorised reduction)
+static inline double dotc(const double* x, const double* y, int k) {
+  double s = 0.0;
+#pragma omp simd reduction(+ : s)
+  for (int l = 0; l < k; ++l) s += x[l] * y[l];
+  return s;
+}
+
 bool host_cholesky_upper(int n, const double* G, double* R) {
-  // G = R^T R, R upper triangular (column-major)
+  // G = R^T R, R upper triangular (column-major: R[j * n + k] = R(k, j), so the
+  // first j entries of column j are contiguous).  Column by column (Alg. 4.2.2
+  // in its dot-product form); the entries of row j right of the diagonal are
+  // independent and computed in parallel.
   for (size_t i = 0; i < (size_t)n * n; ++i) R[i] = 0.0;
+  const bool par = n >= 128;
   for (int j = 0; j < n; ++j) {
-    double s = G[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) s -= R[(size_t)j * n + k] * R[(size_t)j * n + k];
+    const double* rj = R + (size_t)j * n;
+    const double s = G[(size_t)j * n + j] - dotc(rj, rj, j);
     if (!(s > 0.0)) return false;
     const double rjj = std::sqrt(s);
     R[(size_t)j * n + j] = rjj;
+#pragma omp parallel for if (par && n - j > 64) schedule(static)
     for (int i = j + 1; i < n; ++i) {
-      double t = G[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= R[(size_t)j * n + k] * R[(size_t)i * n + k];
-      R[(size_t)i * n + j] = t / rjj;
+      double* ri = R + (size_t)i * n;
+      ri[j] = (G[(size_t)i * n + j] - dotc(rj, ri, j)) / rjj;
     }
   }
   return true;
+}
+
+int host_pivoted_cholesky(int c, const double* G, double tol, int max_rank, std::vector<int>& piv,
+                          std::vector<double>& R) {
+  // Outer loop of Alg. 4.2.2 with complete (diagonal) pivoting: the next pivot is
+  // the largest remaining diagonal entry d_j of the Schur complement.  The factor
+  // is also kept transposed (Rt[i * c + l] = R(l, i)) so that the inner products
+  // over the earlier pivots are contiguous.
+  std::vector<double> d(c);
+  for (int j = 0; j < c; ++j) d[j] = G[(size_t)j * c + j];
+  std::vector<char> used(c, 0);
+  std::vector<double> Rt((size_t)c * c, 0.0);
+  R.assign(0, 0.0);
+  piv.clear();
+  int r = 0;
+  const bool par = c >= 128;
+  while (r < c && (max_rank <= 0 || r < max_rank)) {
+    int jp = -1;
+    double best = tol;
+    for (int j = 0; j < c; ++j)
+      if (!used[j] && d[j] > best) {
+        best = d[j];
+        jp = j;
+      }
+    if (jp < 0) break;
+    used[jp] = 1;
+    piv.push_back(jp);
+    R.resize((size_t)(r + 1) * c, 0.0);
+    double* rk = &R[(size_t)r * c];
+    const double rkk = std::sqrt(d[jp]);
+    rk[jp] = rkk;
+    Rt[(size_t)jp * c + r] = rkk;
+    const double* tj = &Rt[(size_t)jp * c];
+#pragma omp parallel for if (par && (long)c * r > 100000) schedule(static)
+    for (int i = 0; i < c; ++i) {
+      if (used[i]) continue;
+      const double v = (G[(size_t)jp * c + i] - dotc(tj, &Rt[(size_t)i * c], r)) / rkk;
+      rk[i] = v;
+      Rt[(size_t)i * c + r] = v;
+      d[i] -= v * v;
+    }
+    ++r;
+  }
+  return r;
+}
+
+void host_upper_inverse(int r, const double* U, double* Ui) {
+  // Ui = U^{-1} for upper triangular U (both row-major); column j of Ui by back
+  // substitution, rows of U read contiguously; the columns are independent
+  std::fill(Ui, Ui + (size_t)r * r, 0.0);
+#pragma omp parallel if (r >= 128)
+  {
+    std::vector<double> x(r);
+#pragma omp for schedule(dynamic, 8)
+    for (int j = 0; j < r; ++j) {
+      for (int i = j; i >= 0; --i) {
+        const double* ui = U + (size_t)i * r;
+        const double s = (i == j ? 1.0 : 0.0) - dotc(ui + i + 1, &x[i + 1], j - i);
+        x[i] = s / ui[i];
+      }
+      for (int i = 0; i <= j; ++i) Ui[(size_t)i * r + j] = x[i];
+    }
+  }
+}
+
+void host_gemm_nt(int m, int n, int k, const double* A, int lda, const double* B, int ldb, const double* dk,
+                  double* C, int ldc, bool sym) {
+  // C = A diag(dk) B^T, A (m x k) and B (n x k) row-major: inner products of rows.
+  // 4 x 2 tiles of C share their row loads (8 vectorised reductions per pass);
+  // sym (A diag(dk) A^T) computes the tiles on and above the diagonal and mirrors.
+  std::vector<double> Bs;
+  if (dk) {
+    Bs.resize((size_t)n * k);
+    for (int j = 0; j < n; ++j)
+      for (int l = 0; l < k; ++l) Bs[(size_t)j * k + l] = B[(size_t)j * ldb + l] * dk[l];
+    B = Bs.data();
+    ldb = k;
+  }
+  const int mt = (m + 3) / 4;
+#pragma omp parallel for if ((long)m * n * k > 2000000) schedule(dynamic, 1)
+  for (int ti = 0; ti < mt; ++ti) {
+    const int i0 = 4 * ti;
+    const int j_begin = sym ? i0 : 0;
+    for (int j0 = j_begin; j0 < n; j0 += 2) {
+      if (i0 + 4 <= m && j0 + 2 <= n) {
+        const double *a0 = A + (size_t)i0 * lda, *a1 = a0 + lda, *a2 = a1 + lda, *a3 = a2 + lda;
+        const double *b0 = B + (size_t)j0 * ldb, *b1 = b0 + ldb;
+        double s00 = 0, s01 = 0, s10 = 0, s11 = 0, s20 = 0, s21 = 0, s30 = 0, s31 = 0;
+#pragma omp simd reduction(+ : s00, s01, s10, s11, s20, s21, s30, s31)
+        for (int l = 0; l < k; ++l) {
+          const double x0 = b0[l], x1 = b1[l];
+          s00 += a0[l] * x0;
+          s01 += a0[l] * x1;
+          s10 += a1[l] * x0;
+          s11 += a1[l] * x1;
+          s20 += a2[l] * x0;
+          s21 += a2[l] * x1;
+          s30 += a3[l] * x0;
+          s31 += a3[l] * x1;
+        }
+        const double t[4][2] = {{s00, s01}, {s10, s11}, {s20, s21}, {s30, s31}};
+        for (int u = 0; u < 4; ++u)
+          for (int v = 0; v < 2; ++v) C[(size_t)(i0 + u) * ldc + j0 + v] = t[u][v];
+      } else {
+        for (int i = i0; i < std::min(m, i0 + 4); ++i)
+          for (int j = j0; j < std::min(n, j0 + 2); ++j)
+            C[(size_t)i * ldc + j] = dotc(A + (size_t)i * lda, B + (size_t)j * ldb, k);
+      }
+    }
+  }
+  if (sym)
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < std::min(i, n); ++j)
+        if (j < (i / 4) * 4) C[(size_t)i * ldc + j] = C[(size_t)j * ldc + i];
 }
 
 bool host_lu_solve_complex(int n, std::vector<cd> A, cd* B, int k) {

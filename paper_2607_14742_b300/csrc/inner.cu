@@ -87,47 +87,6 @@ template std::vector<double> gram_h<float>(Ctx&, long, int, int, const float*, i
 template std::vector<double> gram_h<double>(Ctx&, long, int, int, const double*, int, const double*, int);
 
 // ------------------------------------------------------------ orth_rr -----
-// Rank-revealing Cholesky with complete (diagonal) pivoting of the SPD-semidefinite
-// c x c matrix G (row-major).  Stops when the largest remaining pivot is
-// <= tol (or after max_rank pivots).  Returns the pivot order and R (r x c,
-// row-major, original column order) with G ~= R^T R.
-static int pivoted_cholesky(int c, const std::vector<double>& G, double tol, int max_rank, std::vector<int>& piv,
-                            std::vector<double>& R) {
-  std::vector<double> d(c);
-  for (int j = 0; j < c; ++j) d[j] = G[(size_t)j * c + j];
-  std::vector<char> used(c, 0);
-  R.assign(0, 0.0);
-  piv.clear();
-  int r = 0;
-  while (r < c && (max_rank <= 0 || r < max_rank)) {
-    int jp = -1;
-    double best = tol;
-    for (int j = 0; j < c; ++j)
-      if (!used[j] && d[j] > best) {
-        best = d[j];
-        jp = j;
-      }
-    if (jp < 0) break;
-    used[jp] = 1;
-    piv.push_back(jp);
-    R.resize((size_t)(r + 1) * c, 0.0);
-    double* rk = &R[(size_t)r * c];
-    const double rkk = std::sqrt(d[jp]);
-    rk[jp] = rkk;
-    const double* Rd = R.data();
-#pragma omp parallel for if ((long)c * r > 200000) schedule(static)
-    for (int i = 0; i < c; ++i) {
-      if (used[i]) continue;
-      double s = G[(size_t)jp * c + i];
-      for (int l = 0; l < r; ++l) s -= Rd[(size_t)l * c + jp] * Rd[(size_t)l * c + i];
-      rk[i] = s / rkk;
-      d[i] -= rk[i] * rk[i];
-    }
-    ++r;
-  }
-  return r;
-}
-
 template <class T>
 OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double drop_rel,
                 const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo) {
@@ -157,18 +116,13 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   // whose residual norm relative to their column is below sqrt(drop_rel)
   std::vector<int> piv;
   std::vector<double> Rs;
-  const int r1 = pivoted_cholesky(cols, Gs, drop_rel, max_rank, piv, Rs);
+  const int r1 = host_pivoted_cholesky(cols, Gs.data(), drop_rel, max_rank, piv, Rs);
   if (r1 == 0) return o;
   // R11 = Rs(:, piv) is upper triangular; M1 = D^{-1} P R11^{-1} (cols x r1), T1 = Rs D (r1 x cols)
   std::vector<double> R11((size_t)r1 * r1, 0.0), R11i((size_t)r1 * r1, 0.0);
   for (int i = 0; i < r1; ++i)
     for (int k = 0; k < r1; ++k) R11[(size_t)i * r1 + k] = Rs[(size_t)i * cols + piv[k]];
-  for (int j = 0; j < r1; ++j)
-    for (int i = j; i >= 0; --i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= j; ++k) s -= R11[(size_t)i * r1 + k] * R11i[(size_t)k * r1 + j];
-      R11i[(size_t)i * r1 + j] = s / R11[(size_t)i * r1 + i];
-    }
+  host_upper_inverse(r1, R11.data(), R11i.data());
   std::vector<double> M1((size_t)cols * r1, 0.0), T1((size_t)r1 * cols, 0.0);
   for (int k = 0; k < r1; ++k) {
     const int j = piv[k];
@@ -206,13 +160,10 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
     return o;
   }
   // Rinv (r1 x r1, row-major) from the column-major upper factor
-  std::vector<double> Rinv((size_t)r1 * r1, 0.0);
-  for (int j = 0; j < r1; ++j)
-    for (int i = j; i >= 0; --i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= j; ++k) s -= R[(size_t)k * r1 + i] * Rinv[(size_t)k * r1 + j];
-      Rinv[(size_t)i * r1 + j] = s / R[(size_t)i * r1 + i];
-    }
+  std::vector<double> Rrm((size_t)r1 * r1), Rinv((size_t)r1 * r1);
+  for (int a = 0; a < r1; ++a)
+    for (int b = 0; b < r1; ++b) Rrm[(size_t)a * r1 + b] = R[(size_t)b * r1 + a];
+  host_upper_inverse(r1, Rrm.data(), Rinv.data());
   gemm_ts<T, T>(n, r1, r1, 1.0, buf, ldb, upload(c, Rinv), r1, 0.0, X, ldx, c.s);
   o.rank = r1;
   o.T.assign((size_t)r1 * cols, 0.0);
@@ -458,16 +409,7 @@ static int compress_part(Ctx& c, Inner<T>& in, int col0, int ncols, bool right_a
   const int q = o.rank;
   if (q == 0) return 0;
   std::vector<double> TT((size_t)q * q, 0.0), R((size_t)q * q);
-#pragma omp parallel for if ((long)q * q * ncols > 1000000) schedule(dynamic, 4)
-  for (int i = 0; i < q; ++i)
-    for (int k = 0; k <= i; ++k) {
-      double acc = 0.0;
-      const double* ti = &o.T[(size_t)i * ncols];
-      const double* tk = &o.T[(size_t)k * ncols];
-      for (int j = 0; j < ncols; ++j) acc += ti[j] * tk[j];
-      TT[(size_t)i * q + k] = acc;
-      TT[(size_t)k * q + i] = acc;
-    }
+  host_gemm_nt(q, q, ncols, o.T.data(), ncols, o.T.data(), ncols, nullptr, TT.data(), q, true);
   CARE_REQUIRE(host_cholesky_upper(q, TT.data(), R.data()), CARE_ERR_SMALL_DENSE, "compression Cholesky");
   // column-major upper R == row-major R^T = L
   gemm_ts<T, T>(n, q, q, 1.0, in.Z + col0, in.ldz, upload(c, R), q, 0.0, in.Zs, in.ldz, c.s);

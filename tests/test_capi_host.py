@@ -82,6 +82,55 @@ def test_host_symeig_outside_selects_the_same_eigenpairs(n):
     assert np.abs(np.abs(np.sum(V1 * V, axis=0)) - 1.0).max() <= 1e-12
 
 
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 5, 3), (130, 67, 301), (257, 257, 1000)])
+def test_host_gemm_nt(m, n, k):
+    rng = np.random.default_rng(m + n + k)
+    A = rng.standard_normal((m, k))
+    B = rng.standard_normal((n, k))
+    d = rng.choice([-1.0, 1.0, 0.5], size=k)
+    bound = k * 2.0 ** -52 * (np.abs(A) @ np.abs(B).T)
+    assert np.all(np.abs(pb.host_gemm_nt(A, B) - A @ B.T) <= 2 * bound)
+    assert np.all(np.abs(pb.host_gemm_nt(A, B, d) - (A * d) @ B.T) <= 2 * bound)
+    if m == n:
+        S = pb.host_gemm_nt(A, A, d, sym=True)
+        assert np.array_equal(S, S.T)
+        assert np.all(np.abs(S - (A * d) @ A.T) <= 2 * k * 2.0 ** -52 * (np.abs(A) @ np.abs(A).T))
+
+
+@pytest.mark.parametrize("n", [1, 5, 64, 200, 700])
+def test_host_cholesky_and_upper_inverse(n):
+    rng = np.random.default_rng(n)
+    M = rng.standard_normal((n, n))
+    G = M @ M.T + n * np.eye(n)
+    R = pb.host_cholesky_upper(G)
+    assert np.allclose(np.tril(R, -1), 0.0)
+    assert np.abs(R.T @ R - G).max() <= 1e-13 * np.abs(G).max() * n
+    assert np.allclose(R, np.linalg.cholesky(G).T, rtol=0, atol=1e-12 * np.sqrt(np.abs(G).max()) * n)
+    Ri = pb.host_upper_inverse(R)
+    assert np.allclose(np.tril(Ri, -1), 0.0)
+    assert np.abs(R @ Ri - np.eye(n)).max() <= 1e-12 * n
+    with pytest.raises(pb.CareError):
+        pb.host_cholesky_upper(-np.eye(3))
+
+
+@pytest.mark.parametrize("c,rank", [(1, 1), (9, 4), (150, 150), (300, 211)])
+def test_host_pivoted_cholesky_rank_revealing(c, rank):
+    """G = X^T X with X of rank r: the pivoted factor has rank r, upper triangular
+    in pivot order, reproduces G, and the pivots are the largest Schur diagonals."""
+    rng = np.random.default_rng(c * 7 + rank)
+    X = rng.standard_normal((c + 50, rank)) @ rng.standard_normal((rank, c))
+    G = X.T @ X
+    piv, R = pb.host_pivoted_cholesky(G, 1e-10 * np.abs(G).max())
+    assert len(piv) == rank and len(set(piv.tolist())) == rank
+    assert np.abs(R.T @ R - G).max() <= 1e-9 * np.abs(G).max()
+    Rp = R[:, piv]
+    assert np.allclose(np.tril(Rp, -1), 0.0)
+    assert np.all(np.diag(Rp) > 0) and np.all(np.diff(np.diag(Rp)) <= 1e-9 * Rp[0, 0])
+    assert piv[0] == np.argmax(np.diag(G))
+    p2, R2 = pb.host_pivoted_cholesky(G, 0.0, max_rank=3)
+    assert len(p2) == min(3, rank) and np.array_equal(p2, piv[:len(p2)])
+
+
 def test_host_symeig_degenerate():
     w, V = pb.host_symeig(np.eye(6))
     assert np.allclose(w, 1.0) and np.allclose(V.T @ V, np.eye(6))
