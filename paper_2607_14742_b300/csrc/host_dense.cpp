@@ -44,6 +44,14 @@ inline void givens(double x, double z, double& c, double& s) {
 
 }  // namespace
 
+// dot product of contiguous vectors (vectorised reduction)
+static inline double dotc(const double* x, const double* y, int k) {
+  double s = 0.0;
+#pragma omp simd reduction(+ : s)
+  for (int l = 0; l < k; ++l) s += x[l] * y[l];
+  return s;
+}
+
 // Eigenvectors.  With Q_T = G_1 G_2 ... G_N the product of the QR-step
 // rotations and H_k the tridiagonalisation reflectors, eigenvector t is
 // V(:, t) = H_0 H_1 ... H_{n-3} G_1 ... G_N e_j (j its tridiagonal index).
@@ -155,14 +163,8 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
     const double beta = 2.0 / vn2;
     // p = beta * A22 v  (A22 symmetric: p_i = beta * sum_j a(k+1+j, k+1+i) v_j, column i contiguous)
 #pragma omp parallel for if (par) schedule(static)
-    for (int i = 0; i < m; ++i) {
-      const double* col = &a[(size_t)(k + 1 + i) * n + k + 1];
-      double acc = 0.0;
-      for (int j = 0; j < m; ++j) acc += col[j] * v[j];
-      p[i] = beta * acc;
-    }
-    double pv = 0.0;
-    for (int i = 0; i < m; ++i) pv += p[i] * v[i];
+    for (int i = 0; i < m; ++i) p[i] = beta * dotc(&a[(size_t)(k + 1 + i) * n + k + 1], v.data(), m);
+    const double pv = dotc(p.data(), v.data(), m);
     const double K = 0.5 * beta * pv;
     for (int i = 0; i < m; ++i) wv[i] = p[i] - K * v[i];
 #pragma omp parallel for if (par) schedule(static)
@@ -440,14 +442,6 @@ bool host_eigvals(int n, const double* A, double* wr, double* wi) {
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(wr[i]) || !std::isfinite(wi[i])) return false;
   return true;
-}
-
-// dot product of contiguous vectors (vectorised reduction)
-static inline double dotc(const double* x, const double* y, int k) {
-  double s = 0.0;
-#pragma omp simd reduction(+ : s)
-  for (int l = 0; l < k; ++l) s += x[l] * y[l];
-  return s;
 }
 
 bool host_cholesky_upper(int n, const double* G, double* R) {
