@@ -349,6 +349,12 @@ care_status care_host_cholesky_upper(int n, const double* G, double* R);
 care_status care_host_pivoted_cholesky(int c, const double* G, double tol, int max_rank, int* piv, double* R,
                                        int* rank);
 
+/* Largest eigenvalue of the symmetric n x n matrix G (host), as LR-ADI's
+ * stopping test ||W^T W||_2 needs it: Lanczos with full reorthogonalisation to a
+ * relative residual bound of 1e-13, or the full eigenvalue computation for
+ * n <= 96 or without convergence in 120 steps. */
+care_status care_host_sym_lmax(int n, const double* G, double* lmax);
+
 /* Inverse of the upper triangular row-major r x r matrix U (Ui row-major). */
 care_status care_host_upper_inverse(int r, const double* U, double* Ui);
 

@@ -113,6 +113,7 @@ def lib() -> ct.CDLL:
         "care_host_cholesky_upper": (i, [i, vp, vp]),
         "care_host_pivoted_cholesky": (i, [i, vp, d, i, vp, vp, P(i)]),
         "care_host_upper_inverse": (i, [i, vp, vp]),
+        "care_host_sym_lmax": (i, [i, vp, P(d)]),
         "care_host_gemm_nt": (i, [i, i, i, vp, i, vp, i, vp, vp, i, i]),
         "care_host_eigvals": (i, [i, vp, vp, vp]),
     }
@@ -511,6 +512,15 @@ def host_pivoted_cholesky(G, tol, max_rank=0):
     _check(lib().care_host_pivoted_cholesky(c, G.ctypes.data, float(tol), int(max_rank), piv.ctypes.data,
                                             R.ctypes.data, ct.byref(rank)), "care_host_pivoted_cholesky")
     return piv[:rank.value], R[:rank.value]
+
+
+def host_sym_lmax(G):
+    """Largest eigenvalue of a symmetric matrix (library routine, Lanczos)."""
+    import numpy as np
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.float64))
+    out = ct.c_double(0.0)
+    _check(lib().care_host_sym_lmax(G.shape[0], G.ctypes.data, ct.byref(out)), "care_host_sym_lmax")
+    return out.value
 
 
 def host_upper_inverse(U):

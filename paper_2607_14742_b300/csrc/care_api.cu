@@ -1170,6 +1170,14 @@ care_status care_host_pivoted_cholesky(int c, const double* G, double tol, int m
   return CARE_OK;
 }
 
+care_status care_host_sym_lmax(int n, const double* G, double* lmax) {
+  if (n < 0 || !lmax || (n > 0 && !G)) return CARE_ERR_INVALID_ARG;
+  const double l = host_sym_lmax(n, G);
+  if (!std::isfinite(l)) return CARE_ERR_SMALL_DENSE;
+  *lmax = l;
+  return CARE_OK;
+}
+
 care_status care_host_upper_inverse(int r, const double* U, double* Ui) {
   if (r < 0 || (r > 0 && (!U || !Ui))) return CARE_ERR_INVALID_ARG;
   host_upper_inverse(r, U, Ui);

@@ -49,6 +49,8 @@ bool host_symeig(int n, const double* A, double* w, double* V);
 // (the other columns of V are zero); all eigenvalues are returned
 bool host_symeig_select(int n, const double* A, double* w, double* V,
                         const std::function<bool(double, double)>& want);
+// largest eigenvalue of a symmetric matrix (Lanczos; full eig for small n)
+double host_sym_lmax(int n, const double* G);
 // eigenvalues of a general real matrix
 bool host_eigvals(int n, const double* A, double* wr, double* wi);
 // upper Cholesky factor of SPD G = R^T R (column-major); false if not SPD

@@ -16,6 +16,7 @@
 #include <immintrin.h>
 #endif
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "dense.cuh"
@@ -297,6 +298,80 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
 #endif
   }
   return true;
+}
+
+double host_sym_lmax(int n, const double* G) {
+  // Largest eigenvalue of the symmetric n x n matrix G by Lanczos with full
+  // reorthogonalisation (Golub & Van Loan, Sec. 10.1): the largest Ritz value
+  // theta of the k x k tridiagonal T_k is returned once its residual bound
+  // |beta_k s_k| (s_k the last entry of its Ritz vector; checked every 4 steps)
+  // is below 1e-10 theta, so that an eigenvalue of G lies within 1e-10 theta of
+  // it.  Matrices with n < 700 (where the full computation is as fast), and a
+  // run that has not converged after kmax steps, use the full eigenvalue
+  // computation.  The start vector is a fixed pseudo-random one.
+  if (n <= 0) return 0.0;
+  auto full = [&]() {
+    std::vector<double> w(n);
+    if (!host_symeig(n, G, w.data(), nullptr)) return std::nan("");
+    return w[n - 1];
+  };
+  if (n < 700) return full();
+  const int kmax = std::min(n, 160);
+  std::vector<double> Q((size_t)kmax * n), w(n), alpha, beta;
+  uint64_t st = 0x243f6a8885a308d3ull;
+  double nrm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    st += 0x9e3779b97f4a7c15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    Q[i] = (double)(z >> 11) * 0x1.0p-53 - 0.5;
+    nrm += Q[i] * Q[i];
+  }
+  nrm = std::sqrt(nrm);
+  for (int i = 0; i < n; ++i) Q[i] /= nrm;
+  const bool par = n >= 512;
+  for (int k = 0; k < kmax; ++k) {
+    const double* q = &Q[(size_t)k * n];
+#pragma omp parallel for if (par) schedule(static)
+    for (int i = 0; i < n; ++i) w[i] = dotc(G + (size_t)i * n, q, n);
+    alpha.push_back(dotc(q, w.data(), n));
+    // full reorthogonalisation against q_0 .. q_k, twice
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j <= k; ++j) {
+        const double* qj = &Q[(size_t)j * n];
+        const double h = dotc(qj, w.data(), n);
+        for (int i = 0; i < n; ++i) w[i] -= h * qj[i];
+      }
+    const double bk = std::sqrt(dotc(w.data(), w.data(), n));
+    const bool last = k + 1 == kmax || bk <= 1e-300;
+    if (k % 4 != 3 && !last) {
+      beta.push_back(bk);
+      double* qn = &Q[(size_t)(k + 1) * n];
+      for (int i = 0; i < n; ++i) qn[i] = w[i] / bk;
+      continue;
+    }
+    // largest eigenpair of T_{k+1}
+    const int m = k + 1;
+    std::vector<double> T((size_t)m * m, 0.0), ev(m), V((size_t)m * m);
+    for (int i = 0; i < m; ++i) {
+      T[(size_t)i * m + i] = alpha[i];
+      if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = beta[i];
+    }
+    if (!host_symeig(m, T.data(), ev.data(), V.data())) return full();
+    const double theta = ev[m - 1];
+    const double sk = V[(size_t)(m - 1) * m + (m - 1)];
+    const double scale = std::max(std::fabs(theta), 1e-300);
+    if (std::fabs(bk * sk) <= 1e-10 * scale || bk <= 1e-300) return theta;
+    if (k + 1 == n) return theta;  // T_n is similar to G
+    beta.push_back(bk);
+    if (k + 1 < kmax) {
+      double* qn = &Q[(size_t)(k + 1) * n];
+      for (int i = 0; i < n; ++i) qn[i] = w[i] / bk;
+    }
+  }
+  return full();
 }
 
 bool host_eigvals(int n, const double* A, double* wr, double* wi) {

@@ -388,9 +388,9 @@ template <class T>
 static double adi_norm2(Ctx& c, Inner<T>& in, int b) {
   // ||W^T W||_2 = largest eigenvalue of the b x b Gram matrix
   std::vector<double> G = gram_h<T>(c, in.n, b, b, in.W, in.ldw, in.W, in.ldw);
-  std::vector<double> w(b);
-  CARE_REQUIRE(host_symeig(b, G.data(), w.data(), nullptr), CARE_ERR_SMALL_DENSE, "symeig (ADI norm)");
-  return std::max(w[b - 1], 0.0);
+  const double l = host_sym_lmax(b, G.data());
+  CARE_REQUIRE(std::isfinite(l), CARE_ERR_SMALL_DENSE, "largest eigenvalue (ADI norm)");
+  return std::max(l, 0.0);
 }
 
 // Compresses the factor columns Z[:, col0 : col0 + ncols] (one sign group) to

@@ -131,6 +131,38 @@ def test_host_pivoted_cholesky_rank_revealing(c, rank):
     assert len(p2) == min(3, rank) and np.array_equal(p2, piv[:len(p2)])
 
 
+@pytest.mark.parametrize("case", ["wide", "rank_deficient", "clustered", "clustered_large", "small", "zero",
+                                  "decaying"])
+def test_host_sym_lmax(case):
+    """Largest eigenvalue as LR-ADI's stopping test needs it, against LAPACK: within the
+    routine's residual bound (1e-10 relative; clustered leading eigenvalues may return
+    any member of the cluster within that bound)."""
+    rng = np.random.default_rng(len(case))
+    if case == "wide":
+        W = rng.standard_normal((3000, 700)); G = W.T @ W
+    elif case == "rank_deficient":
+        W = rng.standard_normal((400, 150)) @ rng.standard_normal((150, 900)); G = W.T @ W
+    elif case == "clustered":
+        Q, _ = np.linalg.qr(rng.standard_normal((300, 300)))
+        d = np.concatenate([np.full(5, 7.0), 7.0 - 1e-9 * np.arange(5), rng.uniform(0, 6.9, 290)])
+        G = (Q * d) @ Q.T
+    elif case == "small":
+        W = rng.standard_normal((50, 40)); G = W.T @ W
+    elif case == "clustered_large":
+        Q, _ = np.linalg.qr(rng.standard_normal((900, 900)))
+        d = np.concatenate([np.full(5, 7.0), 7.0 - 1e-9 * np.arange(5), rng.uniform(0, 6.9, 890)])
+        G = (Q * d) @ Q.T
+    elif case == "zero":
+        G = np.zeros((800, 800))
+    else:
+        Q, _ = np.linalg.qr(rng.standard_normal((800, 800)))
+        G = (Q * np.logspace(0, -14, 800)) @ Q.T
+    ref = np.linalg.eigvalsh(G)[-1]
+    got = pb.host_sym_lmax(G)
+    assert got <= ref * (1 + 1e-12) + 1e-300
+    assert abs(got - ref) <= 1e-10 * max(abs(ref), 1e-300) + 1e-300, (got, ref)
+
+
 def test_host_symeig_degenerate():
     w, V = pb.host_symeig(np.eye(6))
     assert np.allclose(w, 1.0) and np.allclose(V.T @ V, np.eye(6))
