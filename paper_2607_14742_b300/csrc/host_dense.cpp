@@ -151,9 +151,16 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
     const int m = n - k - 1;
     if (vec) hoff[k] = voff;
     voff += m;
-    double xnorm = 0.0;
-    for (int i = 0; i < m; ++i) xnorm = std::hypot(xnorm, at(a, n, k + 1 + i, k));
-    if (xnorm == 0.0) continue;
+    // ||a(k+1:n, k)|| with scaling by the largest entry (contiguous column)
+    const double* colk = &a[(size_t)k * n + k + 1];
+    double amax = 0.0;
+    for (int i = 0; i < m; ++i) amax = std::max(amax, std::fabs(colk[i]));
+    if (amax == 0.0) continue;
+    double ss = 0.0;
+    const double ia = 1.0 / amax;
+#pragma omp simd reduction(+ : ss)
+    for (int i = 0; i < m; ++i) ss += (colk[i] * ia) * (colk[i] * ia);
+    const double xnorm = amax * std::sqrt(ss);
     const double x0 = at(a, n, k + 1, k);
     const double alpha = x0 > 0 ? -xnorm : xnorm;
     for (int i = 0; i < m; ++i) v[i] = at(a, n, k + 1 + i, k);
@@ -162,24 +169,44 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
     for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
     if (vn2 == 0.0) continue;
     const double beta = 2.0 / vn2;
-    // p = beta * A22 v  (A22 symmetric: p_i = beta * sum_j a(k+1+j, k+1+i) v_j, column i contiguous)
-#pragma omp parallel for if (par) schedule(static)
-    for (int i = 0; i < m; ++i) p[i] = beta * dotc(&a[(size_t)(k + 1 + i) * n + k + 1], v.data(), m);
+    // p = beta * A22 v from the lower triangle of A22 (column j holds A22(i, j), i >= j,
+    // contiguously): column j gives p_j its inner product with v[j..] and adds
+    // A22(i, j) v_j to p_i, i > j (per-thread partial vectors, summed afterwards)
+    std::fill(p.begin(), p.begin() + m, 0.0);
+    const bool parm = par && m >= 96;
+#pragma omp parallel if (parm)
+    {
+      std::vector<double> pt(m, 0.0);
+#pragma omp for schedule(dynamic, 16) nowait
+      for (int j = 0; j < m; ++j) {
+        const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
+        const double vj = v[j];
+        double sj = 0.0;
+#pragma omp simd reduction(+ : sj)
+        for (int i = j; i < m; ++i) {
+          sj += col[i] * v[i];
+          pt[i] += col[i] * vj;
+        }
+        pt[j] += sj - col[j] * vj;  // the diagonal entry counted once
+      }
+#pragma omp critical
+      for (int i = 0; i < m; ++i) p[i] += pt[i];
+    }
+    for (int i = 0; i < m; ++i) p[i] *= beta;
     const double pv = dotc(p.data(), v.data(), m);
     const double K = 0.5 * beta * pv;
     for (int i = 0; i < m; ++i) wv[i] = p[i] - K * v[i];
-#pragma omp parallel for if (par) schedule(static)
+    // rank-2 update of the lower triangle: A22 -= v wv^T + wv v^T
+#pragma omp parallel for if (parm) schedule(dynamic, 16)
     for (int j = 0; j < m; ++j) {
       double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
       const double vj = v[j], wj = wv[j];
-      for (int i = 0; i < m; ++i) col[i] -= v[i] * wj + wv[i] * vj;
+#pragma omp simd
+      for (int i = j; i < m; ++i) col[i] -= v[i] * wj + wv[i] * vj;
     }
+    // only the lower triangle is kept up to date: the subdiagonal entry is all
+    // that later steps read of column k
     at(a, n, k + 1, k) = alpha;
-    at(a, n, k, k + 1) = alpha;
-    for (int i = k + 2; i < n; ++i) {
-      at(a, n, i, k) = 0.0;
-      at(a, n, k, i) = 0.0;
-    }
     if (vec) {
       std::copy(v.begin(), v.begin() + m, hv.begin() + hoff[k]);
       hbeta[k] = beta;
