@@ -18,6 +18,9 @@
 #include <cmath>
 #include <cstdint>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "dense.cuh"
 
@@ -145,7 +148,7 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
     hbeta.assign(n, 0.0);
     hoff.assign(n, 0);
   }
-  std::vector<double> v(n), p(n), wv(n);
+  std::vector<double> v(n), p(n), wv(n), pbuf;
   size_t voff = 0;
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
@@ -172,12 +175,23 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
     // p = beta * A22 v from the lower triangle of A22 (column j holds A22(i, j), i >= j,
     // contiguously): column j gives p_j its inner product with v[j..] and adds
     // A22(i, j) v_j to p_i, i > j (per-thread partial vectors, summed afterwards)
+    // (static cyclic column assignment and a thread-ordered sum keep the result
+    // bitwise reproducible)
     std::fill(p.begin(), p.begin() + m, 0.0);
     const bool parm = par && m >= 96;
-#pragma omp parallel if (parm)
+    int nt = 1;
+#ifdef _OPENMP
+    if (parm) nt = omp_get_max_threads();
+#endif
+    pbuf.assign((size_t)nt * m, 0.0);
+#pragma omp parallel num_threads(nt) if (parm)
     {
-      std::vector<double> pt(m, 0.0);
-#pragma omp for schedule(dynamic, 16) nowait
+      int tid = 0;
+#ifdef _OPENMP
+      tid = omp_get_thread_num();
+#endif
+      double* pt = &pbuf[(size_t)tid * m];
+#pragma omp for schedule(static, 16)
       for (int j = 0; j < m; ++j) {
         const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
         const double vj = v[j];
@@ -189,9 +203,9 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
         }
         pt[j] += sj - col[j] * vj;  // the diagonal entry counted once
       }
-#pragma omp critical
-      for (int i = 0; i < m; ++i) p[i] += pt[i];
     }
+    for (int t = 0; t < nt; ++t)
+      for (int i = 0; i < m; ++i) p[i] += pbuf[(size_t)t * m + i];
     for (int i = 0; i < m; ++i) p[i] *= beta;
     const double pv = dotc(p.data(), v.data(), m);
     const double K = 0.5 * beta * pv;
