@@ -256,6 +256,19 @@ struct Alg1Out {
   std::vector<double> QB;  // rq x m = Q_Z^T B
 };
 
+// The basis columns after orth_rr and the coefficients that go with them: with a
+// deferred R^{-1} the basis is the first-pass block in Wb2 and the coefficients
+// S (qp x w, row-major) become R^{-1} S.
+static const double* basis_and_coeffs(const Ref& R, const OrthOut& O, int qp, int w, std::vector<double>& S) {
+  if (O.Rinv.empty() || qp == 0 || w == 0) return R.Wb;
+  std::vector<double> St((size_t)w * qp), RS((size_t)qp * w);
+  for (int i = 0; i < qp; ++i)
+    for (int j = 0; j < w; ++j) St[(size_t)j * qp + i] = S[(size_t)i * w + j];
+  host_gemm_nt(qp, w, qp, O.Rinv.data(), qp, St.data(), qp, nullptr, RS.data(), w, false);
+  S.swap(RS);
+  return R.Wb2;
+}
+
 // Residual factor decomposition (Algorithm 1) in FP64 for Z = Q_Z T_Z:
 // F = [Z, A^T Z, Z Z^T B, C^T] is expressed in the orthonormal basis
 // [Q_Z, Q_perp], where Q_perp spans the part of [A^T Z, C^T] outside range(Q_Z)
@@ -284,7 +297,8 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
     for (int i = 0; i < rq; ++i) s += Cw[(size_t)i * q1 + j] * Cw[(size_t)i * q1 + j];
     fl[j] = 1e-28 * s;
   }
-  OrthOut O = orth_rr<double>(c, n, q1, R.Wb, R.ldbig, R.Wb2, R.ldbig, 1e-12, &fl, true, 0, nullptr, 0);
+  OrthOut O = orth_rr<double>(c, n, q1, R.Wb, R.ldbig, R.Wb2, R.ldbig, 1e-12, &fl, true, 0, nullptr, 0,
+                              Cout != nullptr);
   const int qp = O.rank;
   const int rt = rq + qp;
   // T blocks, each rt x (r | r | m | p), row-major
@@ -361,7 +375,10 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
     }
   }
   gemm_ts<double, To>(n, rq, cw, 1.0, R.QZ, R.ldq, upload(c, S1), cw, 0.0, Cout, ldco, c.s);
-  if (qp) gemm_ts<double, To>(n, qp, cw, 1.0, R.Wb, R.ldbig, upload(c, S2), cw, 1.0, Cout, ldco, c.s);
+  if (qp) {
+    const double* Vb = basis_and_coeffs(R, O, qp, cw, S2);
+    gemm_ts<double, To>(n, qp, cw, 1.0, Vb, R.ldbig, upload(c, S2), cw, 1.0, Cout, ldco, c.s);
+  }
   return o;
 }
 
@@ -387,7 +404,7 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
     for (int i = 0; i < r; ++i) s += Cy[(size_t)i * ny + j] * Cy[(size_t)i * ny + j];
     fl[j] = 1e-28 * s;
   }
-  OrthOut O = orth_rr<double>(c, n, ny, R.Wb, R.ldbig, R.Wb2, R.ldbig, 1e-12, &fl, true, 0, nullptr, 0);
+  OrthOut O = orth_rr<double>(c, n, ny, R.Wb, R.ldbig, R.Wb2, R.ldbig, 1e-12, &fl, true, 0, nullptr, 0, true);
   const int qp = O.rank, rt = r + qp, sc = r + ny;
   // Gamma (rt x sc) and P = Gamma N Gamma^T
   std::vector<double> Gam((size_t)rt * sc, 0.0), Nd(sc);
@@ -428,7 +445,8 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
   }
   if (rn) {
     if (r) gemm_ts<double, double>(n, r, rn, 1.0, R.QZ, R.ldq, upload(c, S1), rn, 0.0, R.QZn, R.ldq, c.s);
-    gemm_ts<double, double>(n, qp, rn, 1.0, R.Wb, R.ldbig, upload(c, S2), rn, r ? 1.0 : 0.0, R.QZn, R.ldq, c.s);
+    const double* Vb = basis_and_coeffs(R, O, qp, rn, S2);
+    gemm_ts<double, double>(n, qp, rn, 1.0, Vb, R.ldbig, upload(c, S2), rn, r ? 1.0 : 0.0, R.QZn, R.ldq, c.s);
   }
   std::swap(R.QZ, R.QZn);
   R.r = rn;

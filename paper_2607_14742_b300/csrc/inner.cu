@@ -89,7 +89,8 @@ template std::vector<double> gram_h<double>(Ctx&, long, int, int, const double*,
 // ------------------------------------------------------------ orth_rr -----
 template <class T>
 OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double drop_rel,
-                const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo) {
+                const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo,
+                bool defer_rinv) {
   OrthOut o;
   CARE_REQUIRE(out == nullptr || !second_pass, CARE_ERR_INVALID_ARG, "orth_rr: out needs one pass");
   if (cols == 0) return o;
@@ -164,7 +165,10 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   for (int a = 0; a < r1; ++a)
     for (int b = 0; b < r1; ++b) Rrm[(size_t)a * r1 + b] = R[(size_t)b * r1 + a];
   host_upper_inverse(r1, Rrm.data(), Rinv.data());
-  gemm_ts<T, T>(n, r1, r1, 1.0, buf, ldb, upload(c, Rinv), r1, 0.0, X, ldx, c.s);
+  if (defer_rinv)
+    o.Rinv = Rinv;  // basis = buf * Rinv, formed by the caller's product
+  else
+    gemm_ts<T, T>(n, r1, r1, 1.0, buf, ldb, upload(c, Rinv), r1, 0.0, X, ldx, c.s);
   o.rank = r1;
   o.T.assign((size_t)r1 * cols, 0.0);
 #pragma omp parallel for if ((long)r1 * r1 * cols > 1000000) schedule(dynamic, 4)
@@ -178,9 +182,9 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   return o;
 }
 template OrthOut orth_rr<float>(Ctx&, long, int, float*, int, float*, int, double, const std::vector<double>*,
-                                bool, int, float*, int);
+                                bool, int, float*, int, bool);
 template OrthOut orth_rr<double>(Ctx&, long, int, double*, int, double*, int, double,
-                                 const std::vector<double>*, bool, int, double*, int);
+                                 const std::vector<double>*, bool, int, double*, int, bool);
 
 template <class T>
 std::vector<double> cgs2(Ctx& c, long n, const T* Q, int ldq, int r, T* X, int ldx, int cols) {

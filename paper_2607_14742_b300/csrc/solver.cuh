@@ -53,12 +53,19 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
 // host) gives per-column squared norms below which a column counts as zero.
 struct OrthOut {
   int rank = 0;
-  std::vector<double> T;  // rank x cols
+  std::vector<double> T;     // rank x cols
+  std::vector<double> Rinv;  // non-empty: the basis is buf * Rinv (rank x rank, row-major), see defer_rinv
 };
 // With `out` (one pass only) the basis is written there and X is left intact.
+// defer_rinv (second pass only): the last product of the Cholesky QR, basis =
+// Y1 R^{-1}, is not formed; Y1 is left in buf and R^{-1} returned in Rinv, for
+// callers that only multiply the basis by a small matrix S (they form
+// Y1 (R^{-1} S) instead, saving an n x rank x rank product).  If the second
+// Cholesky fails, the basis is formed in X as without the flag and Rinv is empty.
 template <class T>
 OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double drop_rel,
-                const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo);
+                const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo,
+                bool defer_rinv = false);
 
 // X (n x cols) -= Q (Q^T X) twice (classical Gram-Schmidt with
 // reorthogonalisation); returns the r x cols coefficients.
