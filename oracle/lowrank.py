@@ -3,9 +3,13 @@
 Test infrastructure only (see ``oracle/__init__.py``).
 
 Everything is float64 (the paper's u_s = u = u_r = u_c = FP64 setting,
-Section 5).  Shifted solves use a sparse (SuperLU) or dense (LAPACK) LU
-factorisation of M_p = (A + p I)^T, complex when p is complex; the feedback term
-of the closed-loop matrix A_k = A - B K^T is removed with the
+Section 5) unless an inner precision u_s = FP32 is asked for (``inner="fp32"``):
+then NLR-ADI and the correction LR-ADI solves run in IEEE single precision
+(float32 / complex64 arrays, so numpy and LAPACK compute in single precision),
+as in the FP32 rows of Section 5.1, while Algorithms 1 and 2 stay in float64.
+Shifted solves use a sparse (SuperLU) or dense (LAPACK) LU factorisation of
+M_p = (A + p I)^T, complex when p is complex; the feedback term of the
+closed-loop matrix A_k = A - B K^T is removed with the
 Sherman-Morrison-Woodbury formula of Section 4.
 
 Readings of points the paper leaves open (each is a named choice here):
@@ -38,17 +42,20 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 U_FP64 = 2.0 ** -53
+INNER_DTYPES = {"fp64": (np.float64, np.complex128), "fp32": (np.float32, np.complex64)}
 
 
 class ShiftedSolver:
-    """Applies M_p^{-1} with M_p = (A + p I)^T = A^T + p I (Section 4, SMW formula)."""
+    """Applies M_p^{-1} with M_p = (A + p I)^T = A^T + p I (Section 4, SMW formula),
+    in the inner precision ``inner`` ("fp64" or "fp32")."""
 
-    def __init__(self, A, dense: bool = False):
+    def __init__(self, A, dense: bool = False, inner: str = "fp64"):
         self.dense = dense
+        self.rdt, self.cdt = INNER_DTYPES[inner]
         if dense:
-            self.At = np.asarray(A.T if not sp.issparse(A) else A.T.toarray(), dtype=float)
+            self.At = np.asarray(A.T if not sp.issparse(A) else A.T.toarray(), dtype=float).astype(self.rdt)
         else:
-            self.At = sp.csc_matrix(A.T)
+            self.At = sp.csc_matrix(A.T).astype(self.rdt)
         self.n = self.At.shape[0]
         self._cache = {}
         self.nsolves = 0
@@ -58,13 +65,14 @@ class ShiftedSolver:
         if key in self._cache:
             return self._cache[key]
         self._cache.clear()
+        dt = self.cdt if np.imag(p) != 0 else self.rdt
         if self.dense:
-            M = self.At + p * np.eye(self.n)
+            M = (self.At + np.asarray(p, dtype=dt) * np.eye(self.n, dtype=dt)).astype(dt)
             f = sla.lu_factor(M)
             solve = lambda R, f=f: sla.lu_solve(f, R)
         else:
-            M = (self.At + p * sp.identity(self.n, format="csc")).tocsc()
-            f = spla.splu(M.astype(complex) if np.iscomplexobj(p) or np.imag(p) != 0 else M)
+            M = (self.At.astype(dt) + np.asarray(p, dtype=dt) * sp.identity(self.n, format="csc", dtype=dt)).tocsc()
+            f = spla.splu(M)
             solve = f.solve
         self._cache[key] = solve
         return solve
@@ -73,7 +81,7 @@ class ShiftedSolver:
         self.nsolves += 1
         p = complex(p) if np.imag(p) != 0 else float(np.real(p))
         solve = self._factor(p)
-        R = np.asarray(R, dtype=complex if isinstance(p, complex) else float)
+        R = np.asarray(R, dtype=self.cdt if isinstance(p, complex) else self.rdt)
         return solve(R)
 
 
@@ -86,9 +94,10 @@ def smw_solve(solver: ShiftedSolver, B, K, p, W):
     if K is None or not np.any(K):
         return V0
     Y = solver.solve(p, K)
-    m = B.shape[1]
-    S = np.eye(m) - B.T @ Y
-    return V0 + Y @ np.linalg.solve(S, B.T @ V0)
+    Bt = np.asarray(B, dtype=Y.real.dtype).T
+    m = Bt.shape[0]
+    S = np.eye(m, dtype=Y.dtype) - Bt @ Y
+    return V0 + Y @ np.linalg.solve(S, Bt @ V0)
 
 
 def _orth(X, rtol=1e-12):
@@ -138,7 +147,7 @@ def projection_shifts(A, B, K, U, hmin=4, maxblocks=4):
     return out
 
 
-def lradi(A, B, K, W, tol, jmax=50, solver=None, dense=False, split=None, hmin=4):
+def lradi(A, B, K, W, tol, jmax=50, solver=None, dense=False, split=None, hmin=4, inner="fp64"):
     """LR-ADI for  F X + X F^T + W W^T = 0  with F = A_k^T = A^T - K B^T, X ~ Z Z^T.
 
     Residual-factor form (Section 4 reading): W_0 = W and per shift p_j
@@ -150,13 +159,22 @@ def lradi(A, B, K, W, tol, jmax=50, solver=None, dense=False, split=None, hmin=4
                   Z <- [Z, gamma (Re V_j + delta Im V_j), gamma sqrt(delta^2 + 1) Im V_j].
     Stops when ||W^T W||_2 <= tol ||W_0^T W_0||_2 or after jmax shifts.
 
+    ``inner`` = "fp32" runs every step (solves, W update, Z blocks, the residual
+    norm and the shift computation) in single precision.
+
     ``split`` = number of leading columns of W that belong to the first of two
     jointly solved equations (the +/- correction pair of Framework 1); the
     Z columns are then returned as (Z_first, Z_second).
     """
     if solver is None:
-        solver = ShiftedSolver(A, dense=dense)
-    W = np.array(W, dtype=float)
+        solver = ShiftedSolver(A, dense=dense, inner=inner)
+    rdt = solver.rdt
+    W = np.array(W, dtype=rdt)
+    if rdt != np.float64:
+        # the inner equation as u_s holds it: A_k's data rounded to u_s
+        A = A.astype(rdt) if sp.issparse(A) else np.asarray(A).astype(rdt)
+        B = np.asarray(B).astype(rdt)
+        K = None if K is None else np.asarray(K).astype(rdt)
     n, b = W.shape
     w0 = np.linalg.norm(W.T @ W, 2)
     blocks = []
@@ -174,55 +192,58 @@ def lradi(A, B, K, W, tol, jmax=50, solver=None, dense=False, split=None, hmin=4
         used.append(p)
         V = smw_solve(solver, B, K, p, W)
         if p.imag == 0.0:
-            pr = p.real
+            pr = rdt(p.real)
             V = V.real if np.iscomplexobj(V) else V
-            W = W - 2.0 * pr * V
-            blk = math.sqrt(-2.0 * pr) * V
+            W = W - rdt(2.0) * pr * V
+            blk = rdt(math.sqrt(-2.0 * p.real)) * V
             blocks.append([blk])
             last_block = blk
             j += 1
         else:
-            gam = 2.0 * math.sqrt(-p.real)
-            dlt = p.real / p.imag
+            gam = rdt(2.0 * math.sqrt(-p.real))
+            dlt = rdt(p.real / p.imag)
             Vr, Vi = V.real, V.imag
             W = W + gam * gam * (Vr + dlt * Vi)
             b1 = gam * (Vr + dlt * Vi)
-            b2 = gam * math.sqrt(dlt * dlt + 1.0) * Vi
+            b2 = gam * rdt(math.sqrt(float(dlt) * float(dlt) + 1.0)) * Vi
             blocks.append([b1, b2])
             last_block = np.hstack([b1, b2])
             j += 2
         res_hist.append(np.linalg.norm(W.T @ W, 2) / w0 if w0 > 0 else 0.0)
     cols = [c for blk in blocks for c in blk]
-    Z = np.hstack(cols) if cols else np.zeros((n, 0))
+    Z = np.hstack(cols) if cols else np.zeros((n, 0), dtype=rdt)
     info = dict(steps=j, shifts=used, res_hist=np.array(res_hist), nsolves=solver.nsolves)
     if split is None:
         return Z, info
-    Zp = np.hstack([c[:, :split] for c in cols]) if cols else np.zeros((n, 0))
-    Zm = np.hstack([c[:, split:] for c in cols]) if cols else np.zeros((n, 0))
+    Zp = np.hstack([c[:, :split] for c in cols]) if cols else np.zeros((n, 0), dtype=rdt)
+    Zm = np.hstack([c[:, split:] for c in cols]) if cols else np.zeros((n, 0), dtype=rdt)
     return (Zp, Zm), info
 
 
-def nlradi(A, B, C, tol_lyap=1e-12, tol_newton=1e-12, kmax=20, jmax=50, dense=False):
+def nlradi(A, B, C, tol_lyap=1e-12, tol_newton=1e-12, kmax=20, jmax=50, dense=False, inner="fp64"):
     """NLR-ADI initial approximation (Section 4 reading): Newton-Kleinman whose
     step i solves A_i^T X + X A_i + C^T C + K_i K_i^T = 0, A_i = A - B K_i^T,
-    by LR-ADI with right-hand side factor [C^T, K_i]; K_{i+1} = Z Z^T B."""
+    by LR-ADI with right-hand side factor [C^T, K_i]; K_{i+1} = Z Z^T B.
+    With inner="fp32" every step runs in single precision (Z, K included)."""
     n, m = B.shape
-    solver = ShiftedSolver(A, dense=dense)
-    K = np.zeros((n, m))
-    inner = 0
-    Z = np.zeros((n, 0))
+    solver = ShiftedSolver(A, dense=dense, inner=inner)
+    rdt = solver.rdt
+    Bs, Cs = np.asarray(B).astype(rdt), np.asarray(C).astype(rdt)
+    K = np.zeros((n, m), dtype=rdt)
+    inner_steps = 0
+    Z = np.zeros((n, 0), dtype=rdt)
     steps = 0
     for i in range(kmax):
-        W = C.T if not np.any(K) else np.hstack([C.T, K])
-        Z, info = lradi(A, B, K, W, tol_lyap, jmax, solver=solver)
-        inner += info["steps"]
+        W = Cs.T if not np.any(K) else np.hstack([Cs.T, K])
+        Z, info = lradi(A, Bs, K, W, tol_lyap, jmax, solver=solver, inner=inner)
+        inner_steps += info["steps"]
         steps = i + 1
-        Knew = Z @ (Z.T @ B)
+        Knew = Z @ (Z.T @ Bs)
         dk = np.linalg.norm(Knew - K)
         K = Knew
         if dk <= tol_newton * np.linalg.norm(Knew):
             break
-    return Z, dict(newton_steps=steps, adi_steps=inner)
+    return Z, dict(newton_steps=steps, adi_steps=inner_steps)
 
 
 def residual_factor(A, B, C, Z, eta_r_rel=1e-4):
@@ -288,8 +309,10 @@ def res_paper(A, B, C, Z, res_fro):
 
 
 def framework1(A, B, C, tau_R=1e-12, kmax=20, jmax=50, tol_lyap=1e-12, tol_newton=1e-12,
-               eta_r_rel=1e-4, eta_s_mult=10.0, stag=0.999, dense=False, Z1=None):
-    """Framework 1 (Factorization-based Newton iterative refinement), Section 2, in FP64.
+               eta_r_rel=1e-4, eta_s_mult=10.0, stag=0.999, dense=False, Z1=None, inner="fp64"):
+    """Framework 1 (Factorization-based Newton iterative refinement), Section 2, with
+    the inner solves (NLR-ADI and the correction LR-ADI) in ``inner`` precision and
+    Algorithms 1-2 in FP64.
 
     1. Z_1 from NLR-ADI (unless given).
     2. For k = 1..kmax: Algorithm 1 -> C+, C-, ||R(Z_k)||_F; stop if
@@ -298,13 +321,14 @@ def framework1(A, B, C, tau_R=1e-12, kmax=20, jmax=50, tol_lyap=1e-12, tol_newto
        K_k = Z_k Z_k^T B, as one LR-ADI run on [C+, C-]; Algorithm 2 -> Z_{k+1}.
     """
     if Z1 is None:
-        Z, init = nlradi(A, B, C, tol_lyap, tol_newton, kmax, jmax, dense=dense)
+        Z, init = nlradi(A, B, C, tol_lyap, tol_newton, kmax, jmax, dense=dense, inner=inner)
+        Z = np.asarray(Z, dtype=float)  # stored in u = FP64
     else:
         Z, init = np.array(Z1, float), dict(newton_steps=0, adi_steps=0)
     ctc = np.linalg.norm(C @ C.T)
-    solver = ShiftedSolver(A, dense=dense)
+    solver = ShiftedSolver(A, dense=dense, inner=inner)
     hist = []
-    inner = 0
+    inner_steps = 0
     status = "not_converged"
     outer = 0
     for k in range(1, kmax + 1):
@@ -319,11 +343,11 @@ def framework1(A, B, C, tau_R=1e-12, kmax=20, jmax=50, tol_lyap=1e-12, tol_newto
             break
         K = Z @ (Z.T @ B)
         (Zp, Zm), info = lradi(A, B, K, np.hstack([Cp, Cm]), tol_lyap, jmax, solver=solver,
-                               split=Cp.shape[1])
-        inner += info["steps"]
-        Z, _ = solution_factor(Z, Zp, Zm, eta_s_mult)
+                               split=Cp.shape[1], inner=inner)
+        inner_steps += info["steps"]
+        Z, _ = solution_factor(Z, np.asarray(Zp, float), np.asarray(Zm, float), eta_s_mult)
     return Z, dict(status=status, res_hist=np.array(hist), rel_res=hist[-1] / ctc,
-                   iter0=(init["newton_steps"], init["adi_steps"]), iter=(outer, inner),
+                   iter0=(init["newton_steps"], init["adi_steps"]), iter=(outer, inner_steps),
                    rank=Z.shape[1], res_paper=res_paper(A, B, C, Z, hist[-1]))
 
 

@@ -183,3 +183,31 @@ def test_table1_example1_fp64():
         assert abs(info["iter0"][0] - case["iter0"][0]) <= 3
         assert abs(info["iter"][0] - case["iter"][0]) <= 1
         assert abs(info["rank"] - case["rank"]) <= 3
+
+
+@pytest.mark.slow
+def test_table1_example1_fp32_conditioning_threshold():
+    """Golden (Section 5.1, Table 1, FP32 rows, and the text after it): with NLR-ADI and
+    the correction solves in single precision (dense direct shifted solves) and
+    Algorithms 1-2 in FP64, the refinement reaches the paper's Res level in the paper's
+    number of refinement steps at kappa_2(A) = 1e2, while at kappa_2(A) = 1e8 it does not
+    converge: after the same few steps its relative residual is still orders of magnitude
+    above the converged one (the conditioning threshold d1 kappa_F(L_k) u_s < 1 of
+    Theorem 1 is crossed)."""
+    g = json.load(open(os.path.join(GOLD, "table1_example1_fp32.json")))
+    case = next(c for c in g["cases"] if c["q"] == 2.0)
+    p = ci.paper_example1(q=case["q"])
+    Z, info = ol.framework1(p.A.to_dense(), p.B, p.C, tau_R=1e-14, dense=True, inner="fp32",
+                            tol_lyap=1e-5, tol_newton=1e-5)
+    assert info["status"] == "ok"
+    assert info["res_paper"] <= 10 * case["res"]
+    assert abs(info["iter"][0] - case["iter"][0]) <= 1
+    assert info["rel_res"] <= 1e-14
+    bad = g["fails_to_converge"][0]
+    p8 = ci.paper_example1(q=bad["q"])
+    A8 = p8.A.to_dense()
+    Z1, _ = ol.nlradi(A8, p8.B, p8.C, tol_lyap=1e-5, tol_newton=1e-5, dense=True, inner="fp32")
+    Z8, info8 = ol.framework1(A8, p8.B, p8.C, tau_R=1e-14, dense=True, inner="fp32", tol_lyap=1e-5,
+                              kmax=case["iter"][0] + 2, Z1=np.asarray(Z1, float))
+    assert info8["status"] != "ok"
+    assert info8["rel_res"] >= 1e5 * info["rel_res"]
