@@ -202,6 +202,56 @@ def test_host_eigvals_structured():
     assert np.allclose(np.sort(pb.host_eigvals(T).real), np.sort(np.diag(T)))
 
 
+def test_entry_points_reject_invalid_arguments_before_any_device_work():
+    """Every entry point checks its arguments first and returns CARE_ERR_INVALID_ARG
+    (status 1) without touching a device, so these calls are safe on a host with no GPU."""
+    import ctypes as ct
+    L = pb.lib()
+    INVALID = 1
+    sz = ct.c_size_t(0)
+    op0 = pb.op_t()
+    bad_csr = pb.csr_t(-1, 0, None, None, None)
+    ok_csr = pb.csr_t(4, 4, 16, 16, 16)  # never dereferenced: another argument is invalid
+    o = pb.default_options()
+    dummy = ct.c_void_p(256)
+    cases = {
+        "op_size n<0": L.care_op_size(-1, 0, ct.byref(sz)),
+        "op_size null": L.care_op_size(4, 3, None),
+        "op_prepare null A": L.care_op_prepare(None, dummy, 0, None, ct.byref(op0)),
+        "op_prepare n<0": L.care_op_prepare(ct.byref(bad_csr), dummy, 0, None, ct.byref(op0)),
+        "spmm dtype": L.care_spmm(ct.byref(op0), 2, 0, 0.0, 0.0, None, 4, 4, None, 4, None),
+        "spmm real with imaginary shift": L.care_spmm(ct.byref(op0), 0, 0, 0.0, 1.0, None, 4, 4, None, 4, None),
+        "gram n<0": L.care_gram(0, -1, 2, 2, dummy, 2, dummy, 2, dummy, 2, dummy, 1024, None),
+        "gram dtype": L.care_gram(3, 10, 2, 2, dummy, 2, dummy, 2, dummy, 2, dummy, 1024, None),
+        "gram ldx<a": L.care_gram(0, 10, 3, 2, dummy, 2, dummy, 2, dummy, 2, dummy, 1024, None),
+        "gram null G": L.care_gram(0, 10, 2, 2, dummy, 2, dummy, 2, None, 2, dummy, 1024, None),
+        "gram_noalloc over limit": L.care_gram_noalloc(0, 10, 1100, 1000, dummy, 1100, dummy, 1000, dummy, 1000,
+                                                       None),
+        "shifted ws null op": L.care_shifted_solve_workspace_size(None, 1, 2, 1, ct.byref(o), ct.byref(sz)),
+        "workspace n<0": L.care_workspace_size(-1, 0, 1, 1, 8, 1, ct.byref(o), ct.byref(sz)),
+        "workspace r_cap 0": L.care_workspace_size(4, 4, 1, 1, 0, 1, ct.byref(o), ct.byref(sz)),
+        "solve null A": L.care_solve(None, dummy, 4, 1, dummy, 1, 1, 1e-10, 1, ct.byref(o), dummy, 4, 8, dummy,
+                                     1024, None, None),
+        "solve null B": L.care_solve(ct.byref(ok_csr), None, 4, 1, dummy, 1, 1, 1e-10, 1, ct.byref(o), dummy, 4,
+                                     8, dummy, 1024, None, None),
+        "solve tol 0": L.care_solve(ct.byref(ok_csr), dummy, 4, 1, dummy, 1, 1, 0.0, 1, ct.byref(o), dummy, 4, 8,
+                                    dummy, 1024, None, None),
+        "lradi null A": L.lyap_lradi(None, None, 4, None, 4, 0, dummy, 4, 1, 1e-5, 1, ct.byref(o), dummy, 4, 8,
+                                     dummy, 1024, None, None),
+        "resfac null A": L.care_residual_factor(None, dummy, 4, 1, dummy, 1, 1, dummy, 4, 1, 1e-4, None, 4, None,
+                                                None, 4, None, 8, None, dummy, 1024, None),
+        "autotune null op": L.care_autotune(None, 1, 2, 1, ct.byref(o), dummy, 1024, None, None),
+        "batched workspace 0 workers": L.care_workspace_size_batched(1, None, None, None, None, 1, ct.byref(o), 0,
+                                                                     ct.byref(sz)),
+        "batched count<0": L.care_solve_batched(-1, None, None, None, None, None, None, None, 1e-10, 1,
+                                                ct.byref(o), None, None, None, 1, None, 0, None, None),
+        "host symeig n<0": L.care_host_symeig(-1, None, None, None),
+        "host gemm sym m!=n": L.care_host_gemm_nt(3, 2, 1, dummy, 1, dummy, 1, None, dummy, 2, 1),
+    }
+    bad = {k: v for k, v in cases.items() if v != INVALID}
+    assert not bad, bad
+
+
 def test_workspace_size_grows_with_problem():
     a = pb.workspace_size(400, 1920, 1, 1, 64, "mixed")
     b = pb.workspace_size(250000, 1248000, 5, 5, 512, "mixed")
