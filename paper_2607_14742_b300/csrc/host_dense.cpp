@@ -140,7 +140,14 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
   const bool vec = V != nullptr;
   const bool par = n >= 96;
   // 1. Householder tridiagonalisation A <- H_k A H_k, H_k = I - beta_k v_k v_k^T with
-  //    v_k supported on k+1..n-1; the reflectors are kept for the eigenvectors
+  //    v_k supported on k+1..n-1 (Alg. 8.3.1); the reflectors are kept for the
+  //    eigenvectors.  Panels of TRI_NB reflectors (the blocked form of the same
+  //    reduction, as in LAPACK's dsytrd): within a panel the trailing matrix is not
+  //    updated; each column is brought up to date from the panel's (v_t, w_t) just
+  //    before its reflector is formed, and p = beta A v is corrected by the same
+  //    terms.  After the panel the trailing lower triangle receives all of its
+  //    rank-2 updates A -= V W^T + W V^T in one pass.
+  constexpr int TRI_NB = 32;
   std::vector<double> hv, hbeta;
   std::vector<size_t> hoff;
   if (vec) {
@@ -149,81 +156,116 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
     hoff.assign(n, 0);
   }
   std::vector<double> v(n), p(n), wv(n), pbuf;
+  std::vector<double> Vp((size_t)TRI_NB * n), Wp((size_t)TRI_NB * n), y1(TRI_NB), y2(TRI_NB);
   size_t voff = 0;
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;
-    if (vec) hoff[k] = voff;
-    voff += m;
-    // ||a(k+1:n, k)|| with scaling by the largest entry (contiguous column)
-    const double* colk = &a[(size_t)k * n + k + 1];
-    double amax = 0.0;
-    for (int i = 0; i < m; ++i) amax = std::max(amax, std::fabs(colk[i]));
-    if (amax == 0.0) continue;
-    double ss = 0.0;
-    const double ia = 1.0 / amax;
+  for (int k0 = 0; k0 + 2 < n; k0 += TRI_NB) {
+    const int kend = std::min(k0 + TRI_NB, n - 2);  // reflectors k0 .. kend-1
+    std::fill(Vp.begin(), Vp.end(), 0.0);
+    std::fill(Wp.begin(), Wp.end(), 0.0);
+    for (int k = k0; k < kend; ++k) {
+      const int jj = k - k0;
+      const int m = n - k - 1;
+      if (vec) hoff[k] = voff;
+      voff += m;
+      // column k (rows k..n-1) with the panel's earlier rank-2 updates applied
+      double* colfull = &a[(size_t)k * n];
+      for (int t = 0; t < jj; ++t) {
+        const double wk = Wp[(size_t)t * n + k], vk = Vp[(size_t)t * n + k];
+        const double* vt = &Vp[(size_t)t * n];
+        const double* wt = &Wp[(size_t)t * n];
+#pragma omp simd
+        for (int g = k; g < n; ++g) colfull[g] -= vt[g] * wk + wt[g] * vk;
+      }
+      // ||a(k+1:n, k)|| with scaling by the largest entry (contiguous column)
+      const double* colk = colfull + k + 1;
+      double amax = 0.0;
+      for (int i = 0; i < m; ++i) amax = std::max(amax, std::fabs(colk[i]));
+      if (amax == 0.0) continue;
+      double ss = 0.0;
+      const double ia = 1.0 / amax;
 #pragma omp simd reduction(+ : ss)
-    for (int i = 0; i < m; ++i) ss += (colk[i] * ia) * (colk[i] * ia);
-    const double xnorm = amax * std::sqrt(ss);
-    const double x0 = at(a, n, k + 1, k);
-    const double alpha = x0 > 0 ? -xnorm : xnorm;
-    for (int i = 0; i < m; ++i) v[i] = at(a, n, k + 1 + i, k);
-    v[0] -= alpha;
-    double vn2 = 0.0;
-    for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
-    if (vn2 == 0.0) continue;
-    const double beta = 2.0 / vn2;
-    // p = beta * A22 v from the lower triangle of A22 (column j holds A22(i, j), i >= j,
-    // contiguously): column j gives p_j its inner product with v[j..] and adds
-    // A22(i, j) v_j to p_i, i > j (per-thread partial vectors, summed afterwards)
-    // (static cyclic column assignment and a thread-ordered sum keep the result
-    // bitwise reproducible)
-    std::fill(p.begin(), p.begin() + m, 0.0);
-    const bool parm = par && m >= 96;
-    int nt = 1;
+      for (int i = 0; i < m; ++i) ss += (colk[i] * ia) * (colk[i] * ia);
+      const double xnorm = amax * std::sqrt(ss);
+      const double x0 = colk[0];
+      const double alpha = x0 > 0 ? -xnorm : xnorm;
+      for (int i = 0; i < m; ++i) v[i] = colk[i];
+      v[0] -= alpha;
+      const double vn2 = dotc(v.data(), v.data(), m);
+      if (vn2 == 0.0) continue;
+      const double beta = 2.0 / vn2;
+      // p = A22 v from the stored lower triangle of A22 (column j holds A22(i, j),
+      // i >= j, contiguously): column j gives p_j its inner product with v[j..]
+      // and adds A22(i, j) v_j to p_i, i > j.  Static cyclic columns and a
+      // thread-ordered sum of the per-thread partial vectors keep the result
+      // bitwise reproducible.
+      std::fill(p.begin(), p.begin() + m, 0.0);
+      const bool parm = par && m >= 96;
+      int nt = 1;
 #ifdef _OPENMP
-    if (parm) nt = omp_get_max_threads();
+      if (parm) nt = omp_get_max_threads();
 #endif
-    pbuf.assign((size_t)nt * m, 0.0);
+      pbuf.assign((size_t)nt * m, 0.0);
 #pragma omp parallel num_threads(nt) if (parm)
-    {
-      int tid = 0;
+      {
+        int tid = 0;
 #ifdef _OPENMP
-      tid = omp_get_thread_num();
+        tid = omp_get_thread_num();
 #endif
-      double* pt = &pbuf[(size_t)tid * m];
+        double* pt = &pbuf[(size_t)tid * m];
 #pragma omp for schedule(static, 16)
-      for (int j = 0; j < m; ++j) {
-        const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
-        const double vj = v[j];
-        double sj = 0.0;
+        for (int j = 0; j < m; ++j) {
+          const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
+          const double vj = v[j];
+          double sj = 0.0;
 #pragma omp simd reduction(+ : sj)
-        for (int i = j; i < m; ++i) {
-          sj += col[i] * v[i];
-          pt[i] += col[i] * vj;
+          for (int i = j; i < m; ++i) {
+            sj += col[i] * v[i];
+            pt[i] += col[i] * vj;
+          }
+          pt[j] += sj - col[j] * vj;  // the diagonal entry counted once
         }
-        pt[j] += sj - col[j] * vj;  // the diagonal entry counted once
+      }
+      for (int t = 0; t < nt; ++t)
+        for (int i = 0; i < m; ++i) p[i] += pbuf[(size_t)t * m + i];
+      // the panel's pending updates: A22 v -= V (W^T v) + W (V^T v)
+      for (int t = 0; t < jj; ++t) {
+        y1[t] = dotc(&Wp[(size_t)t * n + k + 1], v.data(), m);
+        y2[t] = dotc(&Vp[(size_t)t * n + k + 1], v.data(), m);
+      }
+      for (int t = 0; t < jj; ++t) {
+        const double* vt = &Vp[(size_t)t * n + k + 1];
+        const double* wt = &Wp[(size_t)t * n + k + 1];
+        const double a1 = y1[t], a2 = y2[t];
+#pragma omp simd
+        for (int i = 0; i < m; ++i) p[i] -= vt[i] * a1 + wt[i] * a2;
+      }
+      for (int i = 0; i < m; ++i) p[i] *= beta;
+      const double pv = dotc(p.data(), v.data(), m);
+      const double K = 0.5 * beta * pv;
+      for (int i = 0; i < m; ++i) wv[i] = p[i] - K * v[i];
+      std::copy(v.begin(), v.begin() + m, Vp.begin() + (size_t)jj * n + k + 1);
+      std::copy(wv.begin(), wv.begin() + m, Wp.begin() + (size_t)jj * n + k + 1);
+      // only the lower triangle is kept up to date: the subdiagonal entry is all
+      // that later steps read of column k
+      at(a, n, k + 1, k) = alpha;
+      if (vec) {
+        std::copy(v.begin(), v.begin() + m, hv.begin() + hoff[k]);
+        hbeta[k] = beta;
       }
     }
-    for (int t = 0; t < nt; ++t)
-      for (int i = 0; i < m; ++i) p[i] += pbuf[(size_t)t * m + i];
-    for (int i = 0; i < m; ++i) p[i] *= beta;
-    const double pv = dotc(p.data(), v.data(), m);
-    const double K = 0.5 * beta * pv;
-    for (int i = 0; i < m; ++i) wv[i] = p[i] - K * v[i];
-    // rank-2 update of the lower triangle: A22 -= v wv^T + wv v^T
-#pragma omp parallel for if (parm) schedule(dynamic, 16)
-    for (int j = 0; j < m; ++j) {
-      double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
-      const double vj = v[j], wj = wv[j];
+    // trailing lower triangle (columns >= kend): A -= V W^T + W V^T over the panel
+    const int np_ = kend - k0;
+#pragma omp parallel for if (par && n - kend >= 96) schedule(dynamic, 8)
+    for (int j = kend; j < n; ++j) {
+      double* col = &a[(size_t)j * n];
+      for (int t = 0; t < np_; ++t) {
+        const double wj = Wp[(size_t)t * n + j], vj = Vp[(size_t)t * n + j];
+        if (wj == 0.0 && vj == 0.0) continue;
+        const double* vt = &Vp[(size_t)t * n];
+        const double* wt = &Wp[(size_t)t * n];
 #pragma omp simd
-      for (int i = j; i < m; ++i) col[i] -= v[i] * wj + wv[i] * vj;
-    }
-    // only the lower triangle is kept up to date: the subdiagonal entry is all
-    // that later steps read of column k
-    at(a, n, k + 1, k) = alpha;
-    if (vec) {
-      std::copy(v.begin(), v.begin() + m, hv.begin() + hoff[k]);
-      hbeta[k] = beta;
+        for (int g = j; g < n; ++g) col[g] -= vt[g] * wj + wt[g] * vj;
+      }
     }
   }
   std::vector<double> d(n), e(n, 0.0);
