@@ -1,18 +1,25 @@
-"""Conditioning sweep of Section 5.1 (Table 1, Example 1) with the oracle: FP64 and
-FP32 inner solves (dense direct shifted solves), Algorithms 1-2 in FP64.
+"""Conditioning sweeps with the oracle: FP64 and FP32 inner solves (dense direct
+shifted solves), Algorithms 1-2 in FP64.
 
-Test infrastructure (see ``oracle/__init__.py``): prints one markdown table row per
-kappa_2(A) = 10^q and inner precision for the design notes; nothing here is used
-by the GPU path.
+  * Section 5.1 (Table 1, Example 1, n = 1000): kappa_2(A) = 10^q.
+  * ``--dense200``: the n = 200 dense conditioning family of ``care_inputs``
+    (kappa_2(A) ~ 10^k), with the error against the dense Newton solution.
+
+Test infrastructure (see ``oracle/__init__.py``): prints markdown table rows for the
+design notes; nothing here is used by the GPU path.
 
     python -m oracle.table1_fp32_sweep [q ...]
+    python -m oracle.table1_fp32_sweep --dense200 [k ...]
 """
 from __future__ import annotations
 
 import sys
 import time
 
+import numpy as np
+
 import care_inputs as ci
+from oracle import dense as od
 from oracle import lowrank as ol
 
 
@@ -36,5 +43,25 @@ def main(qs):
                   f"{i0[0]}({i0[1]}) | {it[0]}({it[1]}) | {info['rank']} | {s:.0f} |", flush=True)
 
 
+def main_dense200(ks):
+    print("| k | kappa_2(A) | inner | status | Res | rel. residual | error vs dense Newton | Iter | rank |")
+    print("|---|---:|---|---|---:|---:|---:|---|---:|")
+    for k in ks:
+        p = ci.config_dense_conditioning(k)
+        A = p.A.to_dense()
+        X = od.newton_care(A, p.B, p.C)["X"]
+        for inner in ("fp64", "fp32"):
+            tol = 1e-5 if inner == "fp32" else 1e-12
+            Z, info = ol.framework1(A, p.B, p.C, tau_R=1e-12, dense=True, inner=inner, tol_lyap=tol, tol_newton=tol)
+            err = np.linalg.norm(Z @ Z.T - X) / np.linalg.norm(X)
+            print(f"| {k} | {np.linalg.cond(A):.1e} | {inner} | {info['status']} | {info['res_paper']:.1e} | "
+                  f"{info['rel_res']:.1e} | {err:.1e} | {info['iter'][0]}({info['iter'][1]}) | {info['rank']} |",
+                  flush=True)
+
+
 if __name__ == "__main__":
-    main([float(x) for x in sys.argv[1:]] or [1, 2, 3, 4, 5, 6, 7, 8])
+    args = sys.argv[1:]
+    if args and args[0] == "--dense200":
+        main_dense200([int(x) for x in args[1:]] or list(range(7)))
+    else:
+        main([float(x) for x in args] or [1, 2, 3, 4, 5, 6, 7, 8])
