@@ -10,7 +10,7 @@
 
 namespace care {
 
-static int g_verbose = 0;
+static thread_local int g_verbose = 0;  // per calling thread (batched workers solve concurrently)
 int verbose_level() { return g_verbose; }
 void set_verbose(int v) { g_verbose = v; }
 

@@ -1010,10 +1010,32 @@ static void bicg_iteration(const KArgs<T>& a, SpmmArgs<T>& sp, int grid, cudaStr
   CARE_LAUNCH();
 }
 
-// Per-thread, per-device capture stream and fork/join events (created once).
+// Per-thread, per-device capture stream and fork/join events (created once,
+// destroyed when the thread exits: the batched solver's worker threads are
+// short-lived, and every launch on these streams has been synchronised by then).
 struct CaptureRes {
   cudaStream_t cs = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  CaptureRes() = default;
+  CaptureRes(const CaptureRes&) = delete;
+  CaptureRes& operator=(const CaptureRes&) = delete;
+  ~CaptureRes() {
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+// Per-thread, per-device executable graphs of one BiCGStab instantiation,
+// destroyed with the thread for the same reason.
+struct GraphExecCache {
+  cudaGraphExec_t e[64] = {nullptr};
+  GraphExecCache() = default;
+  GraphExecCache(const GraphExecCache&) = delete;
+  GraphExecCache& operator=(const GraphExecCache&) = delete;
+  ~GraphExecCache() {
+    for (cudaGraphExec_t x : e)
+      if (x) cudaGraphExecDestroy(x);
+  }
 };
 static CaptureRes& capture_res() {
   thread_local CaptureRes r[64];
@@ -1047,10 +1069,10 @@ static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, 
   // Capture `poll` iterations once and replay the graph; the executable graph is
   // kept per thread and updated in place when only kernel parameters change.
   const long per_iter = 5 + (PREC == 2 ? 4L * a.tri_sweeps : 0);
-  thread_local cudaGraphExec_t exec_cache[64] = {nullptr};
+  thread_local GraphExecCache exec_cache;
   int dev = 0;
   CARE_CUDA(cudaGetDevice(&dev));
-  cudaGraphExec_t& exec = exec_cache[dev & 63];
+  cudaGraphExec_t& exec = exec_cache.e[dev & 63];
   CaptureRes& cr = capture_res();
   bool graphs = maxit >= poll;
   if (graphs) {
