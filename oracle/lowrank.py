@@ -42,7 +42,37 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 U_FP64 = 2.0 ** -53
-INNER_DTYPES = {"fp64": (np.float64, np.complex128), "fp32": (np.float32, np.complex64)}
+INNER_DTYPES = {"fp64": (np.float64, np.complex128), "fp32": (np.float32, np.complex64),
+                "bf16": (np.float32, np.complex64), "fp16": (np.float32, np.complex64)}
+
+
+def _round_bf16(x):
+    """Round float32 values to the nearest bfloat16 (8 significant bits, ties to even),
+    returned as float32: the IEEE bit pattern's low 16 bits are rounded away."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = ((b + np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000))
+    r = np.where(np.isfinite(x), r, b)  # inf / nan unchanged
+    return r.view(np.float32)
+
+
+def storage_rounding(inner: str):
+    """Lower inner precisions (the paper's future work, Section 6) are modelled as
+    FP32 arithmetic whose stored results -- shifted-solve solutions, ADI residual and
+    factor blocks, K, and the operator's entries -- are rounded to ``inner`` (bf16:
+    8, fp16: 11 significant bits).  Identity for fp32 / fp64."""
+    if inner == "bf16":
+        f = _round_bf16
+    elif inner == "fp16":
+        f = lambda x: np.asarray(x, np.float32).astype(np.float16).astype(np.float32)
+    else:
+        return lambda x: x
+
+    def rnd(x):
+        x = np.asarray(x)
+        if np.iscomplexobj(x):
+            return (f(x.real) + 1j * f(x.imag)).astype(np.complex64)
+        return f(x)
+    return rnd
 
 
 class ShiftedSolver:
@@ -52,10 +82,12 @@ class ShiftedSolver:
     def __init__(self, A, dense: bool = False, inner: str = "fp64"):
         self.dense = dense
         self.rdt, self.cdt = INNER_DTYPES[inner]
+        self.rnd = storage_rounding(inner)
         if dense:
-            self.At = np.asarray(A.T if not sp.issparse(A) else A.T.toarray(), dtype=float).astype(self.rdt)
+            self.At = self.rnd(np.asarray(A.T if not sp.issparse(A) else A.T.toarray(), dtype=float).astype(self.rdt))
         else:
             self.At = sp.csc_matrix(A.T).astype(self.rdt)
+            self.At.data = self.rnd(self.At.data)
         self.n = self.At.shape[0]
         self._cache = {}
         self.nsolves = 0
@@ -82,7 +114,7 @@ class ShiftedSolver:
         p = complex(p) if np.imag(p) != 0 else float(np.real(p))
         solve = self._factor(p)
         R = np.asarray(R, dtype=self.cdt if isinstance(p, complex) else self.rdt)
-        return solve(R)
+        return self.rnd(solve(R))
 
 
 def smw_solve(solver: ShiftedSolver, B, K, p, W):
@@ -97,7 +129,7 @@ def smw_solve(solver: ShiftedSolver, B, K, p, W):
     Bt = np.asarray(B, dtype=Y.real.dtype).T
     m = Bt.shape[0]
     S = np.eye(m, dtype=Y.dtype) - Bt @ Y
-    return V0 + Y @ np.linalg.solve(S, Bt @ V0)
+    return solver.rnd(V0 + Y @ np.linalg.solve(S, Bt @ V0))
 
 
 def _orth(X, rtol=1e-12):
@@ -168,13 +200,17 @@ def lradi(A, B, K, W, tol, jmax=50, solver=None, dense=False, split=None, hmin=4
     """
     if solver is None:
         solver = ShiftedSolver(A, dense=dense, inner=inner)
-    rdt = solver.rdt
-    W = np.array(W, dtype=rdt)
+    rdt, rnd = solver.rdt, solver.rnd
+    W = rnd(np.array(W, dtype=rdt))
     if rdt != np.float64:
         # the inner equation as u_s holds it: A_k's data rounded to u_s
-        A = A.astype(rdt) if sp.issparse(A) else np.asarray(A).astype(rdt)
-        B = np.asarray(B).astype(rdt)
-        K = None if K is None else np.asarray(K).astype(rdt)
+        if sp.issparse(A):
+            A = A.astype(rdt)
+            A.data = rnd(A.data)
+        else:
+            A = rnd(np.asarray(A).astype(rdt))
+        B = rnd(np.asarray(B).astype(rdt))
+        K = None if K is None else rnd(np.asarray(K).astype(rdt))
     n, b = W.shape
     w0 = np.linalg.norm(W.T @ W, 2)
     blocks = []
@@ -194,8 +230,8 @@ def lradi(A, B, K, W, tol, jmax=50, solver=None, dense=False, split=None, hmin=4
         if p.imag == 0.0:
             pr = rdt(p.real)
             V = V.real if np.iscomplexobj(V) else V
-            W = W - rdt(2.0) * pr * V
-            blk = rdt(math.sqrt(-2.0 * p.real)) * V
+            W = rnd(W - rdt(2.0) * pr * V)
+            blk = rnd(rdt(math.sqrt(-2.0 * p.real)) * V)
             blocks.append([blk])
             last_block = blk
             j += 1
@@ -203,9 +239,9 @@ def lradi(A, B, K, W, tol, jmax=50, solver=None, dense=False, split=None, hmin=4
             gam = rdt(2.0 * math.sqrt(-p.real))
             dlt = rdt(p.real / p.imag)
             Vr, Vi = V.real, V.imag
-            W = W + gam * gam * (Vr + dlt * Vi)
-            b1 = gam * (Vr + dlt * Vi)
-            b2 = gam * rdt(math.sqrt(float(dlt) * float(dlt) + 1.0)) * Vi
+            W = rnd(W + gam * gam * (Vr + dlt * Vi))
+            b1 = rnd(gam * (Vr + dlt * Vi))
+            b2 = rnd(gam * rdt(math.sqrt(float(dlt) * float(dlt) + 1.0)) * Vi)
             blocks.append([b1, b2])
             last_block = np.hstack([b1, b2])
             j += 2
@@ -227,8 +263,8 @@ def nlradi(A, B, C, tol_lyap=1e-12, tol_newton=1e-12, kmax=20, jmax=50, dense=Fa
     With inner="fp32" every step runs in single precision (Z, K included)."""
     n, m = B.shape
     solver = ShiftedSolver(A, dense=dense, inner=inner)
-    rdt = solver.rdt
-    Bs, Cs = np.asarray(B).astype(rdt), np.asarray(C).astype(rdt)
+    rdt, rnd = solver.rdt, solver.rnd
+    Bs, Cs = rnd(np.asarray(B).astype(rdt)), rnd(np.asarray(C).astype(rdt))
     K = np.zeros((n, m), dtype=rdt)
     inner_steps = 0
     Z = np.zeros((n, 0), dtype=rdt)
@@ -238,7 +274,7 @@ def nlradi(A, B, C, tol_lyap=1e-12, tol_newton=1e-12, kmax=20, jmax=50, dense=Fa
         Z, info = lradi(A, Bs, K, W, tol_lyap, jmax, solver=solver, inner=inner)
         inner_steps += info["steps"]
         steps = i + 1
-        Knew = Z @ (Z.T @ Bs)
+        Knew = rnd(Z @ (Z.T @ Bs))
         dk = np.linalg.norm(Knew - K)
         K = Knew
         if dk <= tol_newton * np.linalg.norm(Knew):
@@ -342,10 +378,17 @@ def framework1(A, B, C, tau_R=1e-12, kmax=20, jmax=50, tol_lyap=1e-12, tol_newto
             status = "stagnated"
             break
         K = Z @ (Z.T @ B)
-        (Zp, Zm), info = lradi(A, B, K, np.hstack([Cp, Cm]), tol_lyap, jmax, solver=solver,
+        # the correction equation is linear in W W^T: its right-hand side is scaled by a
+        # power of two to O(1) before the inner-precision solve and Z+- unscaled after
+        # (exact in binary arithmetic; it keeps the shrinking residual factors inside the
+        # narrow exponent range of fp16)
+        W = np.hstack([Cp, Cm])
+        wmax = float(np.max(np.abs(W))) if W.size else 0.0
+        sc = 2.0 ** -math.floor(math.log2(wmax)) if wmax > 0 else 1.0
+        (Zp, Zm), info = lradi(A, B, K, sc * W, tol_lyap, jmax, solver=solver,
                                split=Cp.shape[1], inner=inner)
         inner_steps += info["steps"]
-        Z, _ = solution_factor(Z, np.asarray(Zp, float), np.asarray(Zm, float), eta_s_mult)
+        Z, _ = solution_factor(Z, np.asarray(Zp, float) / sc, np.asarray(Zm, float) / sc, eta_s_mult)
     return Z, dict(status=status, res_hist=np.array(hist), rel_res=hist[-1] / ctc,
                    iter0=(init["newton_steps"], init["adi_steps"]), iter=(outer, inner_steps),
                    rank=Z.shape[1], res_paper=res_paper(A, B, C, Z, hist[-1]))

@@ -9,7 +9,12 @@ Test infrastructure (see ``oracle/__init__.py``): prints markdown table rows for
 design notes; nothing here is used by the GPU path.
 
     python -m oracle.table1_fp32_sweep [q ...]
+    python -m oracle.table1_fp32_sweep --inners bf16,fp16 [q ...]
     python -m oracle.table1_fp32_sweep --dense200 [k ...]
+
+bf16 / fp16 are the storage-rounding model of ``oracle.lowrank.storage_rounding``
+(FP32 arithmetic, results rounded to the narrow format); their inner tolerances are
+1e-2 and 1e-3 (a few units of u_s), FP32's is the paper's 1e-5.
 """
 from __future__ import annotations
 
@@ -23,21 +28,29 @@ from oracle import dense as od
 from oracle import lowrank as ol
 
 
+INNER_TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2}
+
+
 def run(q: float, inner: str):
     p = ci.paper_example1(q=q)
     A = p.A.to_dense()
-    tol = 1e-5 if inner == "fp32" else 1e-12
+    tol = INNER_TOL[inner]
     t = time.time()
     _, info = ol.framework1(A, p.B, p.C, tau_R=1e-14, dense=True, inner=inner, tol_lyap=tol, tol_newton=tol)
     return info, time.time() - t
 
 
-def main(qs):
+def main(qs, inners=("fp64", "fp32")):
     print("| kappa_2(A) | inner | status | Res | rel. residual | Iter0 | Iter | rank | s |")
     print("|---|---|---|---:|---:|---|---|---:|---:|")
     for q in qs:
-        for inner in ("fp64", "fp32"):
-            info, s = run(q, inner)
+        for inner in inners:
+            try:
+                info, s = run(q, inner)
+            except (np.linalg.LinAlgError, FloatingPointError, ValueError) as e:
+                print(f"| 1e{q:g} | {inner} | failed ({type(e).__name__}: overflow/non-finite) | | | | | | |",
+                      flush=True)
+                continue
             i0, it = info["iter0"], info["iter"]
             print(f"| 1e{q:g} | {inner} | {info['status']} | {info['res_paper']:.2e} | {info['rel_res']:.1e} | "
                   f"{i0[0]}({i0[1]}) | {it[0]}({it[1]}) | {info['rank']} | {s:.0f} |", flush=True)
@@ -63,5 +76,7 @@ if __name__ == "__main__":
     args = sys.argv[1:]
     if args and args[0] == "--dense200":
         main_dense200([int(x) for x in args[1:]] or list(range(7)))
+    elif args and args[0] == "--inners":
+        main([float(x) for x in args[2:]] or [1, 2, 3, 4], inners=tuple(args[1].split(",")))
     else:
         main([float(x) for x in args] or [1, 2, 3, 4, 5, 6, 7, 8])

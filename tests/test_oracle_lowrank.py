@@ -237,3 +237,33 @@ def test_toeplitz_section52_n32768():
         assert info["status"] == "ok", (inner, info["status"])
         assert info["res_paper"] <= 10 * ref["res"], (inner, info["res_paper"])
         assert abs(info["iter"][0] - ref["iter"][0]) <= 1, (inner, info["iter"])
+
+
+def test_bf16_rounding_model():
+    """The lower-precision model's bfloat16 rounding: 8 significant bits, ties to even,
+    exact on representable values, monotone, inf/nan kept."""
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -7, -2.8, 0.0, np.inf], np.float32)
+    r = ol._round_bf16(x)
+    assert r[0] == 1.0 and r[1] == 1.0            # tie -> even (1.0)
+    assert r[2] == np.float32(1.0 + 2 * 2.0 ** -7)  # tie -> even (1 + 2^-6)
+    assert r[3] == x[3] and r[5] == 0.0 and np.isinf(r[6])
+    assert r[4] == np.float32(-2.796875)
+    y = np.sort(np.random.default_rng(5).standard_normal(10000).astype(np.float32))
+    ry = ol._round_bf16(y)
+    assert np.all(np.diff(ry) >= 0)
+    assert np.all(np.abs(ry - y) <= 2.0 ** -8 * np.abs(y))  # u = 2^-8 for 8 significant bits
+
+
+@pytest.mark.slow
+def test_bf16_inner_solves_converge_below_threshold_with_more_steps():
+    """Lower inner precision (the paper's future work), modelled as FP32 arithmetic with
+    bfloat16 storage: at kappa_2(A) = 10 the refinement still reaches the paper's Res
+    level, but needs more refinement steps than with FP32 inner solves (the contraction
+    factor of Theorem 1 grows with u_s)."""
+    p = ci.paper_example1(q=1.0)
+    A = p.A.to_dense()
+    Zb, ib = ol.framework1(A, p.B, p.C, tau_R=1e-14, dense=True, inner="bf16", tol_lyap=1e-2, tol_newton=1e-2)
+    Zs, is_ = ol.framework1(A, p.B, p.C, tau_R=1e-14, dense=True, inner="fp32", tol_lyap=1e-5, tol_newton=1e-5)
+    assert ib["status"] == "ok" and is_["status"] == "ok"
+    assert ib["res_paper"] <= 1e-14
+    assert ib["iter"][0] > is_["iter"][0]
