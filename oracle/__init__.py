@@ -10,7 +10,9 @@ Everything here is plain NumPy/SciPy in float64, written for obviousness, not
 speed.  The one exception is the inner precision u_s of Framework 1
 (``inner="fp32"``), in which NLR-ADI and the correction LR-ADI run on float32 /
 complex64 arrays, so that NumPy and LAPACK compute them in IEEE single
-precision, as in the FP32 rows of Section 5.1:
+precision, as in the FP32 rows of Section 5.1.  The paper's future-work precisions
+(``inner="bf16"`` / ``"fp16"``) are modelled as FP32 arithmetic whose stored
+results are rounded to the narrow format (``oracle.lowrank.storage_rounding``):
 
 ``oracle.dense``    -- the CARE residual operator, a Bartels-Stewart Lyapunov
                        solver, Newton's method in the paper's correction form
