@@ -133,6 +133,9 @@ typedef struct {
                           /* products X^T Y, [0] FP64 and [1] FP32 inputs            */
   double gram_gflop[2];   /* their algorithmic GFLOP: 2 n a b, or n a (a+1) for X^T X */
   long long gram_calls[2];/* their number                                             */
+  double gemm_ms[2];      /* the same for the tall-skinny products Y = alpha X S + beta */
+  double gemm_gflop[2];   /* Y (n x a times a x b; 2 n a b GFLOP), [0] FP64, [1] FP32   */
+  long long gemm_calls[2];/* inputs                                                     */
 } care_info;
 
 /* Prepared operator: A^T in CSR (FP64 and FP32 values) plus its diagonal, laid

@@ -61,7 +61,8 @@ class info_t(ct.Structure):
                 ("spmm_calls", ct.c_longlong), ("krylov_unconverged", ct.c_int), ("nhist", ct.c_int),
                 ("res_hist", ct.c_double * HIST_MAX), ("res_rel_CtC", ct.c_double), ("res_paper", ct.c_double),
                 ("ms_phase", ct.c_double * 4), ("ms_total", ct.c_double),
-                ("gram_ms", ct.c_double * 2), ("gram_gflop", ct.c_double * 2), ("gram_calls", ct.c_longlong * 2)]
+                ("gram_ms", ct.c_double * 2), ("gram_gflop", ct.c_double * 2), ("gram_calls", ct.c_longlong * 2),
+                ("gemm_ms", ct.c_double * 2), ("gemm_gflop", ct.c_double * 2), ("gemm_calls", ct.c_longlong * 2)]
 
 
 class op_t(ct.Structure):
@@ -201,7 +202,8 @@ def _info_dict(inf: info_t) -> dict:
                 krylov_unconverged=inf.krylov_unconverged, res_hist=list(inf.res_hist[:inf.nhist]),
                 res_rel_CtC=inf.res_rel_CtC, res_paper=inf.res_paper, ms_phase=list(inf.ms_phase),
                 ms_total=inf.ms_total, gram_ms=list(inf.gram_ms), gram_gflop=list(inf.gram_gflop),
-                gram_calls=list(inf.gram_calls))
+                gram_calls=list(inf.gram_calls), gemm_ms=list(inf.gemm_ms), gemm_gflop=list(inf.gemm_gflop),
+                gemm_calls=list(inf.gemm_calls))
 
 
 class Workspace:

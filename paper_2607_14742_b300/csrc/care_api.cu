@@ -374,10 +374,10 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
       else S2[(size_t)(i - rq) * cw + col] = v;
     }
   }
-  gemm_ts<double, To>(n, rq, cw, 1.0, R.QZ, R.ldq, upload(c, S1), cw, 0.0, Cout, ldco, c.s);
+  gemm_c<double, To>(c, n, rq, cw, 1.0, R.QZ, R.ldq, upload(c, S1), cw, 0.0, Cout, ldco);
   if (qp) {
     const double* Vb = basis_and_coeffs(R, O, qp, cw, S2);
-    gemm_ts<double, To>(n, qp, cw, 1.0, Vb, R.ldbig, upload(c, S2), cw, 1.0, Cout, ldco, c.s);
+    gemm_c<double, To>(c, n, qp, cw, 1.0, Vb, R.ldbig, upload(c, S2), cw, 1.0, Cout, ldco);
   }
   return o;
 }
@@ -444,9 +444,9 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
     }
   }
   if (rn) {
-    if (r) gemm_ts<double, double>(n, r, rn, 1.0, R.QZ, R.ldq, upload(c, S1), rn, 0.0, R.QZn, R.ldq, c.s);
+    if (r) gemm_c<double, double>(c, n, r, rn, 1.0, R.QZ, R.ldq, upload(c, S1), rn, 0.0, R.QZn, R.ldq);
     const double* Vb = basis_and_coeffs(R, O, qp, rn, S2);
-    gemm_ts<double, double>(n, qp, rn, 1.0, Vb, R.ldbig, upload(c, S2), rn, r ? 1.0 : 0.0, R.QZn, R.ldq, c.s);
+    gemm_c<double, double>(c, n, qp, rn, 1.0, Vb, R.ldbig, upload(c, S2), rn, r ? 1.0 : 0.0, R.QZn, R.ldq);
   }
   std::swap(R.QZ, R.QZn);
   R.r = rn;
@@ -581,7 +581,7 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     std::vector<double> KB((size_t)r * m);
     for (int i = 0; i < r; ++i)
       for (int j = 0; j < m; ++j) KB[(size_t)i * m + j] = S.R.s[i] * S.R.s[i] * a1.QB[(size_t)i * m + j];
-    gemm_ts<double, T>(n, r, m, 1.0, S.R.QZ, S.R.ldq, upload(c, KB), m, 0.0, S.in.K, S.in.ldm, c.s);
+    gemm_c<double, T>(c, n, r, m, 1.0, S.R.QZ, S.R.ldq, upload(c, KB), m, 0.0, S.in.K, S.in.ldm);
     t1 = now_ms();
     const int bw = a1.rp + a1.rm;
     // FP64 inner factors are compressed at FP64 accuracy (harmless before Algorithm 2's own
@@ -610,10 +610,14 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.spmm_calls = c.spmm_calls;
   inf.krylov_unconverged = c.krylov_unconverged;
   inf.ms_total = now_ms() - t0;
+  harvest_timings(c);
   for (int q = 0; q < 2; ++q) {
     inf.gram_ms[q] = c.gram_ms[q];
     inf.gram_gflop[q] = c.gram_gflop[q];
     inf.gram_calls[q] = c.gram_calls[q];
+    inf.gemm_ms[q] = c.gemm_ms[q];
+    inf.gemm_gflop[q] = c.gemm_gflop[q];
+    inf.gemm_calls[q] = c.gemm_calls[q];
   }
   if (info) *info = inf;
   return st;
@@ -655,10 +659,14 @@ static care_status lradi_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.res_rel_CtC = a.res;
   inf.status = a.converged ? CARE_OK : CARE_NOT_CONVERGED;
   inf.ms_total = now_ms() - t0;
+  harvest_timings(c);
   for (int q = 0; q < 2; ++q) {
     inf.gram_ms[q] = c.gram_ms[q];
     inf.gram_gflop[q] = c.gram_gflop[q];
     inf.gram_calls[q] = c.gram_calls[q];
+    inf.gemm_ms[q] = c.gemm_ms[q];
+    inf.gemm_gflop[q] = c.gemm_gflop[q];
+    inf.gemm_calls[q] = c.gemm_calls[q];
   }
   if (info) *info = inf;
   return (care_status)inf.status;

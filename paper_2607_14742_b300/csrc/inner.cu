@@ -73,6 +73,7 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   CARE_CUDA(cudaEventRecord(c.ge1, c.s));
   CARE_CUDA(cudaMemcpyAsync(h.data(), c.dG, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   CARE_CUDA(cudaStreamSynchronize(c.s));
+  harvest_timings(c);
   float ms = 0.f;
   CARE_CUDA(cudaEventElapsedTime(&ms, c.ge0, c.ge1));
   const int k = sizeof(T) == 8 ? 0 : 1;
@@ -132,12 +133,12 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   for (int t = 0; t < r1; ++t)
     for (int j = 0; j < cols; ++j) T1[(size_t)t * cols + j] = Rs[(size_t)t * cols + j] * d[j];
   if (out) {
-    gemm_ts<T, T>(n, cols, r1, 1.0, X, ldx, upload(c, M1), r1, 0.0, out, ldo, c.s);
+    gemm_c<T, T>(c, n, cols, r1, 1.0, X, ldx, upload(c, M1), r1, 0.0, out, ldo);
     o.rank = r1;
     o.T = std::move(T1);
     return o;
   }
-  gemm_ts<T, T>(n, cols, r1, 1.0, X, ldx, upload(c, M1), r1, 0.0, buf, ldb, c.s);
+  gemm_c<T, T>(c, n, cols, r1, 1.0, X, ldx, upload(c, M1), r1, 0.0, buf, ldb);
   if (!second_pass) {
     copy2d<T, T>(n, r1, buf, ldb, 1, X, ldx, 1, 1.0, c.s);
     o.rank = r1;
@@ -168,7 +169,7 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   if (defer_rinv)
     o.Rinv = Rinv;  // basis = buf * Rinv, formed by the caller's product
   else
-    gemm_ts<T, T>(n, r1, r1, 1.0, buf, ldb, upload(c, Rinv), r1, 0.0, X, ldx, c.s);
+    gemm_c<T, T>(c, n, r1, r1, 1.0, buf, ldb, upload(c, Rinv), r1, 0.0, X, ldx);
   o.rank = r1;
   o.T.assign((size_t)r1 * cols, 0.0);
 #pragma omp parallel for if ((long)r1 * r1 * cols > 1000000) schedule(dynamic, 4)
@@ -192,7 +193,7 @@ std::vector<double> cgs2(Ctx& c, long n, const T* Q, int ldq, int r, T* X, int l
   if (r == 0 || cols == 0) return C;
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<double> Ck = gram_h<T>(c, n, r, cols, Q, ldq, X, ldx);
-    gemm_ts<T, T>(n, r, cols, -1.0, Q, ldq, upload(c, Ck), cols, 1.0, X, ldx, c.s);
+    gemm_c<T, T>(c, n, r, cols, -1.0, Q, ldq, upload(c, Ck), cols, 1.0, X, ldx);
     for (size_t i = 0; i < C.size(); ++i) C[i] += Ck[i];
   }
   return C;
@@ -257,7 +258,7 @@ static void apply_F(Ctx& c, Inner<T>& in, bool hasK, const T* X, T* Y, int h) {
   c.spmm_calls++;
   if (hasK) {
     std::vector<double> BtX = gram_h<T>(c, in.n, in.m, h, in.B, in.ldm, X, in.ldq);
-    gemm_ts<T, T>(in.n, in.m, h, -1.0, in.K, in.ldm, upload(c, BtX), h, 1.0, Y, in.ldq, c.s);
+    gemm_c<T, T>(c, in.n, in.m, h, -1.0, in.K, in.ldm, upload(c, BtX), h, 1.0, Y, in.ldq);
   }
 }
 
@@ -372,12 +373,12 @@ static void smw_solve(Ctx& c, Inner<T>& in, Shift p, int b, bool hasK) {
         E[(size_t)(2 * k + 1) * (2 * b) + 2 * j] = -t.im;
         E[(size_t)(2 * k + 1) * (2 * b) + 2 * j + 1] = t.re;
       }
-    gemm_ts<T, T>(n, 2 * m, 2 * b, 1.0, in.SOL + 2 * b, in.ldr, upload(c, E), 2 * b, 1.0, in.SOL, in.ldr, c.s);
+    gemm_c<T, T>(c, n, 2 * m, 2 * b, 1.0, in.SOL + 2 * b, in.ldr, upload(c, E), 2 * b, 1.0, in.SOL, in.ldr);
   } else {
     std::vector<double> E((size_t)m * b);
     for (int k = 0; k < m; ++k)
       for (int j = 0; j < b; ++j) E[(size_t)k * b + j] = Tm[(size_t)j * m + k].re;
-    gemm_ts<T, T>(n, m, b, 1.0, in.SOL + b, in.ldr, upload(c, E), b, 1.0, in.SOL, in.ldr, c.s);
+    gemm_c<T, T>(c, n, m, b, 1.0, in.SOL + b, in.ldr, upload(c, E), b, 1.0, in.SOL, in.ldr);
   }
 }
 
@@ -416,7 +417,7 @@ static int compress_part(Ctx& c, Inner<T>& in, int col0, int ncols, bool right_a
   host_gemm_nt(q, q, ncols, o.T.data(), ncols, o.T.data(), ncols, nullptr, TT.data(), q, true);
   CARE_REQUIRE(host_cholesky_upper(q, TT.data(), R.data()), CARE_ERR_SMALL_DENSE, "compression Cholesky");
   // column-major upper R == row-major R^T = L
-  gemm_ts<T, T>(n, q, q, 1.0, in.Z + col0, in.ldz, upload(c, R), q, 0.0, in.Zs, in.ldz, c.s);
+  gemm_c<T, T>(c, n, q, q, 1.0, in.Z + col0, in.ldz, upload(c, R), q, 0.0, in.Zs, in.ldz);
   const int dst = right_aligned ? col0 + ncols - q : col0;
   copy2d<T, T>(n, q, in.Zs, in.ldz, 1, in.Z + dst, in.ldz, 1, 1.0, c.s);
   return q;
@@ -485,20 +486,20 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
         Ei[(size_t)(2 * q + 1) * b + q] = 1.0;
       }
       const double* dE = upload(c, E);
-      gemm_ts<T, T>(n, 2 * b, b, g * g, in.SOL, in.ldr, dE, b, 1.0, in.W, in.ldw, c.s);
-      if (rp) gemm_ts<T, T>(n, 2 * b, rp, g, in.SOL, in.ldr, dE, b, 0.0, in.Z + np, in.ldz, c.s);
-      if (rm) gemm_ts<T, T>(n, 2 * b, rm, g, in.SOL, in.ldr, dE + rp, b, 0.0, in.Z + pm0, in.ldz, c.s);
+      gemm_c<T, T>(c, n, 2 * b, b, g * g, in.SOL, in.ldr, dE, b, 1.0, in.W, in.ldw);
+      if (rp) gemm_c<T, T>(c, n, 2 * b, rp, g, in.SOL, in.ldr, dE, b, 0.0, in.Z + np, in.ldz);
+      if (rm) gemm_c<T, T>(c, n, 2 * b, rm, g, in.SOL, in.ldr, dE + rp, b, 0.0, in.Z + pm0, in.ldz);
       const double gi = g * std::sqrt(d * d + 1.0);
       const double* dEi = upload(c, Ei);
-      if (rp) gemm_ts<T, T>(n, 2 * b, rp, gi, in.SOL, in.ldr, dEi, b, 0.0, in.Z + np + rp, in.ldz, c.s);
-      if (rm) gemm_ts<T, T>(n, 2 * b, rm, gi, in.SOL, in.ldr, dEi + rp, b, 0.0, in.Z + pm0 + rm, in.ldz, c.s);
+      if (rp) gemm_c<T, T>(c, n, 2 * b, rp, gi, in.SOL, in.ldr, dEi, b, 0.0, in.Z + np + rp, in.ldz);
+      if (rm) gemm_c<T, T>(c, n, 2 * b, rm, gi, in.SOL, in.ldr, dEi + rp, b, 0.0, in.Z + pm0 + rm, in.ldz);
       j += 2;
     }
     if (knew) {
       // K_new += Z_blk (Z_blk^T B)
       const int add = mult * rp;
       std::vector<double> ZtB = gram_h<T>(c, n, add, in.m, in.Z + np, in.ldz, in.B, in.ldm);
-      gemm_ts<T, T>(n, add, in.m, 1.0, in.Z + np, in.ldz, upload(c, ZtB), in.m, 1.0, in.Knew, in.ldm, c.s);
+      gemm_c<T, T>(c, n, add, in.m, 1.0, in.Z + np, in.ldz, upload(c, ZtB), in.m, 1.0, in.Knew, in.ldm);
     }
     if (rp) {
       last0 = np;

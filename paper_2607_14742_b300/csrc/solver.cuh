@@ -29,6 +29,17 @@ struct Ctx {
   double gram_ms[2] = {0.0, 0.0}, gram_gflop[2] = {0.0, 0.0};
   long long gram_calls[2] = {0, 0};
   cudaEvent_t ge0 = nullptr, ge1 = nullptr;
+  // the same for the tall-skinny products X S (gemm_c): their event pairs are queued
+  // and read at the next point where the stream has been synchronised (harvest_timings)
+  double gemm_ms[2] = {0.0, 0.0}, gemm_gflop[2] = {0.0, 0.0};
+  long long gemm_calls[2] = {0, 0};
+  struct PendingTiming {
+    cudaEvent_t e0, e1;
+    double gflop;
+    int k;
+  };
+  std::vector<PendingTiming> tpend;
+  std::vector<cudaEvent_t> tpool;
   int krylov_unconverged = 0;
   bool counting() const { return ar.counting(); }
   Ctx() = default;
@@ -37,8 +48,58 @@ struct Ctx {
   ~Ctx() {
     if (ge0) cudaEventDestroy(ge0);
     if (ge1) cudaEventDestroy(ge1);
+    for (const PendingTiming& t : tpend) {
+      cudaEventDestroy(t.e0);
+      cudaEventDestroy(t.e1);
+    }
+    for (cudaEvent_t e : tpool) cudaEventDestroy(e);
   }
 };
+
+// Reads the queued product timings; every queued event has been recorded on c.s
+// before the synchronisation that precedes this call, so nothing waits here in
+// practice (cudaEventSynchronize returns at once).
+inline void harvest_timings(Ctx& c) {
+  for (const Ctx::PendingTiming& t : c.tpend) {
+    CARE_CUDA(cudaEventSynchronize(t.e1));
+    float ms = 0.f;
+    CARE_CUDA(cudaEventElapsedTime(&ms, t.e0, t.e1));
+    c.gemm_ms[t.k] += ms;
+    c.gemm_gflop[t.k] += t.gflop;
+    c.gemm_calls[t.k] += 1;
+    c.tpool.push_back(t.e0);
+    c.tpool.push_back(t.e1);
+  }
+  c.tpend.clear();
+}
+
+inline cudaEvent_t timing_event(Ctx& c) {
+  if (!c.tpool.empty()) {
+    cudaEvent_t e = c.tpool.back();
+    c.tpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  CARE_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+// gemm_ts on c.s (Y = alpha X S + beta Y), timed with CUDA events on the same stream;
+// [0] FP64 inputs, [1] FP32 inputs; algorithmic GFLOP 2 n a b
+template <class Ti, class To>
+inline void gemm_c(Ctx& c, long n, int a, int b, double alpha, const Ti* X, int ldx, const double* S, int lds,
+                   double beta, To* Y, int ldy) {
+  if (n <= 0 || a <= 0 || b <= 0) {
+    gemm_ts<Ti, To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, c.s);
+    return;
+  }
+  if (c.tpend.size() >= 512) harvest_timings(c);  // bounds the queue (waits for the oldest)
+  cudaEvent_t e0 = timing_event(c), e1 = timing_event(c);
+  CARE_CUDA(cudaEventRecord(e0, c.s));
+  gemm_ts<Ti, To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, c.s);
+  CARE_CUDA(cudaEventRecord(e1, c.s));
+  c.tpend.push_back({e0, e1, 2.0 * (double)n * a * b * 1e-9, sizeof(Ti) == 8 ? 0 : 1});
+}
 
 // host <-> device helpers for small matrices
 const double* upload(Ctx& c, const std::vector<double>& h);
