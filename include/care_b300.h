@@ -52,9 +52,12 @@ typedef enum {
   CARE_NOT_CONVERGED = 5,     /* k_max refinement steps without reaching tol (Z valid)  */
   CARE_STAGNATED = 6,         /* residual ratio above stag_ratio (Section 5; Z valid)   */
   CARE_INNER_FAILED = 7,      /* LR-ADI / Krylov made no progress                       */
-  CARE_UNSTABLE = 8,          /* a projected Ritz value of A_k^T has Re >= 0            */
+  CARE_UNSTABLE = 8,          /* A_k not stable: no projected Ritz value with Re < 0,   */
+                              /* or the LR-ADI residual grows by more than 1e12        */
   CARE_NONFINITE = 9,         /* NaN/Inf met in inputs or iterates                      */
-  CARE_ERR_SMALL_DENSE = 10   /* a small dense host factorisation failed                */
+  CARE_ERR_SMALL_DENSE = 10,  /* a small dense host factorisation failed                */
+  CARE_TIMEOUT = 11           /* a bounded device wait (tensor-core pipeline) expired;  */
+                              /* the kernel drained its copies and returned            */
 } care_status;
 
 typedef enum {
@@ -136,6 +139,9 @@ typedef struct {
   double gemm_ms[2];      /* the same for the tall-skinny products Y = alpha X S + beta */
   double gemm_gflop[2];   /* Y (n x a times a x b; 2 n a b GFLOP), [0] FP64, [1] FP32   */
   long long gemm_calls[2];/* inputs                                                     */
+  double tc_ms;           /* device ms of the FP64 products run on the tensor cores    */
+  double tc_gflop;        /* (BF16 slices, care_gram_tc mode 0) and their algorithmic  */
+  long long tc_calls;     /* FP64 GFLOP; Grams and X S products together              */
 } care_info;
 
 /* Prepared operator: A^T in CSR (FP64 and FP32 values) plus its diagonal, laid
@@ -324,6 +330,42 @@ care_status care_residual_factor(const care_csr* A, const double* B, int ldb, in
 /* Number of kernels this library has launched in the process so far (all
  * entry points, all streams); for launch accounting in benchmarks. */
 unsigned long long care_kernel_launches(void);
+
+/* ---- tensor-core products (tcgen05 + TMA, sm_103a) ---------------------- */
+/* The dense n x r by r x r contractions of Algorithms 1-2 and of LR-ADI
+ * (Section 4 complexity, O(n q^2)) on the tensor cores.  mode 0 is
+ * FP64-accurate: every row of X^T and Y^T (column of X, Y) is scaled by a power
+ * of two, rounded to a 49-bit fixed-point integer relative to its largest entry
+ * and split exactly into seven 7-bit BF16 slices; the 34 slice products with
+ * a + b <= 7 run on the BF16 tensor pipe with exact integer chunk sums (the
+ * splitting idea of Ozaki et al. 2012).  mode 1 = TF32 inputs, mode 2 = BF16
+ * inputs, both with FP32 accumulation (the low-precision Grams of the
+ * CARE_PREC_MIXED_TF32 / _BF16 shift generation). */
+int care_tc_available(void);        /* 1 on an sm_103 device with the driver's TMA encoder */
+/* Solver use of the mode-0 products: 0 off (FP64 FMA on the CUDA cores), 1 where
+ * profitable (default: contraction >= 1024, both output sizes >= 48, >= 2 GFLOP),
+ * 2 every FP64 product of the solver (for tests).  Process-wide. */
+void care_set_tensor_cores(int on);
+
+/* Device scratch for care_gram_tc / care_gemm_ts (tc = 1) with a + b <= maxdim. */
+size_t care_tc_work_size(int maxdim);
+
+/* G = X^T Y on the tensor cores; X (n x a, ldx), Y (n x b, ldy) row-major, FP64
+ * for mode 0 and FP32 for modes 1-2; G FP64 row-major a x b (ldg).  X == Y with
+ * the same ld computes the upper tiles only and mirrors them (exactly
+ * symmetric).  work: care_tc_work_size(a + b) bytes.  Synchronises s (reads
+ * the kernels' error word): CARE_TIMEOUT if a bounded wait expired. */
+care_status care_gram_tc(int mode, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy, double* G,
+                         int ldg, void* work, size_t work_bytes, care_stream_t s);
+
+/* Y = alpha X S + beta Y, X (n x a, ldx) and Y (n x b, ldy) row-major, S (a x b,
+ * lds) row-major FP64 on the device; dtype 0 FP64 X, Y; 1 FP32 X, Y (CUDA cores
+ * only).  tc = 1 (dtype 0): FP64-accurate tensor-core slices (work:
+ * care_tc_work_size(a + b) bytes; synchronises s); tc = 0: FP64/FP32 FMA on the
+ * CUDA cores (work unused, asynchronous).  The tall-skinny product of
+ * Algorithms 1-2 (C+- and Z_{k+1} formation) and of the CGS2 projections. */
+care_status care_gemm_ts(int dtype, int tc, int n, int a, int b, double alpha, const void* X, int ldx, const double* S,
+                         int lds, double beta, void* Y, int ldy, void* work, size_t work_bytes, care_stream_t s);
 
 /* ---- small dense host routines (exported for host-only tests) ----------- */
 

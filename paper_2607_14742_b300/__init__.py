@@ -62,7 +62,8 @@ class info_t(ct.Structure):
                 ("res_hist", ct.c_double * HIST_MAX), ("res_rel_CtC", ct.c_double), ("res_paper", ct.c_double),
                 ("ms_phase", ct.c_double * 4), ("ms_total", ct.c_double),
                 ("gram_ms", ct.c_double * 2), ("gram_gflop", ct.c_double * 2), ("gram_calls", ct.c_longlong * 2),
-                ("gemm_ms", ct.c_double * 2), ("gemm_gflop", ct.c_double * 2), ("gemm_calls", ct.c_longlong * 2)]
+                ("gemm_ms", ct.c_double * 2), ("gemm_gflop", ct.c_double * 2), ("gemm_calls", ct.c_longlong * 2),
+                ("tc_ms", ct.c_double), ("tc_gflop", ct.c_double), ("tc_calls", ct.c_longlong)]
 
 
 class op_t(ct.Structure):
@@ -109,6 +110,11 @@ def lib() -> ct.CDLL:
         "care_autotune_workspace_size": (i, [P(op_t), i, i, i, P(sz)]),
         "care_autotune": (i, [P(op_t), i, i, i, P(opts_t), vp, sz, vp, P(d)]),
         "care_kernel_launches": (ct.c_ulonglong, []),
+        "care_tc_available": (i, []),
+        "care_set_tensor_cores": (None, [i]),
+        "care_tc_work_size": (sz, [i]),
+        "care_gram_tc": (i, [i, i, i, i, vp, i, vp, i, vp, i, vp, sz, vp]),
+        "care_gemm_ts": (i, [i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, sz, vp]),
         "care_host_symeig": (i, [i, vp, vp, vp]),
         "care_host_symeig_outside": (i, [i, vp, vp, vp, d, d]),
         "care_host_cholesky_upper": (i, [i, vp, vp]),
@@ -203,7 +209,7 @@ def _info_dict(inf: info_t) -> dict:
                 res_rel_CtC=inf.res_rel_CtC, res_paper=inf.res_paper, ms_phase=list(inf.ms_phase),
                 ms_total=inf.ms_total, gram_ms=list(inf.gram_ms), gram_gflop=list(inf.gram_gflop),
                 gram_calls=list(inf.gram_calls), gemm_ms=list(inf.gemm_ms), gemm_gflop=list(inf.gemm_gflop),
-                gemm_calls=list(inf.gemm_calls))
+                gemm_calls=list(inf.gemm_calls), tc_ms=inf.tc_ms, tc_gflop=inf.tc_gflop, tc_calls=inf.tc_calls)
 
 
 class Workspace:
@@ -420,6 +426,50 @@ def gram(X: torch.Tensor, Y: torch.Tensor):
     _check(lib().care_gram(0 if X.dtype == torch.float64 else 1, n, a, b, _ptr(X), X.stride(0), _ptr(Y),
                            Y.stride(0), _ptr(G), b, _ptr(ws), ws.numel(), _stream()), "care_gram")
     return G
+
+
+TC_MODES = {"f64": 0, "tf32": 1, "bf16": 2}
+
+
+def tc_available() -> bool:
+    """True on an sm_103 device (tcgen05 + TMA)."""
+    return bool(lib().care_tc_available())
+
+
+def set_tensor_cores(mode):
+    """Solver use of the FP64-accurate tensor-core products: 0 off, 1 where
+    profitable (default), 2 every FP64 product (tests)."""
+    lib().care_set_tensor_cores(int(mode))
+
+
+def gram_tc(X: torch.Tensor, Y: torch.Tensor, mode="f64"):
+    """G = X^T Y (float64 a x b) on the tensor cores: mode "f64" (float64 inputs,
+    FP64-accurate BF16 slices), "tf32" or "bf16" (float32 inputs)."""
+    assert X.dtype == Y.dtype and X.shape[0] == Y.shape[0]
+    md = TC_MODES[mode]
+    assert X.dtype == (torch.float64 if md == 0 else torch.float32)
+    n, a = X.shape
+    b = Y.shape[1]
+    G = torch.empty(a, b, dtype=torch.float64, device=X.device)
+    ws = torch.empty(lib().care_tc_work_size(a + b), dtype=torch.uint8, device=X.device)
+    _check(lib().care_gram_tc(md, n, a, b, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), _ptr(G), b, _ptr(ws),
+                              ws.numel(), _stream()), "care_gram_tc")
+    return G
+
+
+def gemm_ts(X: torch.Tensor, S: torch.Tensor, alpha=1.0, beta=0.0, Y: torch.Tensor | None = None, tc=False):
+    """Y = alpha X S + beta Y for row-major X (n x a), S (a x b, float64); tc=True runs
+    the FP64-accurate tensor-core path (float64 X, Y)."""
+    n, a = X.shape
+    b = S.shape[1]
+    S = S.to(torch.float64).contiguous()
+    if Y is None:
+        Y = torch.zeros(n, b, dtype=X.dtype, device=X.device)
+    ws = torch.empty(lib().care_tc_work_size(a + b) if tc else 8, dtype=torch.uint8, device=X.device)
+    _check(lib().care_gemm_ts(0 if X.dtype == torch.float64 else 1, int(bool(tc)), n, a, b, float(alpha), _ptr(X),
+                              X.stride(0), _ptr(S), S.stride(0), float(beta), _ptr(Y), Y.stride(0), _ptr(ws),
+                              ws.numel(), _stream()), "care_gemm_ts")
+    return Y
 
 
 GRAM_NOALLOC_SCRATCH_DOUBLES = 1048576

@@ -222,7 +222,16 @@ static void alloc_ref(Ctx& c, Ref& R, long n, int rcap, int bigcap) {
   R.Wb2 = c.ar.get<double>((size_t)n * R.ldbig);
 }
 
-static void alloc_small(Ctx& c, long n, int maxc, int smallcap) {
+// tc_maxdim > 0 also reserves the scratch of the tensor-core FP64 products whose
+// operand widths add up to at most tc_maxdim (Algorithms 1-2).
+static void alloc_small(Ctx& c, long n, int maxc, int smallcap, int tc_maxdim = 0) {
+  if (tc_maxdim > 0) {
+    // reserved whether or not the tensor cores are switched on, so that the
+    // workspace query does not depend on the switch
+    c.tc = tc_alloc(c.ar, tc_maxdim);
+    c.tc_maxdim = tc_maxdim;
+    if (!c.counting()) CARE_CUDA(cudaMemsetAsync(c.tc.err, 0, sizeof(int), c.s));
+  }
   c.dS_cap = (size_t)smallcap;
   c.dS = c.ar.get<double>(c.dS_cap);
   c.dG_cap = (size_t)smallcap;
@@ -498,7 +507,7 @@ struct Session {
 
 template <class T>
 static void alloc_session(Ctx& c, Session<T>& S, int n, int nnz, int m, int p, const Caps& k, bool ref) {
-  alloc_small(c, n, k.maxc, k.small);
+  alloc_small(c, n, k.maxc, k.small, ref ? std::max(k.rcap + k.bigcap, 2 * k.bigcap) : 0);
   alloc_prob(c, S.P, n, m, p);
   S.in.alloc(c, n, m, k.bcap, k.adicap, k.hcap);
   S.ldct = pad_ld<T>(std::max(p, 1));
@@ -611,6 +620,9 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.krylov_unconverged = c.krylov_unconverged;
   inf.ms_total = now_ms() - t0;
   harvest_timings(c);
+  inf.tc_ms = c.tc_ms;
+  inf.tc_gflop = c.tc_gflop;
+  inf.tc_calls = c.tc_calls;
   for (int q = 0; q < 2; ++q) {
     inf.gram_ms[q] = c.gram_ms[q];
     inf.gram_gflop[q] = c.gram_gflop[q];
@@ -660,6 +672,9 @@ static care_status lradi_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.status = a.converged ? CARE_OK : CARE_NOT_CONVERGED;
   inf.ms_total = now_ms() - t0;
   harvest_timings(c);
+  inf.tc_ms = c.tc_ms;
+  inf.tc_gflop = c.tc_gflop;
+  inf.tc_calls = c.tc_calls;
   for (int q = 0; q < 2; ++q) {
     inf.gram_ms[q] = c.gram_ms[q];
     inf.gram_gflop[q] = c.gram_gflop[q];
@@ -682,7 +697,7 @@ static care_status resfac_impl(Ctx& c, const care_csr* A, const double* B, int l
   void* opmem = c.ar.get<char>(op_bytes(n, A->nnz));
   Prob P;
   Ref R;
-  alloc_small(c, n, k.maxc, k.small);
+  alloc_small(c, n, k.maxc, k.small, 3 * k.rcap + p + m);
   alloc_prob(c, P, n, m, p);
   alloc_ref(c, R, n, k.rcap, std::max(k.rcap + p, k.rcap));
   const int ccap = std::max(c_cap, 0);
@@ -810,6 +825,7 @@ const char* care_status_string(int s) {
     case CARE_UNSTABLE: return "CARE_UNSTABLE";
     case CARE_NONFINITE: return "CARE_NONFINITE";
     case CARE_ERR_SMALL_DENSE: return "CARE_ERR_SMALL_DENSE";
+    case CARE_TIMEOUT: return "CARE_TIMEOUT";
     default: return "CARE_UNKNOWN_STATUS";
   }
 }
@@ -1172,6 +1188,67 @@ care_status care_residual_factor(const care_csr* A, const double* B, int ldb, in
 }
 
 unsigned long long care_kernel_launches(void) { return care::launches(); }
+
+int care_tc_available(void) {
+  const bool ok = tc_available();
+  cudaGetLastError();
+  return ok ? 1 : 0;
+}
+
+void care_set_tensor_cores(int on) { tc_set_enabled(on); }
+
+size_t care_tc_work_size(int maxdim) {
+  Arena a;
+  tc_alloc(a, std::max(maxdim, 1));
+  return a.off + 256;
+}
+
+care_status care_gram_tc(int mode, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy, double* G,
+                         int ldg, void* work, size_t work_bytes, care_stream_t s) {
+  if (mode < 0 || mode > 2 || n < 0 || a < 0 || b < 0 || ldx < a || ldy < b || ldg < b) return CARE_ERR_INVALID_ARG;
+  if (a > 0 && b > 0 && (!G || !work || (n > 0 && (!X || !Y)))) return CARE_ERR_INVALID_ARG;
+  if (a == 0 || b == 0) return CARE_OK;
+  return run_guarded([&] {
+    CARE_REQUIRE(tc_available(), CARE_ERR_CUDA, "tensor cores (sm_103a) not available");
+    Arena ar;
+    ar.base = static_cast<char*>(work);
+    ar.cap = work_bytes;
+    const int md = a + b;
+    TcScratch sc = tc_alloc(ar, md);
+    cudaStream_t cs = (cudaStream_t)s;
+    CARE_CUDA(cudaMemsetAsync(sc.err, 0, sizeof(int), cs));
+    if (mode == 0)
+      tc_gram_f64(n, a, b, (const double*)X, ldx, (const double*)Y, ldy, G, ldg, sc, md, cs);
+    else
+      tc_gram_lowp(mode, n, a, b, (const float*)X, ldx, (const float*)Y, ldy, G, ldg, sc, md, cs);
+    return tc_check(sc, cs) ? CARE_TIMEOUT : CARE_OK;
+  });
+}
+
+care_status care_gemm_ts(int dtype, int tc, int n, int a, int b, double alpha, const void* X, int ldx, const double* S,
+                         int lds, double beta, void* Y, int ldy, void* work, size_t work_bytes, care_stream_t s) {
+  if ((dtype != 0 && dtype != 1) || n < 0 || a < 0 || b < 0 || ldx < a || lds < b || ldy < b) return CARE_ERR_INVALID_ARG;
+  if (n > 0 && b > 0 && (!Y || (a > 0 && (!X || !S)))) return CARE_ERR_INVALID_ARG;
+  if (tc && (dtype != 0 || !work)) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    cudaStream_t cs = (cudaStream_t)s;
+    if (tc && a > 0) {
+      CARE_REQUIRE(tc_available(), CARE_ERR_CUDA, "tensor cores (sm_103a) not available");
+      Arena ar;
+      ar.base = static_cast<char*>(work);
+      ar.cap = work_bytes;
+      TcScratch sc = tc_alloc(ar, a + b);
+      CARE_CUDA(cudaMemsetAsync(sc.err, 0, sizeof(int), cs));
+      tc_gemm_ts_f64<double>(n, a, b, alpha, (const double*)X, ldx, S, lds, beta, (double*)Y, ldy, sc, a + b, cs);
+      return tc_check(sc, cs) ? CARE_TIMEOUT : CARE_OK;
+    }
+    if (dtype == 0)
+      gemm_ts<double, double>(n, a, b, alpha, (const double*)X, ldx, S, lds, beta, (double*)Y, ldy, cs);
+    else
+      gemm_ts<float, float>(n, a, b, alpha, (const float*)X, ldx, S, lds, beta, (float*)Y, ldy, cs);
+    return CARE_OK;
+  });
+}
 
 care_status care_host_symeig(int n, const double* A, double* w, double* V) {
   if (n < 0 || (n > 0 && (!A || !w))) return CARE_ERR_INVALID_ARG;

@@ -195,37 +195,36 @@ bool host_symeig_select(int n, const double* A, double* w, double* V,
       const double beta = 2.0 / vn2;
       // p = A22 v from the stored lower triangle of A22 (column j holds A22(i, j),
       // i >= j, contiguously): column j gives p_j its inner product with v[j..]
-      // and adds A22(i, j) v_j to p_i, i > j.  Static cyclic columns and a
-      // thread-ordered sum of the per-thread partial vectors keep the result
-      // bitwise reproducible.
+      // and adds A22(i, j) v_j to p_i, i > j.  The columns are dealt in blocks
+      // of 16 to a fixed number of partial vectors (block b to partial b mod
+      // SYMV_PARTS), each partial is formed by one thread in column order, and
+      // the partials are summed in index order: the result is bitwise the same
+      // for any number of threads.
+      constexpr int SYMV_PARTS = 32;
       std::fill(p.begin(), p.begin() + m, 0.0);
       const bool parm = par && m >= 96;
-      int nt = 1;
-#ifdef _OPENMP
-      if (parm) nt = omp_get_max_threads();
-#endif
-      pbuf.assign((size_t)nt * m, 0.0);
-#pragma omp parallel num_threads(nt) if (parm)
-      {
-        int tid = 0;
-#ifdef _OPENMP
-        tid = omp_get_thread_num();
-#endif
-        double* pt = &pbuf[(size_t)tid * m];
-#pragma omp for schedule(static, 16)
-        for (int j = 0; j < m; ++j) {
-          const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
-          const double vj = v[j];
-          double sj = 0.0;
+      const int nblk = (m + 15) / 16;
+      const int nparts = parm ? std::min(SYMV_PARTS, nblk) : 1;
+      pbuf.assign((size_t)nparts * m, 0.0);
+#pragma omp parallel for if (parm) schedule(dynamic, 1)
+      for (int t = 0; t < nparts; ++t) {
+        double* pt = &pbuf[(size_t)t * m];
+        for (int blk = t; blk < nblk; blk += nparts) {
+          const int jend = std::min(m, 16 * blk + 16);
+          for (int j = 16 * blk; j < jend; ++j) {
+            const double* col = &a[(size_t)(k + 1 + j) * n + k + 1];
+            const double vj = v[j];
+            double sj = 0.0;
 #pragma omp simd reduction(+ : sj)
-          for (int i = j; i < m; ++i) {
-            sj += col[i] * v[i];
-            pt[i] += col[i] * vj;
+            for (int i = j; i < m; ++i) {
+              sj += col[i] * v[i];
+              pt[i] += col[i] * vj;
+            }
+            pt[j] += sj - col[j] * vj;  // the diagonal entry counted once
           }
-          pt[j] += sj - col[j] * vj;  // the diagonal entry counted once
         }
       }
-      for (int t = 0; t < nt; ++t)
+      for (int t = 0; t < nparts; ++t)
         for (int i = 0; i < m; ++i) p[i] += pbuf[(size_t)t * m + i];
       // the panel's pending updates: A22 v -= V (W^T v) + W (V^T v)
       for (int t = 0; t < jj; ++t) {

@@ -69,7 +69,15 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
     CARE_CUDA(cudaEventCreate(&c.ge1));
   }
   CARE_CUDA(cudaEventRecord(c.ge0, c.s));
-  gram<T>(n, a, b, X, ldx, Y, ldy, c.dG, b, c.gw, c.gw_cap, c.s);
+  const bool sym0 = a == b && (const void*)X == (const void*)Y && ldx == ldy;
+  bool on_tc = false;
+  if (sizeof(T) == 8 && tc_use(c, n, a, b, sym0 ? a : a + b)) {
+    tc_gram_f64(n, a, b, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<const double*>(Y), ldy, c.dG,
+                b, c.tc, c.tc_maxdim, c.s);
+    c.tc_used = on_tc = true;
+  } else {
+    gram<T>(n, a, b, X, ldx, Y, ldy, c.dG, b, c.gw, c.gw_cap, c.s);
+  }
   CARE_CUDA(cudaEventRecord(c.ge1, c.s));
   CARE_CUDA(cudaMemcpyAsync(h.data(), c.dG, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   CARE_CUDA(cudaStreamSynchronize(c.s));
@@ -77,10 +85,16 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   float ms = 0.f;
   CARE_CUDA(cudaEventElapsedTime(&ms, c.ge0, c.ge1));
   const int k = sizeof(T) == 8 ? 0 : 1;
-  const bool sym = a == b && (const void*)X == (const void*)Y && ldx == ldy;
-  c.gram_ms[k] += ms;
-  c.gram_gflop[k] += (sym ? (double)n * a * (a + 1) : 2.0 * n * a * b) * 1e-9;
-  c.gram_calls[k] += 1;
+  const double gf = (sym0 ? (double)n * a * (a + 1) : 2.0 * n * a * b) * 1e-9;
+  if (on_tc) {
+    c.tc_ms += ms;
+    c.tc_gflop += gf;
+    c.tc_calls += 1;
+  } else {
+    c.gram_ms[k] += ms;
+    c.gram_gflop[k] += gf;
+    c.gram_calls[k] += 1;
+  }
   if (verbose_level() >= 1) c.ms_gram += now_ms() - t0;
   return h;
 }
@@ -302,6 +316,13 @@ static std::vector<Shift> proj_shifts(Ctx& c, Inner<T>& in, bool hasK, const T* 
     for (int j = 0; j < h; ++j) Hc[(size_t)j * h + i] = Hp[(size_t)i * h + j];
   std::vector<double> wr(h), wi(h);
   CARE_REQUIRE(host_eigvals(h, Hc.data(), wr.data(), wi.data()), CARE_ERR_SMALL_DENSE, "eigvals (shifts)");
+  // Every Ritz value in the closed right half-plane: the projection has no stable
+  // direction, so the operator (A - B K^T, stable by hypothesis of Theorem 1 and of
+  // K_0 = 0) is not.  Isolated right-half-plane values are mirrored below, since a
+  // stable non-normal operator can have them.
+  bool any_stable = false;
+  for (int i = 0; i < h; ++i) any_stable |= wr[i] < 0.0;
+  CARE_REQUIRE(any_stable, CARE_UNSTABLE, "every projected Ritz value has Re >= 0");
   const double imtol = sizeof(T) == 4 ? 1e-6 : 1e-10;
   for (int i = 0; i < h; ++i) {
     const double re = wr[i], im = wi[i];
@@ -512,6 +533,9 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
     nm += mult * rm;
     r = adi_norm2<T>(c, in, b) / w0;
     if (!std::isfinite(r)) CARE_THROW(CARE_NONFINITE, "LR-ADI residual not finite");
+    // with left half-plane shifts the residual factor of a stable operator does not
+    // grow by orders of magnitude; growth beyond 1e12 means the operator is unstable
+    CARE_REQUIRE(r <= 1e12, CARE_UNSTABLE, "LR-ADI residual diverges");
     if (verbose_level() >= 2)
       fprintf(stderr, "[care]   adi j=%d p=(%.4e,%.4e) res=%.3e cols=%d+%d\n", j, p.re, p.im, r, np, nm);
   }

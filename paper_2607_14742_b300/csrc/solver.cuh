@@ -7,6 +7,7 @@
 
 #include "dense.cuh"
 #include "krylov.cuh"
+#include "tc.cuh"
 
 namespace care {
 
@@ -41,6 +42,14 @@ struct Ctx {
   std::vector<PendingTiming> tpend;
   std::vector<cudaEvent_t> tpool;
   int krylov_unconverged = 0;
+  // tensor-core products: scratch, the operand-width limit it was sized for, and
+  // whether a product ran since the last check of its error word
+  TcScratch tc;
+  int tc_maxdim = 0;
+  bool tc_used = false;
+  int lowp = 0;  // low-precision tensor-core Grams of the shift generation: 0 off, 1 TF32, 2 BF16
+  double tc_ms = 0.0, tc_gflop = 0.0;  // device time and FP64-equivalent GFLOP of the sliced products
+  long long tc_calls = 0;
   bool counting() const { return ar.counting(); }
   Ctx() = default;
   Ctx(const Ctx&) = delete;
@@ -64,13 +73,24 @@ inline void harvest_timings(Ctx& c) {
     CARE_CUDA(cudaEventSynchronize(t.e1));
     float ms = 0.f;
     CARE_CUDA(cudaEventElapsedTime(&ms, t.e0, t.e1));
-    c.gemm_ms[t.k] += ms;
-    c.gemm_gflop[t.k] += t.gflop;
-    c.gemm_calls[t.k] += 1;
+    if (t.k == 2) {
+      c.tc_ms += ms;
+      c.tc_gflop += t.gflop;
+      c.tc_calls += 1;
+    } else {
+      c.gemm_ms[t.k] += ms;
+      c.gemm_gflop[t.k] += t.gflop;
+      c.gemm_calls[t.k] += 1;
+    }
     c.tpool.push_back(t.e0);
     c.tpool.push_back(t.e1);
   }
   c.tpend.clear();
+  if (c.tc_used) {
+    c.tc_used = false;
+    const int e = tc_check(c.tc, c.s);
+    CARE_REQUIRE(e == 0, CARE_TIMEOUT, "tensor-core product: a bounded wait expired");
+  }
 }
 
 inline cudaEvent_t timing_event(Ctx& c) {
@@ -84,8 +104,15 @@ inline cudaEvent_t timing_event(Ctx& c) {
   return e;
 }
 
+// Whether an FP64 product of this shape (contraction k, output a x b, operand widths
+// adding up to dims) runs on the tensor cores (FP64-accurate slices).
+inline bool tc_use(const Ctx& c, long k, int a, int b, int dims) {
+  return c.tc.ok() && dims <= c.tc_maxdim && tc_f64_profitable(k, a, b) && tc_available();
+}
+
 // gemm_ts on c.s (Y = alpha X S + beta Y), timed with CUDA events on the same stream;
-// [0] FP64 inputs, [1] FP32 inputs; algorithmic GFLOP 2 n a b
+// [0] FP64 inputs on the CUDA cores, [1] FP32 inputs, [2] FP64 inputs on the tensor
+// cores (sliced); algorithmic GFLOP 2 n a b
 template <class Ti, class To>
 inline void gemm_c(Ctx& c, long n, int a, int b, double alpha, const Ti* X, int ldx, const double* S, int lds,
                    double beta, To* Y, int ldy) {
@@ -96,9 +123,17 @@ inline void gemm_c(Ctx& c, long n, int a, int b, double alpha, const Ti* X, int 
   if (c.tpend.size() >= 512) harvest_timings(c);  // bounds the queue (waits for the oldest)
   cudaEvent_t e0 = timing_event(c), e1 = timing_event(c);
   CARE_CUDA(cudaEventRecord(e0, c.s));
-  gemm_ts<Ti, To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, c.s);
+  int k = sizeof(Ti) == 8 ? 0 : 1;
+  if (sizeof(Ti) == 8 && tc_use(c, n, a, b, a + b)) {
+    tc_gemm_ts_f64<To>(n, a, b, alpha, reinterpret_cast<const double*>(X), ldx, S, lds, beta, Y, ldy, c.tc,
+                       c.tc_maxdim, c.s);
+    c.tc_used = true;
+    k = 2;
+  } else {
+    gemm_ts<Ti, To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, c.s);
+  }
   CARE_CUDA(cudaEventRecord(e1, c.s));
-  c.tpend.push_back({e0, e1, 2.0 * (double)n * a * b * 1e-9, sizeof(Ti) == 8 ? 0 : 1});
+  c.tpend.push_back({e0, e1, 2.0 * (double)n * a * b * 1e-9, k});
 }
 
 // host <-> device helpers for small matrices

@@ -257,3 +257,47 @@ def test_workspace_size_grows_with_problem():
     b = pb.workspace_size(250000, 1248000, 5, 5, 512, "mixed")
     c = pb.workspace_size(250000, 1248000, 5, 5, 512, "fp64")
     assert 0 < a < b < c
+
+
+_DETERMINISM_SCRIPT = r"""
+import hashlib, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import paper_2607_14742_b300 as pb
+rng = np.random.default_rng(20260)
+h = hashlib.sha256()
+for n in (150, 611):
+    # small integers: the BLAS products below are exact in any order, so the inputs
+    # do not depend on the BLAS thread count either
+    M = rng.integers(-8, 9, size=(n, n)).astype(np.float64)
+    A = M + M.T
+    w, V = pb.host_symeig(A)
+    h.update(w.tobytes()); h.update(V.tobytes())
+    ws, Vs = pb.host_symeig_outside(A, np.quantile(w, 0.3), np.quantile(w, 0.8))
+    h.update(ws.tobytes()); h.update(Vs.tobytes())
+    G = M @ M.T + n * np.eye(n)
+    h.update(np.float64(pb.host_sym_lmax(G)).tobytes())
+    h.update(pb.host_cholesky_upper(G).tobytes())
+    piv, R = pb.host_pivoted_cholesky(G, 1e-12 * np.abs(G).max())
+    h.update(piv.tobytes()); h.update(R.tobytes())
+    h.update(pb.host_gemm_nt(M, M, sym=True).tobytes())
+    h.update(pb.host_upper_inverse(np.triu(M) + n * np.eye(n)).tobytes())
+print(h.hexdigest())
+"""
+
+
+def test_host_dense_bitwise_independent_of_thread_count():
+    """The host small-dense routines give bitwise identical results for any OpenMP
+    thread count (the batched solver runs them with a share of the cores per worker,
+    and its instances must equal individual solves bit for bit)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    digests = set()
+    for nt in (1, 3, 8):
+        env = dict(os.environ, OMP_NUM_THREADS=str(nt), OMP_DYNAMIC="false")
+        r = subprocess.run([sys.executable, "-c", _DETERMINISM_SCRIPT, root], env=env, capture_output=True,
+                           text=True, timeout=600)
+        assert r.returncode == 0, r.stderr
+        digests.add(r.stdout.strip())
+    assert len(digests) == 1, digests

@@ -267,3 +267,33 @@ def test_bf16_inner_solves_converge_below_threshold_with_more_steps():
     assert ib["status"] == "ok" and is_["status"] == "ok"
     assert ib["res_paper"] <= 1e-14
     assert ib["iter"][0] > is_["iter"][0]
+
+
+def test_res_paper_hand_computed():
+    """Section 5's Res = ||R||_F / (2 ||A||_F ||Z^T Z||_F + ||B^T B||_F ||Z^T Z||_F^2 + ||C C^T||_F)
+    on a case worked by hand, with every norm chosen so that a dropped factor, a swapped
+    square or a different matrix norm changes the value:
+      A = diag(-1, -2, -2):            ||A||_F = 3        (||A||_2 = 2)
+      Z = [e1, e2]:                    Z^T Z = I_2, ||Z^T Z||_F = sqrt(2)   (||Z||_F^2 = 2)
+      B = (1, 1, 1)^T:                 B^T B = [3], ||B^T B||_F = 3
+      C = I_3:                         C C^T = I_3, ||C C^T||_F = sqrt(3)   (||C||_F^2 = 3)
+    denominator = 2*3*sqrt(2) + 3*2 + sqrt(3) = 6 sqrt(2) + 6 + sqrt(3)."""
+    A = np.diag([-1.0, -2.0, -2.0])
+    Z = np.eye(3)[:, :2]
+    B = np.ones((3, 1))
+    C = np.eye(3)
+    den = 6.0 * math.sqrt(2.0) + 6.0 + math.sqrt(3.0)
+    assert ol.res_paper(A, B, C, Z, den) == pytest.approx(1.0, rel=1e-15)
+    assert ol.res_paper(A, B, C, Z, 2.5) == pytest.approx(2.5 / den, rel=1e-15)
+    # the sparse form of A gives the same ||A||_F
+    import scipy.sparse as sp
+    assert ol.res_paper(sp.csr_matrix(A), B, C, Z, den) == pytest.approx(1.0, rel=1e-15)
+    # plausible misreadings all move the value by more than 5 %
+    r2, r3 = math.sqrt(2.0), math.sqrt(3.0)
+    wrong = [3 * r2 + 6 + r3,           # factor 2 dropped
+             2 * 3 * 2 + 3 * r2 + r3,   # square on the A term instead of the B term
+             2 * 2 * r2 + 6 + r3,       # ||A||_2 instead of ||A||_F
+             2 * 3 * r2 + 6 + 3.0,      # ||C||_F^2 instead of ||C C^T||_F
+             2 * 3 * 2 + 3 * 4 + r3]    # ||Z||_F^2 instead of ||Z^T Z||_F
+    for w in wrong:
+        assert abs(den / w - 1.0) > 0.05
