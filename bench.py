@@ -1,18 +1,26 @@
 """Benchmark: time to relative residual 1e-10 for the large sparse CARE, mixed
 precision (FP32 NLR-ADI / LR-ADI inner solves, FP64 residual factorisation and
-update) vs the all-FP64 path of the same code, on one B300; plus the SpMM
-roofline.  Prints one JSON line.
+update) vs the all-FP64 path of the same code, on one B300; plus the rooflines.
+Prints one JSON line.
 
 Workload: 2D convection-diffusion -Lap(u) + 10 u_x + 100 u_y on a 500 x 500
 interior grid (n = 250,000, nnz = 1,248,000), A = -L, B n x 5 and C 5 x n with
-U[0,1) entries from the seeded generator.  A step is one complete care_solve
-(NLR-ADI + refinement to ||R||_F / ||C^T C||_F <= 1e-10) with the inputs
-resident in HBM; L2 is flushed (a 256 MB write) before every timed step.
+U[0,1) entries from the seeded generator.  A step is one complete solve through
+the public API with host buffers: the pinned host inputs (A in CSR, B, C) are
+copied to the device, care_solve runs (NLR-ADI + refinement to
+||R||_F / ||C^T C||_F <= 1e-10), and Z is copied back.  CUDA events on the
+solve's stream split every step: `value` is the device time of care_solve with
+its inputs resident in HBM, `e2e` the whole step including both copies.  L2 is
+flushed (a 256 MB write) before every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU FP64 oracle (the program the GPU results are
-checked against) on the host cores, on a bounded sample of the same workload.
+checked against) on the host cores, one FP64 SMW shifted solve of the same
+workload per step.  One solve takes tens of seconds on the GPU, so the timed
+work is kept inside a wall-clock budget (--budget, default 1500 s): if the
+requested warm-up and steps cannot fit, fewer are run (at least 3 warm-up
+steps) and the line reports the counts actually run.
 """
 from __future__ import annotations
 
@@ -22,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -32,6 +41,7 @@ TOL = 1e-10
 GRID = 500
 MP = 5
 R_CAP = 1536
+SLICE_PAIRS = 43  # BF16 slice products per FP64 multiply-add in the FP64-accurate tensor-core path
 
 
 def workload_config(prob):
@@ -55,8 +65,9 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, path):
-        self.path = path
+    def __init__(self):
+        fd, self.path = tempfile.mkstemp(prefix="care_bench_clocks_", suffix=".csv")
+        os.close(fd)
         self.p = None
 
     def __enter__(self):
@@ -99,69 +110,75 @@ class Clocks:
             out["sm_max_mhz"] = max(mx)
         out["reasons"] = sorted(reasons)
         out["samples"] = len(sm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         return out
 
 
-def run_reference(args):
-    """CPU FP64 oracle on the host cores: a bounded sample of the same workload."""
-    import numpy as np
-    import care_inputs as ci
-    from oracle import lowrank as ol
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    prob = ci.config_fdm2d(GRID, MP, MP)
-    As = prob.A.to_scipy()
-    cores = os.cpu_count()
-    times = []
-    for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        v, sample = oracle_sample(prob, As)
-        dt = time.perf_counter() - t0
-        if it >= args.warmup:
-            times.append(v)
-    val = statistics.mean(times)
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(prob),
-            "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+# ---------------------------------------------------------------- oracle arm --
+SHIFTS = (-3000.0, -3.0e4, -3.0e5)
 
 
-def oracle_sample(prob, As, shifted_solves=None):
-    """Time the oracle's FP64 LR-ADI shifted solve (SuperLU factorisation of
-    M_p = (A + pI)^T and an SMW block solve with p + m right-hand sides) for three
-    shifts, and scale to a full solve by the number of shifted solves a full
-    FP64 Framework-1 run performs (the GPU run's count, or 150 if unknown)."""
+def oracle_shifted_solve(prob, As, shift):
+    """One FP64 SMW shifted solve of the oracle on the workload's operator: SuperLU
+    factorisation of M_p = (A + pI)^T and the solve for the block [C^T, K] (p + m
+    right-hand sides) with the Sherman-Morrison-Woodbury correction (Section 4)."""
     import numpy as np
     from oracle import lowrank as ol
     solver = ol.ShiftedSolver(As)
     W = np.hstack([prob.C.T, np.zeros((prob.n, MP))])
     K = 1e-3 * prob.B
-    shifts = [-3000.0, -3.0e4, -3.0e5]
     t0 = time.perf_counter()
-    for p in shifts:
-        ol.smw_solve(solver, prob.B, K, p, W)
-    per = (time.perf_counter() - t0) / len(shifts)
-    count = shifted_solves or 150
-    return per * count, (f"3 FP64 SMW shifted solves (SuperLU of (A+pI)^T, {2 * MP} RHS) on the n={prob.n} "
-                         f"operator, {per:.3f} s each, scaled x{count} shifted solves per full solve")
+    ol.smw_solve(solver, prob.B, K, shift, W)
+    return time.perf_counter() - t0
 
 
+SAMPLE = (f"one FP64 SMW shifted solve per step (SuperLU of (A+pI)^T, {2 * MP} right-hand sides, shifts "
+          f"cycling through {SHIFTS}) on the n=250000 operator of the workload")
+
+
+def run_reference(args):
+    """CPU FP64 oracle on the host cores, one shifted solve per step (measured)."""
+    import care_inputs as ci
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = ci.config_fdm2d(GRID, MP, MP)
+    As = prob.A.to_scipy()
+    times = []
+    for it in range(args.warmup + args.steps):
+        dt = oracle_shifted_solve(prob, As, SHIFTS[it % len(SHIFTS)])
+        if it >= args.warmup:
+            times.append(dt)
+    val = statistics.mean(times)
+    unit = "s per FP64 shifted solve"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(prob),
+            "cpu_baseline": {"value": val, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": SAMPLE},
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "a full oracle solve of this workload takes several hundred shifted solves (tens of minutes "
+                    "on the host); the timed unit is one of them"}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ our arm --
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--budget", type=float, default=1500.0, help="wall-clock seconds for the whole run")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) solve")
     ap.add_argument("--only", default="all", choices=["all", "spmm", "gram"],
                     help="spmm / gram: only the SpMM or Gram microbenchmark cases (the profiling cases "
-                         "for k_spmm and k_gram)")
+                         "for k_spmm and k_tc_gemm / k_gram)")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="summarise an ncu --csv launch list (gpu__time_duration.sum) per kernel and exit")
     args = ap.parse_args()
@@ -169,6 +186,7 @@ def main():
         return summarize_launches(args.summarize_launches)
     if args.impl == "reference":
         return run_reference(args)
+    t_start = time.perf_counter()
 
     import numpy as np
     import torch
@@ -192,131 +210,186 @@ def main():
     if args.only == "gram":
         print(json.dumps(gram_cases(pb, torch, dev)))
         return
-    A = pb.CSR.from_arrays(prob.n, prob.A.rowptr, prob.A.colind, prob.A.val, device=dev)
-    B = torch.tensor(prob.B, device=dev)
-    C = torch.tensor(prob.C, device=dev)
-    ws = pb.Workspace()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    # shifted-solve configuration chosen by the library's autotuner (outside the timed region)
-    t_tune = time.perf_counter()
-    tuned, tune_ms = pb.autotune(pb.Operator(A), MP, 2 * MP, prec="mixed")
-    t_tune = time.perf_counter() - t_tune
-    tuned64, _ = pb.autotune(pb.Operator(A), MP, 2 * MP, prec="fp64")
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def solve(prec):
-        return pb.care_solve(A, B, C, tol=TOL, prec=prec, r_cap=R_CAP, workspace=ws,
-                             opts=pb.default_options(krylov_chunk=(tuned if prec == "mixed" else tuned64).krylov_chunk,
-                                                     tri_sweeps=(tuned if prec == "mixed" else tuned64).tri_sweeps,
-                                                     precond=(tuned if prec == "mixed" else tuned64).precond))
-
-    for _ in range(args.warmup):
-        Z, info = solve("mixed")
     stream = torch.cuda.current_stream()
-    ts = []
-    infos = []
-    launches0 = pb.kernel_launches()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks.csv")
-    barrier()
-    # the timed steps sit in an NVTX range so that a profiler can be restricted to them
-    torch.cuda.nvtx.range_push("bench_timed")
-    with clocks:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            Z, info = solve("mixed")
-            e1.record(stream)
-            barrier()
-            ts.append(e0.elapsed_time(e1) / 1e3)
-            infos.append(info)
-    torch.cuda.nvtx.range_pop()
-    launches = pb.kernel_launches() - launches0
-    t = statistics.mean(ts)
-    if world > 1:
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    info = infos[-1]
-    # the all-FP64 path of the same code
-    fp64 = None
-    if args.fp64_steps > 0:
-        Z64, i64 = solve("fp64")
-        t64 = []
-        for _ in range(args.fp64_steps):
-            flush.fill_(1.0)
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            Z64, i64 = solve("fp64")
-            e1.record(stream)
-            barrier()
-            t64.append(e0.elapsed_time(e1) / 1e3)
-        fp64 = {"s_per_solve": statistics.mean(t64), "status": i64["status"], "rank": i64["rank"],
-                "res_rel_CtC": i64["res_rel_CtC"], "iter0": i64["iter0"], "iter": i64["iter"],
-                "speedup_mixed_vs_fp64": statistics.mean(t64) / t}
-    # end to end through the public API: host inputs -> device, Z -> host, every step
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # the SpMM roofline and the FP64 peak first (cheap; they survive a cut run)
+    spmm = spmm_roofline(pb, torch, prob, dev)
+    fp64_peak = pb.fp64_peak()
+    # pinned host inputs: every step copies them to the device and Z back
     hA = [torch.from_numpy(prob.A.rowptr).pin_memory(), torch.from_numpy(prob.A.colind).pin_memory(),
           torch.from_numpy(prob.A.val).pin_memory()]
-    hB = torch.from_numpy(prob.B).pin_memory()
-    hC = torch.from_numpy(prob.C).pin_memory()
+    hB = torch.from_numpy(np.ascontiguousarray(prob.B)).pin_memory()
+    hC = torch.from_numpy(np.ascontiguousarray(prob.C)).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in hA + [hB, hC])
-    e2e_t = []
-    d2h = 0
-    for _ in range(0 if args.no_e2e else max(1, args.steps)):
+    ws = pb.Workspace()
+    # shifted-solve configuration chosen by the library's autotuner (outside the timed region)
+    dA0 = pb.CSR(prob.n, hA[0].to(dev), hA[1].to(dev), hA[2].to(dev))
+    t_tune = time.perf_counter()
+    tuned, tune_ms = pb.autotune(pb.Operator(dA0), MP, 2 * MP, prec="mixed")
+    t_tune = time.perf_counter() - t_tune
+    del dA0
+
+    def opts(prec):
+        return pb.default_options(krylov_chunk=tuned.krylov_chunk, tri_sweeps=tuned.tri_sweeps,
+                                  precond=tuned.precond)
+
+    def step(prec):
+        """One end-to-end solve; returns (device solve s, whole step s, info, d2h bytes)."""
         flush.fill_(1.0)
         barrier()
-        t0 = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
         dA = pb.CSR(prob.n, hA[0].to(dev, non_blocking=True), hA[1].to(dev, non_blocking=True),
                     hA[2].to(dev, non_blocking=True))
         dB = hB.to(dev, non_blocking=True)
         dC = hC.to(dev, non_blocking=True)
-        Ze, ie = pb.care_solve(dA, dB, dC, tol=TOL, prec="mixed", r_cap=R_CAP, workspace=ws,
-                               opts=pb.default_options(krylov_chunk=tuned.krylov_chunk, tri_sweeps=tuned.tri_sweeps,
-                                                       precond=tuned.precond))
-        Zh = Ze.cpu()
-        torch.cuda.synchronize()
-        e2e_t.append(time.perf_counter() - t0)
-        d2h = Zh.numel() * Zh.element_size()
-    # SpMM roofline: the fused BiCGStab SpMM shape (b = 2*(p+m) FP32 columns) and a
-    # cold operator + blocks larger than L2 (the 3D 100^3 operator, 20 columns)
-    spmm = spmm_roofline(pb, torch, prob, dev)
+        ev[1].record(stream)
+        Z, info = pb.care_solve(dA, dB, dC, tol=TOL, prec=prec, r_cap=R_CAP, workspace=ws, opts=opts(prec))
+        ev[2].record(stream)
+        Zh = Z.to("cpu", non_blocking=False)
+        ev[3].record(stream)
+        barrier()
+        return (ev[1].elapsed_time(ev[2]) / 1e3, ev[0].elapsed_time(ev[3]) / 1e3, info,
+                Zh.numel() * Zh.element_size())
+
+    # the all-FP64 path of the same code (same end-to-end step, same options), first,
+    # so that the budget of the mixed steps is known
+    fp64 = None
+    if args.fp64_steps > 0:
+        t64 = []
+        i64 = None
+        for _ in range(args.fp64_steps):
+            v64, _, i64, _ = step("fp64")
+            t64.append(v64)
+        fp64 = {"s_per_solve": statistics.mean(t64), "status": i64["status"], "rank": i64["rank"],
+                "res_rel_CtC": i64["res_rel_CtC"], "iter0": i64["iter0"], "iter": i64["iter"],
+                "ms_phase": i64["ms_phase"]}
+    # warm-up, with a budget check after the first step
+    warm_done = 0
+    t0 = time.perf_counter()
+    step("mixed")
+    warm_done = 1
+    t_step = time.perf_counter() - t0
+    reserve = 30.0 + (30.0 if not args.no_cpu_baseline else 0.0)
+    left = args.budget - (time.perf_counter() - t_start) - reserve
+    warmup = max(1, args.warmup)
+    steps = max(1, args.steps)
+    while (warmup - warm_done + steps) * t_step > left and warmup > 3:
+        warmup -= 1
+    while (warmup - warm_done + steps) * t_step > left and steps > 1:
+        steps -= 1
+    for _ in range(warmup - warm_done):
+        step("mixed")
+
+    clocks = Clocks()
+    vals, e2es, infos = [], [], []
+    d2h = 0
+    launches0 = pb.kernel_launches()
+    barrier()
+    torch.cuda.nvtx.range_push("bench_timed")
+    with clocks:
+        for _ in range(steps):
+            v, e, info, d2h = step("mixed")
+            vals.append(v)
+            e2es.append(e)
+            infos.append(info)
+    torch.cuda.nvtx.range_pop()
+    launches = (pb.kernel_launches() - launches0) // steps
+    t = statistics.mean(vals)
+    te = statistics.mean(e2es)
+    if world > 1:
+        tt = torch.tensor([t, te], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t, te = float(tt[0].item()), float(tt[1].item())
+    info = infos[-1]
+    if fp64 is not None:
+        fp64["speedup_mixed_vs_fp64"] = fp64["s_per_solve"] / t
     pk = peaks()
     line = {
-        "metric": METRIC, "value": t, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": t, "unit": "s", "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": t * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic (seeded; see care_inputs)", "config": workload_config(prob),
+        "steps_requested": args.steps, "warmup_requested": args.warmup,
         "status": info["status"], "res_rel_CtC": info["res_rel_CtC"], "res_paper": info["res_paper"],
         "rank": info["rank"], "iter0": info["iter0"], "iter": info["iter"], "krylov_iters": info["krylov_iters"],
+        "s_per_step_all": vals,
         "ms_phase": {"nlradi": info["ms_phase"][0], "alg1": info["ms_phase"][1], "inner_lradi": info["ms_phase"][2],
                      "alg2": info["ms_phase"][3]},
+        "host_syncs": info["host_syncs"],
         "fp64_path": fp64,
         "autotune": {"krylov_chunk": tuned.krylov_chunk, "tri_sweeps": tuned.tri_sweeps, "precond": tuned.precond,
                      "best_ms": tune_ms, "seconds": t_tune},
-        "e2e": ({"value": statistics.mean(e2e_t), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-                if e2e_t else None),
-        "gpu_launches": launches // max(1, args.steps),
-        "roofline": gram_roofline(info, t),
+        "e2e": {"value": te, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roofline(info, t, pk, fp64_peak),
         "spmm": spmm,
         "clocks": clocks.summary(),
-        "peaks_source": "MEASURED_PEAKS.json" if pk else "fallback 6400 GB/s",
+        "peaks_source": "MEASURED_PEAKS.json" if pk else "fallback 6400 GB/s, 1800 TFLOP/s bf16",
     }
     if rank == 0 and not args.no_cpu_baseline:
-        v, sample = oracle_sample(prob, prob.A.to_scipy(), shifted_solves=(info["iter0"][1] + info["iter"][1]))
-        line["cpu_baseline"] = {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": sample}
+        As = prob.A.to_scipy()
+        ts = [oracle_shifted_solve(prob, As, SHIFTS[i % len(SHIFTS)]) for i in range(4)]
+        per = statistics.mean(ts[1:])
+        nsolves = info["iter0"][1] + info["iter"][1]
+        line["cpu_baseline"] = {"value": per, "unit": "s per FP64 shifted solve", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": SAMPLE + " (3 timed after 1 untimed)",
+                                "full_solve_estimate_s": per * nsolves,
+                                "full_solve_estimate_note": f"extrapolation, not a timing: the measured time per "
+                                                            f"shifted solve x the {nsolves} LR-ADI shifted solves "
+                                                            f"of the timed GPU solve"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def roofline(info, step_s, pk, fp64_peak):
+    """Roofline of the kernel family with the largest device time in the timed step,
+    all measured live (CUDA events on the solve's stream around every launch or
+    solve of the family, summed by the library into care_info):
+      - tensor: FP64-accurate sliced products (k_tc_gemm and its slicing passes);
+        achieved = 43 BF16 slice-pair FLOPs per FP64 FLOP (2 n a b, or n a (a+1) for
+        X^T X) / device time, against the sustained bf16 peak;
+      - hbm: FP32 block Krylov solves (k_spmm, k_bicg_*, k_trisweep, ILU setup);
+        achieved = algorithmic bytes (pass count per iteration, see DESIGN) / time;
+      - alu: FP64 products left on the CUDA cores, against the measured FP64 FMA peak."""
+    hbm = float(pk.get("hbm_gbs", 6400.0))
+    bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1800.0)))
+    fams = {
+        "tc_f64_slices": {"device_s": info["tc_ms"] / 1e3, "bound": "tensor", "unit": "TFLOP/s", "peak": bf16,
+                          "work": info["tc_gflop"] * SLICE_PAIRS * 1e-3, "launches": info["tc_calls"],
+                          "kernel": "k_tc_gemm<0> + slicing: FP64-accurate X^T Y and X S of Algorithms 1-2 "
+                                    "(BF16 slices, tcgen05, TMA), n=250000, widths up to ~3000"},
+        "krylov_f32": {"device_s": info["krylov_ms"] / 1e3, "bound": "hbm", "unit": "GB/s", "peak": hbm,
+                       "work": info["krylov_gbyte"], "launches": None,
+                       "kernel": "block BiCGStab shifted solves (k_spmm, k_bicg_*, k_trisweep, ILU(0) setup), "
+                                 "FP32, n=250000"},
+        "fp64_cuda_cores": {"device_s": (info["gram_ms"][0] + info["gemm_ms"][0]) / 1e3, "bound": "alu",
+                            "unit": "TFLOP/s", "peak": fp64_peak,
+                            "work": (info["gram_gflop"][0] + info["gemm_gflop"][0]) * 1e-3,
+                            "launches": info["gram_calls"][0] + info["gemm_calls"][0],
+                            "kernel": "k_gram<double>, k_gemm_ts<double,*>: FP64 products below the tensor-core "
+                                      "size threshold"},
+    }
+    for f in fams.values():
+        f["achieved"] = f["work"] / f["device_s"] if f["device_s"] > 0 else 0.0
+        f["frac"] = f["achieved"] / f["peak"] if f["peak"] else None
+        f["share_of_step"] = f["device_s"] / step_s
+    name = max(fams, key=lambda k: fams[k]["device_s"])
+    top = fams[name]
+    return {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+            "frac": top["frac"], "traffic": None, "family": name, "kernel": top["kernel"],
+            "device_s": top["device_s"], "share_of_step": top["share_of_step"],
+            "peak_note": {"tensor": "bf16_tflops_sustained of measured", "hbm": "hbm_gbs of measured",
+                          "alu": "FP64 FMA peak measured in this run (care_fp64_peak)"}[top["bound"]],
+            "traffic_note": "not captured live; the per-kernel ncu DRAM bytes are in profiles/",
+            "families": fams, "fp64_fma_peak_tflops": fp64_peak}
 
 
 def summarize_launches(path):
@@ -334,7 +407,6 @@ def summarize_launches(path):
     scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
 
     def short(name):
-        # drop "void " and the trailing (argument list)
         name = re.sub(r"^void ", "", name)
         if name.endswith(")"):
             depth = 0
@@ -372,64 +444,28 @@ def summarize_launches(path):
         print(f"| `{k}` | {c} | {t / 1e3:.1f} | {100 * t / total:.1f}% |")
 
 
-FP64_PEAK_TFLOPS = 1.25  # nominal B300 FP64 (CUDA cores): ~2 FMA/clk/SM x 148 SMs x 2.03 GHz x 2
-
-
-def gram_roofline(info, step_s):
-    """Roofline of the dominant FP64 kernel family of the mixed solve, measured live:
-    the library brackets every FP64 Gram product X^T Y (k_gram<double> + its split-K
-    reduction) and every FP64 tall-skinny product X S (k_gemm_ts) with CUDA events on
-    the solve's stream during the timed step and sums their algorithmic FLOP (2 n a b;
-    n a (a+1) for X^T X) and device time.  The family with the larger device time is
-    reported; both are listed.  Bound by the FP64 FMA pipe of the CUDA cores."""
-    fams = {
-        "gram": {"kernel": "k_gram<double> + k_gram_reduce: FP64 X^T Y of Algorithms 1-2",
-                 "device_s": info["gram_ms"][0] / 1e3, "gflop": info["gram_gflop"][0],
-                 "launches": info["gram_calls"][0]},
-        "gemm_ts": {"kernel": "k_gemm_ts<double, *>: FP64 X S of Algorithms 1-2 (CGS2, Cholesky QR, factor updates)",
-                    "device_s": info.get("gemm_ms", [0, 0])[0] / 1e3, "gflop": info.get("gemm_gflop", [0, 0])[0],
-                    "launches": info.get("gemm_calls", [0, 0])[0]},
-    }
-    for f in fams.values():
-        f["TFLOPs"] = f["gflop"] / f["device_s"] / 1e3 if f["device_s"] > 0 else 0.0
-        f["share_of_step"] = f["device_s"] / step_s
-    name = max(fams, key=lambda k: fams[k]["device_s"])
-    top = fams[name]
-    ach = top["TFLOPs"]
-    return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-            "kernel": top["kernel"] + " (n=250000, widths up to ~2600 columns), measured live in the timed step "
-                      "with CUDA events on its stream",
-            "launches": top["launches"], "device_s": top["device_s"], "share_of_step": top["share_of_step"],
-            "fp64_families": fams,
-            "peak_note": "nominal FP64 rate (no measured FP64 peak); FP32 Gram products of the inner solves: "
-                         f"{info['gram_gflop'][1] / max(info['gram_ms'][1], 1e-9):.2f} TFLOP/s over "
-                         f"{info['gram_ms'][1] / 1e3:.2f} s"}
-
-
 def gram_cases(pb, torch, dev):
-    """Gram microbenchmark (CUDA events on the launching stream, inputs > L2)."""
+    """Gram microbenchmark (CUDA events on the launching stream, inputs > L2):
+    FP64 X^T X on the tensor cores (sliced) and on the CUDA cores."""
     stream = torch.cuda.current_stream()
     out = {}
-    for name, dt, n, a, b in (("f64_sym_n250000_a512", torch.float64, 250000, 512, None),
-                              ("f64_n250000_256x512", torch.float64, 250000, 256, 512),
-                              ("f32_sym_n250000_a1024", torch.float32, 250000, 1024, None)):
-        X = torch.randn(n, a, dtype=dt, device=dev)
-        Y = X if b is None else torch.randn(n, b, dtype=dt, device=dev)
-        flop = n * a * (a + 1) if b is None else 2 * n * a * b
-        ms = []
-        for it in range(7):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pb.gram(X, Y)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if it >= 2:
-                ms.append(e0.elapsed_time(e1))
-        m = statistics.median(ms)
-        out[name] = {"ms": m, "gflop": flop / 1e9, "TFLOPs": flop / m / 1e9}
-        del X, Y
+    for name, n, a in (("f64_sym_n250000_a512", 250000, 512), ("f64_sym_n250000_a2048", 250000, 2048)):
+        X = torch.randn(n, a, dtype=torch.float64, device=dev)
+        flop = n * a * (a + 1)
+        for impl, f in (("tc", lambda: pb.gram_tc(X, X, "f64")), ("cuda_cores", lambda: pb.gram(X, X))):
+            ms = []
+            for it in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                f()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= 2:
+                    ms.append(e0.elapsed_time(e1))
+            m = statistics.median(ms)
+            out[f"{name}_{impl}"] = {"ms": m, "gflop_fp64": flop / 1e9, "TFLOPs_fp64_equiv": flop / m / 1e9}
+        del X
     return out
 
 
@@ -443,9 +479,8 @@ def spmm_roofline(pb, torch, prob, dev):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def timeit(op, X, reps=20):
-        Y = None
         for _ in range(3):
-            Y = pb.spmm(op, X, -1000.0)
+            pb.spmm(op, X, -1000.0)
         ms = []
         for _ in range(reps):
             flush.fill_(1.0)
@@ -480,10 +515,9 @@ def spmm_roofline(pb, torch, prob, dev):
     main = cases["fdm3d_100_b32_f32"]
     out["cases"] = cases
     out["roofline"] = {"bound": "hbm", "achieved": main["GBs"], "peak": peak, "unit": "GB/s",
-                       "frac": main["GBs"] / peak, "traffic": 289.7e6,
-                       "traffic_note": "dram read+write bytes per launch from ncu --set full of this case "
-                                       "(bench.py --only spmm): 191.5 MB read, 98.1 MB written; about 30 MB "
-                                       "of Y is still in L2 when the kernel ends",
+                       "frac": main["GBs"] / peak, "traffic": None,
+                       "traffic_note": "DRAM bytes per launch of this case are in profiles/k_spmm_fdm3d_100_b32.md "
+                                       "(ncu, not captured live)",
                        "kernel": "k_spmm: Y = (A^T + pI) X, CSR, 7-point 100^3 operator (n=1e6, nnz=6.94e6), "
                                  "32 FP32 columns, difference form, L2 flushed; measured on the launching stream"}
     return out

@@ -62,7 +62,15 @@ typedef enum {
 
 typedef enum {
   CARE_PREC_FP64 = 0,       /* u_s = u = u_r = u_c = FP64: the all-FP64 path            */
-  CARE_PREC_MIXED_FP32 = 1  /* u_s = FP32 (NLR-ADI and inner LR-ADI); u, u_r, u_c = FP64 */
+  CARE_PREC_MIXED_FP32 = 1, /* u_s = FP32 (NLR-ADI and inner LR-ADI); u, u_r, u_c = FP64 */
+  CARE_PREC_MIXED_TF32 = 2, /* as MIXED_FP32, and the Grams of the shift generation (the */
+                            /* shift-basis orthonormalisation and the projected matrix)  */
+                            /* on the tensor cores with TF32 inputs, FP32 accumulation   */
+  CARE_PREC_MIXED_BF16 = 3  /* the same with BF16 inputs.  The paper names tensor cores  */
+                            /* as future work (Section 6); only products whose use       */
+                            /* tolerates their rounding (Ritz values for the shifts)     */
+                            /* take them, the Krylov, ADI-norm and refinement arithmetic */
+                            /* stays FP32 / FP64                                         */
 } care_prec;
 
 typedef enum { CARE_KRYLOV_BICGSTAB = 0 } care_krylov;
@@ -142,6 +150,10 @@ typedef struct {
   double tc_ms;           /* device ms of the FP64 products run on the tensor cores    */
   double tc_gflop;        /* (BF16 slices, care_gram_tc mode 0) and their algorithmic  */
   long long tc_calls;     /* FP64 GFLOP; Grams and X S products together              */
+  double krylov_ms;       /* device ms of the block Krylov shifted solves (events)     */
+  double krylov_gbyte;    /* their algorithmic HBM GB (per-iteration pass count)       */
+  long long host_syncs;   /* stream synchronisations made by the host control          */
+  long long lowp_gram_calls; /* TF32 / BF16 tensor-core Grams (MIXED_TF32 / _BF16)     */
 } care_info;
 
 /* Prepared operator: A^T in CSR (FP64 and FP32 values) plus its diagonal, laid
@@ -276,7 +288,9 @@ care_status care_workspace_size(int n, int nnz, int m, int p, int r_cap, care_pr
  * A: CSR of A (device).  B (n x m, ldb) and C (p x n, ldc): FP64 column-major,
  * device.  Z: output, FP64 column-major n x r_cap (ldz >= n), device; the
  * first info->rank columns hold the factor, X ~ Z Z^T.  Returns CARE_OK on
- * convergence; CARE_NOT_CONVERGED / CARE_STAGNATED still return the last Z.
+ * convergence; CARE_NOT_CONVERGED / CARE_STAGNATED still return a factor: the
+ * last one, or the one before it if the last refinement step increased the
+ * residual (info->res_rel_CtC is the residual of the returned factor).
  * Synchronises s.  info (host) may be NULL. */
 care_status care_solve(const care_csr* A, const double* B, int ldb, int m, const double* C, int ldc,
                        int p, double tol, care_prec prec, const care_opts* opts, double* Z, int ldz,
@@ -331,13 +345,18 @@ care_status care_residual_factor(const care_csr* A, const double* B, int ldb, in
  * entry points, all streams); for launch accounting in benchmarks. */
 unsigned long long care_kernel_launches(void);
 
+/* Measured FP64 FMA throughput of the CUDA cores in TFLOP/s (8 independent
+ * dependent-FMA chains per thread over 8 CTAs per SM; best of 3 timed runs with
+ * CUDA events on s): the denominator of the FP64 product rooflines. */
+care_status care_fp64_peak(double* tflops, care_stream_t s);
+
 /* ---- tensor-core products (tcgen05 + TMA, sm_103a) ---------------------- */
 /* The dense n x r by r x r contractions of Algorithms 1-2 and of LR-ADI
  * (Section 4 complexity, O(n q^2)) on the tensor cores.  mode 0 is
  * FP64-accurate: every row of X^T and Y^T (column of X, Y) is scaled by a power
- * of two, rounded to a 49-bit fixed-point integer relative to its largest entry
- * and split exactly into seven 7-bit BF16 slices; the 34 slice products with
- * a + b <= 7 run on the BF16 tensor pipe with exact integer chunk sums (the
+ * of two, rounded to a 56-bit fixed-point integer relative to its largest entry
+ * and split exactly into eight 7-bit BF16 slices; the 43 slice products with
+ * a + b <= 8 run on the BF16 tensor pipe with exact integer chunk sums (the
  * splitting idea of Ozaki et al. 2012).  mode 1 = TF32 inputs, mode 2 = BF16
  * inputs, both with FP32 accumulation (the low-precision Grams of the
  * CARE_PREC_MIXED_TF32 / _BF16 shift generation). */
@@ -346,6 +365,12 @@ int care_tc_available(void);        /* 1 on an sm_103 device with the driver's T
  * profitable (default: contraction >= 1024, both output sizes >= 48, >= 2 GFLOP),
  * 2 every FP64 product of the solver (for tests).  Process-wide. */
 void care_set_tensor_cores(int on);
+
+/* Test hook for the failure path: while on, the tensor-core kernels issue no
+ * operand copies, so their first bounded wait (2 s) expires; they record the
+ * error, release their tensor memory and return, and the entry point reports
+ * CARE_TIMEOUT with the context intact.  Process-wide; off by default. */
+void care_tc_test_starve(int on);
 
 /* Device scratch for care_gram_tc / care_gemm_ts (tc = 1) with a + b <= maxdim. */
 size_t care_tc_work_size(int maxdim);

@@ -26,7 +26,10 @@ LIB_PATH = os.path.join(_HERE, "libcare_b300.so")
 
 PREC_FP64 = 0
 PREC_MIXED_FP32 = 1
-PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED_FP32, "mixed_fp32": PREC_MIXED_FP32}
+PREC_MIXED_TF32 = 2
+PREC_MIXED_BF16 = 3
+PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED_FP32, "mixed_fp32": PREC_MIXED_FP32, "mixed_tf32": PREC_MIXED_TF32,
+        "mixed_bf16": PREC_MIXED_BF16}
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_ILU0 = 2
@@ -63,7 +66,9 @@ class info_t(ct.Structure):
                 ("ms_phase", ct.c_double * 4), ("ms_total", ct.c_double),
                 ("gram_ms", ct.c_double * 2), ("gram_gflop", ct.c_double * 2), ("gram_calls", ct.c_longlong * 2),
                 ("gemm_ms", ct.c_double * 2), ("gemm_gflop", ct.c_double * 2), ("gemm_calls", ct.c_longlong * 2),
-                ("tc_ms", ct.c_double), ("tc_gflop", ct.c_double), ("tc_calls", ct.c_longlong)]
+                ("tc_ms", ct.c_double), ("tc_gflop", ct.c_double), ("tc_calls", ct.c_longlong),
+                ("krylov_ms", ct.c_double), ("krylov_gbyte", ct.c_double), ("host_syncs", ct.c_longlong),
+                ("lowp_gram_calls", ct.c_longlong)]
 
 
 class op_t(ct.Structure):
@@ -110,8 +115,10 @@ def lib() -> ct.CDLL:
         "care_autotune_workspace_size": (i, [P(op_t), i, i, i, P(sz)]),
         "care_autotune": (i, [P(op_t), i, i, i, P(opts_t), vp, sz, vp, P(d)]),
         "care_kernel_launches": (ct.c_ulonglong, []),
+        "care_fp64_peak": (i, [P(d), vp]),
         "care_tc_available": (i, []),
         "care_set_tensor_cores": (None, [i]),
+        "care_tc_test_starve": (None, [i]),
         "care_tc_work_size": (sz, [i]),
         "care_gram_tc": (i, [i, i, i, i, vp, i, vp, i, vp, i, vp, sz, vp]),
         "care_gemm_ts": (i, [i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, sz, vp]),
@@ -209,7 +216,9 @@ def _info_dict(inf: info_t) -> dict:
                 res_rel_CtC=inf.res_rel_CtC, res_paper=inf.res_paper, ms_phase=list(inf.ms_phase),
                 ms_total=inf.ms_total, gram_ms=list(inf.gram_ms), gram_gflop=list(inf.gram_gflop),
                 gram_calls=list(inf.gram_calls), gemm_ms=list(inf.gemm_ms), gemm_gflop=list(inf.gemm_gflop),
-                gemm_calls=list(inf.gemm_calls), tc_ms=inf.tc_ms, tc_gflop=inf.tc_gflop, tc_calls=inf.tc_calls)
+                gemm_calls=list(inf.gemm_calls), tc_ms=inf.tc_ms, tc_gflop=inf.tc_gflop, tc_calls=inf.tc_calls,
+                krylov_ms=inf.krylov_ms, krylov_gbyte=inf.krylov_gbyte, host_syncs=inf.host_syncs,
+                lowp_gram_calls=inf.lowp_gram_calls)
 
 
 class Workspace:
@@ -429,6 +438,13 @@ def gram(X: torch.Tensor, Y: torch.Tensor):
 
 
 TC_MODES = {"f64": 0, "tf32": 1, "bf16": 2}
+
+
+def fp64_peak() -> float:
+    """Measured FP64 FMA throughput of the CUDA cores (TFLOP/s)."""
+    t = ct.c_double(0)
+    _check(lib().care_fp64_peak(ct.byref(t), _stream()), "care_fp64_peak")
+    return t.value
 
 
 def tc_available() -> bool:

@@ -507,7 +507,9 @@ struct Session {
 
 template <class T>
 static void alloc_session(Ctx& c, Session<T>& S, int n, int nnz, int m, int p, const Caps& k, bool ref) {
-  alloc_small(c, n, k.maxc, k.small, ref ? std::max(k.rcap + k.bigcap, 2 * k.bigcap) : 0);
+  // tensor-core scratch: the FP64 products of Algorithms 1-2 (reference sessions) or the
+  // low-precision Grams of the shift generation (width <= 2 x 64)
+  alloc_small(c, n, k.maxc, k.small, ref ? std::max(k.rcap + k.bigcap, 2 * k.bigcap) : 256);
   alloc_prob(c, S.P, n, m, p);
   S.in.alloc(c, n, m, k.bcap, k.adicap, k.hcap);
   S.ldct = pad_ld<T>(std::max(p, 1));
@@ -560,6 +562,19 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.ms_phase[0] += now_ms() - t1;
   care_status st = CARE_NOT_CONVERGED;
   double prev = -1.0, res = 0.0;
+  // the factor before the last Algorithm 2 (its basis stays in QZn until the next
+  // update): returned instead of the last one if the last step made the residual worse
+  int prev_r = 0;
+  std::vector<double> prev_s;
+  auto revert_if_worse = [&]() {
+    if (prev > 0 && res > prev && !prev_s.empty()) {
+      std::swap(S.R.QZ, S.R.QZn);
+      S.R.r = prev_r;
+      S.R.s = prev_s;
+      res = prev;
+      if (inf.nhist < CARE_HIST_MAX) inf.res_hist[inf.nhist++] = S.P.ctc_fro > 0 ? res / S.P.ctc_fro : res;
+    }
+  };
   for (int it = 1; it <= c.o.kmax + 1; ++it) {
     t1 = now_ms();
     materialize_Z(c, S.R, n);
@@ -581,9 +596,13 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     }
     if (prev > 0 && res / prev > c.o.stag_ratio) {
       st = CARE_STAGNATED;
+      revert_if_worse();
       break;
     }
-    if (it == c.o.kmax + 1) break;
+    if (it == c.o.kmax + 1) {
+      revert_if_worse();
+      break;
+    }
     prev = res;
     // K_k = Z Z^T B = Q_Z (s^2 .* Q_Z^T B) in u_s
     const int r = S.R.r;
@@ -602,6 +621,8 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     CARE_CUDA(cudaStreamSynchronize(c.s));
     inf.ms_phase[2] += now_ms() - t1;
     t1 = now_ms();
+    prev_r = S.R.r;
+    prev_s = S.R.s;
     alg2<T>(c, S.R, n, S.in.Z, ad.np, S.in.Z + (S.in.adicap - ad.nm), ad.nm, S.in.ldz, c.o.eta_s_mult);
     CARE_CUDA(cudaStreamSynchronize(c.s));
     inf.ms_phase[3] += now_ms() - t1;
@@ -623,6 +644,10 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.tc_ms = c.tc_ms;
   inf.tc_gflop = c.tc_gflop;
   inf.tc_calls = c.tc_calls;
+  inf.krylov_ms = c.kry_ms;
+  inf.krylov_gbyte = c.kry_gbyte;
+  inf.host_syncs = c.host_syncs;
+  inf.lowp_gram_calls = c.lowp_calls;
   for (int q = 0; q < 2; ++q) {
     inf.gram_ms[q] = c.gram_ms[q];
     inf.gram_gflop[q] = c.gram_gflop[q];
@@ -675,6 +700,10 @@ static care_status lradi_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.tc_ms = c.tc_ms;
   inf.tc_gflop = c.tc_gflop;
   inf.tc_calls = c.tc_calls;
+  inf.krylov_ms = c.kry_ms;
+  inf.krylov_gbyte = c.kry_gbyte;
+  inf.host_syncs = c.host_syncs;
+  inf.lowp_gram_calls = c.lowp_calls;
   for (int q = 0; q < 2; ++q) {
     inf.gram_ms[q] = c.gram_ms[q];
     inf.gram_gflop[q] = c.gram_gflop[q];
@@ -1050,9 +1079,11 @@ care_status care_solve(const care_csr* A, const double* B, int ldb, int m, const
       r_cap <= 0 || !(tol > 0))
     return CARE_ERR_INVALID_ARG;
   if (!A->rowptr || !A->colind || !A->val) return CARE_ERR_INVALID_ARG;
+  if (prec < CARE_PREC_FP64 || prec > CARE_PREC_MIXED_BF16) return CARE_ERR_INVALID_ARG;
   care_status st = run_guarded([&] {
     Ctx c;
     begin(c, opts, (cudaStream_t)s, work, work_bytes);
+    c.lowp = prec == CARE_PREC_MIXED_TF32 ? 1 : (prec == CARE_PREC_MIXED_BF16 ? 2 : 0);
     if (prec == CARE_PREC_FP64) return solve_impl<double>(c, A, B, ldb, m, C, ldc, p, tol, Z, ldz, r_cap, info);
     return solve_impl<float>(c, A, B, ldb, m, C, ldc, p, tol, Z, ldz, r_cap, info);
   });
@@ -1161,10 +1192,12 @@ care_status lyap_lradi(const care_csr* A, const double* B, int ldb, const double
   if (!A || A->n <= 0 || b <= 0 || !W || !Z || !work || ldw < A->n || ldz < A->n || r_cap <= 0 || !(tol > 0))
     return CARE_ERR_INVALID_ARG;
   if (m > 0 && B && K && (ldb < A->n || ldk < A->n)) return CARE_ERR_INVALID_ARG;
+  if (prec < CARE_PREC_FP64 || prec > CARE_PREC_MIXED_BF16) return CARE_ERR_INVALID_ARG;
   care_status st = run_guarded([&] {
     Ctx c;
     begin(c, opts, (cudaStream_t)s, work, work_bytes);
     const int mm = (B && K) ? m : 0;
+    c.lowp = prec == CARE_PREC_MIXED_TF32 ? 1 : (prec == CARE_PREC_MIXED_BF16 ? 2 : 0);
     if (prec == CARE_PREC_FP64) return lradi_impl<double>(c, A, B, ldb, K, ldk, mm, W, ldw, b, tol, Z, ldz, r_cap, info);
     return lradi_impl<float>(c, A, B, ldb, K, ldk, mm, W, ldw, b, tol, Z, ldz, r_cap, info);
   });
@@ -1189,6 +1222,14 @@ care_status care_residual_factor(const care_csr* A, const double* B, int ldb, in
 
 unsigned long long care_kernel_launches(void) { return care::launches(); }
 
+care_status care_fp64_peak(double* tflops, care_stream_t s) {
+  if (!tflops) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    *tflops = fp64_fma_peak_tflops((cudaStream_t)s);
+    return CARE_OK;
+  });
+}
+
 int care_tc_available(void) {
   const bool ok = tc_available();
   cudaGetLastError();
@@ -1196,6 +1237,8 @@ int care_tc_available(void) {
 }
 
 void care_set_tensor_cores(int on) { tc_set_enabled(on); }
+
+void care_tc_test_starve(int on) { tc_set_test_starve(on); }
 
 size_t care_tc_work_size(int maxdim) {
   Arena a;

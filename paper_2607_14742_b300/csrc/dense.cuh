@@ -38,9 +38,19 @@ template <class T>
 void axpby(long n, int cols, double alpha, const T* X, int ldx, double beta, T* Y, int ldy,
            cudaStream_t s);
 
+// LR-ADI complex-pair update (elementwise, see k_dense.cu): W += g^2 (Re V + d Im V);
+// the new X_+ columns g (Re V + d Im V), gi Im V of the first rp columns go to Zp,
+// those of the other b - rp columns to Zm.  V complex interleaved (ldr reals).
+template <class T>
+void cpair_update(long n, int b, int rp, const T* sol, int ldr, double g, double d, double gi, T* W, int ldw, T* Zp,
+                  T* Zm, int ldz, cudaStream_t s);
+
 // Y(:, j) *= d[j] (row-major; d on device, FP64)
 template <class T>
 void scale_cols(long n, int cols, T* Y, int ldy, const double* d, cudaStream_t s);
+
+// measured FP64 FMA throughput of the CUDA cores (TFLOP/s)
+double fp64_fma_peak_tflops(cudaStream_t s);
 
 // ---- host small dense (column-major) ---------------------------------------
 // symmetric eigendecomposition, ascending eigenvalues; V may be null

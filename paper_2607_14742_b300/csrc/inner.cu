@@ -59,7 +59,7 @@ const double* upload(Ctx& c, const std::vector<double>& h) {
 }
 
 template <class T>
-std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, const T* Y, int ldy) {
+std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, const T* Y, int ldy, bool lowp) {
   std::vector<double> h((size_t)a * b, 0.0);
   if (a == 0 || b == 0) return h;
   CARE_REQUIRE((size_t)a * b <= c.dG_cap, CARE_ERR_WORKSPACE, "gram output staging too small");
@@ -71,7 +71,13 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   CARE_CUDA(cudaEventRecord(c.ge0, c.s));
   const bool sym0 = a == b && (const void*)X == (const void*)Y && ldx == ldy;
   bool on_tc = false;
-  if (sizeof(T) == 8 && tc_use(c, n, a, b, sym0 ? a : a + b)) {
+  if (sizeof(T) == 4 && lowp && c.lowp && c.tc.ok() && a + b <= c.tc_maxdim && tc_available()) {
+    // TF32 / BF16 tensor-core Gram of the shift generation (CARE_PREC_MIXED_TF32 / _BF16)
+    tc_gram_lowp(c.lowp, n, a, b, reinterpret_cast<const float*>(X), ldx, reinterpret_cast<const float*>(Y), ldy,
+                 c.dG, b, c.tc, c.tc_maxdim, c.s);
+    c.tc_used = true;
+    c.lowp_calls++;
+  } else if (sizeof(T) == 8 && tc_use(c, n, a, b, sym0 ? a : a + b)) {
     tc_gram_f64(n, a, b, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<const double*>(Y), ldy, c.dG,
                 b, c.tc, c.tc_maxdim, c.s);
     c.tc_used = on_tc = true;
@@ -81,6 +87,7 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   CARE_CUDA(cudaEventRecord(c.ge1, c.s));
   CARE_CUDA(cudaMemcpyAsync(h.data(), c.dG, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   CARE_CUDA(cudaStreamSynchronize(c.s));
+  c.host_syncs++;
   harvest_timings(c);
   float ms = 0.f;
   CARE_CUDA(cudaEventElapsedTime(&ms, c.ge0, c.ge1));
@@ -98,18 +105,18 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   if (verbose_level() >= 1) c.ms_gram += now_ms() - t0;
   return h;
 }
-template std::vector<double> gram_h<float>(Ctx&, long, int, int, const float*, int, const float*, int);
-template std::vector<double> gram_h<double>(Ctx&, long, int, int, const double*, int, const double*, int);
+template std::vector<double> gram_h<float>(Ctx&, long, int, int, const float*, int, const float*, int, bool);
+template std::vector<double> gram_h<double>(Ctx&, long, int, int, const double*, int, const double*, int, bool);
 
 // ------------------------------------------------------------ orth_rr -----
 template <class T>
 OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double drop_rel,
                 const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo,
-                bool defer_rinv) {
+                bool defer_rinv, bool lowp_gram) {
   OrthOut o;
   CARE_REQUIRE(out == nullptr || !second_pass, CARE_ERR_INVALID_ARG, "orth_rr: out needs one pass");
   if (cols == 0) return o;
-  std::vector<double> G = gram_h<T>(c, n, cols, cols, X, ldx, X, ldx);
+  std::vector<double> G = gram_h<T>(c, n, cols, cols, X, ldx, X, ldx, lowp_gram);
   // column scaling; columns at or below their floor are dropped.  drop_rel < 0
   // selects the unscaled mode: pivots are compared with |drop_rel| * max_j G_jj,
   // i.e. the truncation is relative to the largest column of X (used to cut
@@ -197,9 +204,9 @@ OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double
   return o;
 }
 template OrthOut orth_rr<float>(Ctx&, long, int, float*, int, float*, int, double, const std::vector<double>*,
-                                bool, int, float*, int, bool);
+                                bool, int, float*, int, bool, bool);
 template OrthOut orth_rr<double>(Ctx&, long, int, double*, int, double*, int, double,
-                                 const std::vector<double>*, bool, int, double*, int, bool);
+                                 const std::vector<double>*, bool, int, double*, int, bool, bool);
 
 template <class T>
 std::vector<double> cgs2(Ctx& c, long n, const T* Q, int ldq, int r, T* X, int ldx, int cols) {
@@ -289,8 +296,10 @@ static std::vector<Shift> proj_shifts(Ctx& c, Inner<T>& in, bool hasK, const T* 
   const long n = in.n;
   const int hmax = in.hcap;
   // orthonormal basis of the (at most 32) dominant directions of range(S)
+  // the shift basis and the projected matrix only need Ritz values of a few digits:
+  // with CARE_PREC_MIXED_TF32 / _BF16 their Grams run on the tensor cores in TF32 / BF16
   OrthOut o = orth_rr<T>(c, n, h0, const_cast<T*>(S), lds, nullptr, 0, orth_drop<T>(), nullptr, false,
-                         std::min(hmax / 2, 32), in.Q, in.ldq);
+                         std::min(hmax / 2, 32), in.Q, in.ldq, false, true);
   int h = o.rank;
   int last0 = 0, lastw = h;
   int ext = 0;
@@ -309,7 +318,7 @@ static std::vector<Shift> proj_shifts(Ctx& c, Inner<T>& in, bool hasK, const T* 
   std::vector<Shift> out;
   if (h == 0) return out;
   apply_F<T>(c, in, hasK, in.Q, in.FQ, h);
-  std::vector<double> Hp = gram_h<T>(c, n, h, h, in.Q, in.ldq, in.FQ, in.ldq);  // row-major (Q^T F Q)
+  std::vector<double> Hp = gram_h<T>(c, n, h, h, in.Q, in.ldq, in.FQ, in.ldq, true);  // row-major (Q^T F Q)
   // to column-major for the host eigenvalue routine
   std::vector<double> Hc((size_t)h * h);
   for (int i = 0; i < h; ++i)
@@ -360,8 +369,20 @@ static void smw_solve(Ctx& c, Inner<T>& in, Shift p, int b, bool hasK) {
   const int chunk = std::min(kMaxRealCols, std::max(2, (c.o.krylov_chunk > 0 ? c.o.krylov_chunk : 64) * (cplx ? 2 : 1)));
   for (int c0 = 0; c0 < rc; c0 += chunk) {
     const int w = std::min(chunk, rc - c0);
+    if (!c.ke0) {
+      CARE_CUDA(cudaEventCreate(&c.ke0));
+      CARE_CUDA(cudaEventCreate(&c.ke1));
+    }
+    CARE_CUDA(cudaEventRecord(c.ke0, c.s));
     KrylovResult kr = krylov_bicgstab<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr,
                                          w, krylov_tol<T>(c), krylov_maxit<T>(c), c.o.precond, in.kw, c.s);
+    CARE_CUDA(cudaEventRecord(c.ke1, c.s));
+    CARE_CUDA(cudaEventSynchronize(c.ke1));  // the solve has synchronised already
+    float kms = 0.f;
+    CARE_CUDA(cudaEventElapsedTime(&kms, c.ke0, c.ke1));
+    c.kry_ms += kms;
+    c.kry_gbyte += kr.bytes * 1e-9;
+    c.host_syncs += 2 + kr.iters / 4;
     c.krylov_iters += kr.iters;
     c.spmm_calls += kr.spmm;
     if (kr.unconverged) c.krylov_unconverged++;
@@ -500,20 +521,8 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
       // complex pair p, conj(p) in real arithmetic:
       // W <- W + g^2 (Re V + d Im V);  Z <- [Z, g (Re V + d Im V), g sqrt(d^2+1) Im V]
       const double g = 2.0 * std::sqrt(-p.re), d = p.re / p.im;
-      std::vector<double> E((size_t)(2 * b) * b, 0.0), Ei((size_t)(2 * b) * b, 0.0);
-      for (int q = 0; q < b; ++q) {
-        E[(size_t)(2 * q) * b + q] = 1.0;
-        E[(size_t)(2 * q + 1) * b + q] = d;
-        Ei[(size_t)(2 * q + 1) * b + q] = 1.0;
-      }
-      const double* dE = upload(c, E);
-      gemm_c<T, T>(c, n, 2 * b, b, g * g, in.SOL, in.ldr, dE, b, 1.0, in.W, in.ldw);
-      if (rp) gemm_c<T, T>(c, n, 2 * b, rp, g, in.SOL, in.ldr, dE, b, 0.0, in.Z + np, in.ldz);
-      if (rm) gemm_c<T, T>(c, n, 2 * b, rm, g, in.SOL, in.ldr, dE + rp, b, 0.0, in.Z + pm0, in.ldz);
       const double gi = g * std::sqrt(d * d + 1.0);
-      const double* dEi = upload(c, Ei);
-      if (rp) gemm_c<T, T>(c, n, 2 * b, rp, gi, in.SOL, in.ldr, dEi, b, 0.0, in.Z + np + rp, in.ldz);
-      if (rm) gemm_c<T, T>(c, n, 2 * b, rm, gi, in.SOL, in.ldr, dEi + rp, b, 0.0, in.Z + pm0 + rm, in.ldz);
+      cpair_update<T>(n, b, rp, in.SOL, in.ldr, g, d, gi, in.W, in.ldw, in.Z + np, in.Z + pm0, in.ldz, c.s);
       j += 2;
     }
     if (knew) {

@@ -328,6 +328,45 @@ void axpby(long n, int cols, double alpha, const T* X, int ldx, double beta, T* 
 template void axpby<float>(long, int, double, const float*, int, double, float*, int, cudaStream_t);
 template void axpby<double>(long, int, double, const double*, int, double, double*, int, cudaStream_t);
 
+// LR-ADI update for a complex pair (p, conj p) in real arithmetic, elementwise:
+// with V = SOL (complex interleaved, column q at 2q, 2q+1) and u = Re V + d Im V,
+//   W(:, q) += g^2 u_q;
+//   q < rp:  Zp(:, q) = g u_q,          Zp(:, rp + q) = gi Im V_q;
+//   q >= rp: Zm(:, q - rp) = g u_q,     Zm(:, rm + q - rp) = gi Im V_q   (rm = b - rp).
+template <class T>
+__global__ void k_cpair_update(long n, int b, int rp, const T* __restrict__ sol, int ldr, double g, double d,
+                               double gi, T* __restrict__ W, int ldw, T* __restrict__ Zp, T* __restrict__ Zm,
+                               int ldz) {
+  const long total = n * (long)b;
+  const int rm = b - rp;
+  const T tg = (T)g, td = (T)d, tgi = (T)gi, tg2 = (T)(g * g);
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / b;
+    const int q = (int)(e % b);
+    const T re = sol[(size_t)r * ldr + 2 * q], im = sol[(size_t)r * ldr + 2 * q + 1];
+    const T u = re + td * im;
+    W[(size_t)r * ldw + q] += tg2 * u;
+    if (q < rp) {
+      Zp[(size_t)r * ldz + q] = tg * u;
+      Zp[(size_t)r * ldz + rp + q] = tgi * im;
+    } else {
+      Zm[(size_t)r * ldz + (q - rp)] = tg * u;
+      Zm[(size_t)r * ldz + rm + (q - rp)] = tgi * im;
+    }
+  }
+}
+template <class T>
+void cpair_update(long n, int b, int rp, const T* sol, int ldr, double g, double d, double gi, T* W, int ldw, T* Zp,
+                  T* Zm, int ldz, cudaStream_t s) {
+  if (n == 0 || b == 0) return;
+  k_cpair_update<T><<<device_sms() * 4, 256, 0, s>>>(n, b, rp, sol, ldr, g, d, gi, W, ldw, Zp, Zm, ldz);
+  CARE_LAUNCH();
+}
+template void cpair_update<float>(long, int, int, const float*, int, double, double, double, float*, int, float*,
+                                  float*, int, cudaStream_t);
+template void cpair_update<double>(long, int, int, const double*, int, double, double, double, double*, int,
+                                   double*, double*, int, cudaStream_t);
+
 template <class T>
 __global__ void k_scale_cols(long n, int cols, T* __restrict__ Y, int ldy, const double* __restrict__ d) {
   const long total = n * (long)cols;
@@ -403,5 +442,46 @@ void gram_noalloc(long n, int a, int b, const T* X, int ldx, const T* Y, int ldy
 template void gram_noalloc<float>(long, int, int, const float*, int, const float*, int, double*, int, cudaStream_t);
 template void gram_noalloc<double>(long, int, int, const double*, int, const double*, int, double*, int,
                                    cudaStream_t);
+
+}  // namespace care
+
+namespace care {
+
+// FP64 FMA throughput of the CUDA cores (roofline denominator of the FP64
+// products): 8 independent dependent-FMA chains per thread, full occupancy.
+__global__ void __launch_bounds__(256) k_fp64_fma_peak(int iters, double a, double b, double* out) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 12345.678) out[0] = s;  // keeps the chains live
+}
+
+double fp64_fma_peak_tflops(cudaStream_t s) {
+  const int grid = device_sms() * 8, block = 256, iters = 4096;
+  cudaEvent_t e0, e1;
+  CARE_CUDA(cudaEventCreate(&e0));
+  CARE_CUDA(cudaEventCreate(&e1));
+  double best = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {
+    CARE_CUDA(cudaEventRecord(e0, s));
+    k_fp64_fma_peak<<<grid, block, 0, s>>>(iters, 0.9999999, 1e-7, nullptr);
+    CARE_LAUNCH();
+    CARE_CUDA(cudaEventRecord(e1, s));
+    CARE_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CARE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    const double fl = 2.0 * 8.0 * iters * (double)grid * block;
+    if (rep > 0) best = std::max(best, fl / (ms * 1e-3) * 1e-12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
 
 }  // namespace care

@@ -1205,6 +1205,28 @@ done:
   k_copy_out<T><<<device_sms() * 4, kBlock, 0, s>>>(a);
   CARE_LAUNCH();
   {
+    // Algorithmic bytes (what the iteration must move, each block once per pass):
+    // a block pass is n * ld reals; the operator pass reads A^T's values and
+    // indices, row pointers and row sums; a triangular ILU(0) sweep reads about
+    // half of the factor with its indices.  Per iteration: p-update 4 passes
+    // (+1 Jacobi), two SpMMs of 3 passes + the operator, s-update 3 (+1), x/r
+    // update 8 (+2 Jacobi / ILU), and for ILU(0) two applications of 2T triangular
+    // sweeps of 3 passes (+1) each; init 6 passes; ILU(0) setup 1 + sweeps passes
+    // over the factor.
+    const double sv = sizeof(T), sf = sv * (cplx ? 2 : 1);
+    const double blk = (double)op.n * a.ld * sv;
+    const double amat = (double)op.nnz * (sv + 4) + 4.0 * (op.n + 1) + (op.rowsum ? sv * op.n : 0.0);
+    const double trisw = 0.5 * op.nnz * (sf + 4) + 8.0 * op.n;
+    const int T_ = a.tri_sweeps;
+    double per = 2 * amat;
+    if (pmode == 0) per += 21 * blk;
+    else if (pmode == 1) per += 25 * blk + 2 * sf * op.n;
+    else per += (24 + 12.0 * T_) * blk + 4.0 * T_ * trisw;
+    double setup = 6 * blk;
+    if (pmode == 2) setup += (1 + w.ilu_sweeps) * ((double)op.nnz * (2 * sf + 4) + 8.0 * op.n);
+    r.bytes = setup + per * r.iters;
+  }
+  {
     // count unconverged columns (flag != 1 among the valid state entries)
     const int nst = cplx ? cols / 2 : cols;
     std::vector<KState> hs(nst);

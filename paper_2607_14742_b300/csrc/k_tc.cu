@@ -15,7 +15,7 @@ namespace {
 constexpr int BM = 128;          // output rows per tile (TMEM lanes)
 constexpr int BN = 64;           // output columns per tile (accumulator columns)
 constexpr int ROWB = 64;         // bytes per staged operand row (64-byte swizzle)
-constexpr int NSLICE = 7;        // slices of an FP64 operand
+constexpr int NSLICE = 8;        // slices of an FP64 operand
 constexpr int CHUNK = 128;       // K-rows between exact flushes (FP64 mode)
 constexpr int SLAB = 32768;      // K-rows (Gram) / output rows (X S) per slicing pass
 constexpr int EPI_WARPS = 8;
@@ -28,18 +28,18 @@ constexpr long long WAIT_NS = 2000000000LL;  // bound on any single mbarrier wai
 constexpr int ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_ACC = 3, ERR_WAIT_ACCE = 4;
 
 // ---- slice pairs of the FP64 mode ------------------------------------------
-// Pairs (a, b) with a + b <= 7.  Tail pairs (a + b >= 5, accumulator 5) come
+// Pairs (a, b) with a + b <= 8.  Tail pairs (a + b >= 5, accumulator 5) come
 // first within every K-step so that the MMAs of a new chunk can start while the
 // epilogue still drains the exact groups of the previous one; the exact pairs
 // follow, grouped by a + b (accumulator a + b).
 struct PairTable {
   int n;
-  int a[40], b[40], acc[40], first[40];
+  int a[48], b[48], acc[48], first[48];
 };
 constexpr PairTable make_pairs() {
   PairTable t{};
   int k = 0;
-  for (int s = 5; s <= 7; ++s)
+  for (int s = 5; s <= 8; ++s)
     for (int a = 0; a < NSLICE; ++a) {
       const int b = s - a;
       if (b < 0 || b >= NSLICE) continue;
@@ -53,8 +53,9 @@ constexpr PairTable make_pairs() {
   return t;
 }
 constexpr PairTable kPairs = make_pairs();
-constexpr int kFirstExact = 19;  // index of the first exact pair
-static_assert(kPairs.n == 34, "34 slice pairs with a + b <= 7");
+constexpr int kNumPairs = 43;
+constexpr int kFirstExact = 28;  // index of the first exact pair
+static_assert(kPairs.n == kNumPairs, "43 slice pairs with a + b <= 8");
 static_assert(kPairs.acc[kFirstExact] == 0 && kPairs.acc[kFirstExact - 1] == 5, "pair order");
 // device copy (constant bank; the MMA loop indexes it with unrolled constants)
 __constant__ PairTable c_pairs = make_pairs();
@@ -180,6 +181,7 @@ struct TcArgs {
   int y_f32;
   double alpha, beta;
   int* err;
+  int starve;        // test hook: issue no copies (the first wait then expires)
 };
 
 // MODE 0: FP64 slices (kind::f16, BF16 slices); 1: TF32 (kind::tf32, FP32
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int issued = 0;
       uint32_t last_par[C::STAGES];
       for (int s = 0; s < C::STAGES; ++s) last_par[s] = 0;
-      for (int it = 0; it < nst; ++it) {
+      for (int it = 0; it < nst && !g.starve; ++it) {
         if (!mbar_wait(empty + stage, eph, abort_flag, g.err, ERR_WAIT_EMPTY)) break;
         mbar_arrive_tx(full + stage, C::STAGE_BYTES);
         uint8_t* st = sm + stage * C::STAGE_BYTES;
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int kk = 0; kk < C::KEL / C::KSTEP; ++kk) {
             if constexpr (MODE == 0) {
 #pragma unroll
-              for (int p = 0; p < 34; ++p) {
+              for (int p = 0; p < kNumPairs; ++p) {
                 if (p == kFirstExact && c > 0 && st == 0 && kk == 0) {
                   // the epilogue must have read the previous chunk's exact groups
                   if (!mbar_wait(acce, aeph, abort_flag, g.err, ERR_WAIT_ACCE)) {
@@ -485,8 +487,8 @@ __global__ void k_tc_colexp(long rows, int cols, const double* __restrict__ X, l
   }
 }
 
-// 49-bit fixed point of x relative to 2^e (|x| < 2^e), rounded to nearest
-__device__ __forceinline__ long long fixed49(double x, int e) {
+// 56-bit fixed point of x relative to 2^e (|x| < 2^e), rounded to nearest
+__device__ __forceinline__ long long fixed56(double x, int e) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((u >> 52) & 0x7FF);
   unsigned long long M = u & 0xFFFFFFFFFFFFFull;
@@ -494,16 +496,19 @@ __device__ __forceinline__ long long fixed49(double x, int e) {
   if (E == 0) Ee = 1;
   else M |= 1ull << 52;
   if (M == 0) return 0;
-  const int sh = Ee - 1026 - e;  // x * 2^(49-e) = M * 2^sh, sh <= -4
-  if (sh >= 0) return 0;        // not reached for |x| < 2^e
+  const int sh = Ee - 1019 - e;  // x * 2^(56-e) = M * 2^sh, sh <= 3
+  if (sh >= 0) {
+    const long long F = (long long)(M << sh);  // exact: M < 2^53, |F| < 2^56
+    return (u >> 63) ? -F : F;
+  }
   const int r = -sh;
   if (r >= 63) return 0;
   const long long F = (long long)((M + (1ull << (r - 1))) >> r);
   return (u >> 63) ? -F : F;
 }
 
-__device__ __forceinline__ void split7(long long F, int (&s)[NSLICE]) {
-  // round-to-nearest base-2^7 digits: F = sum_a s_a 2^(7(6-a)), |s_0| <= 128, |s_a| <= 64
+__device__ __forceinline__ void split_digits(long long F, int (&s)[NSLICE]) {
+  // round-to-nearest base-2^7 digits: F = sum_a s_a 2^(7(7-a)), |s_0| <= 128, |s_a| <= 64
 #pragma unroll
   for (int a = 0; a < NSLICE - 1; ++a) {
     const int sh = 7 * (NSLICE - 1 - a);
@@ -542,7 +547,7 @@ __global__ void k_tc_slice_T(long rows, int cols, const double* __restrict__ X, 
       const long k = k0 + kk;
       if (k >= rows) continue;
       int s[NSLICE];
-      split7(ei == INT_MIN ? 0 : fixed49(tile[kk][ii], ei), s);
+      split_digits(ei == INT_MIN ? 0 : fixed56(tile[kk][ii], ei), s);
 #pragma unroll
       for (int a = 0; a < NSLICE; ++a) dst[a * slice_stride + (long)i * ldk + k] = slice_bf16(s[a], a);
     }
@@ -564,7 +569,7 @@ __global__ void k_tc_slice_N(long rows, int cols, const double* __restrict__ X, 
     if (lane == 0) e[r] = m == INT_MIN ? 0 : m;
     for (int k = lane; k < cols; k += 32) {
       int s[NSLICE];
-      split7(m == INT_MIN ? 0 : fixed49(xr[k], m), s);
+      split_digits(m == INT_MIN ? 0 : fixed56(xr[k], m), s);
 #pragma unroll
       for (int a = 0; a < NSLICE; ++a) dst[a * slice_stride + r * ldk + k] = slice_bf16(s[a], a);
     }
@@ -655,9 +660,11 @@ void make_map(CUtensorMap* m, bool f32, const void* base, long k_len, long rows,
   CARE_REQUIRE(r == CUDA_SUCCESS, CARE_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 }
 
+int g_tc_starve = 0;
+
 template <int MODE>
-void launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, const TcArgs& g, int tiles, int splits,
-               cudaStream_t s) {
+void launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs g, int tiles, int splits, cudaStream_t s) {
+  g.starve = g_tc_starve;
   using C = TcCfg<MODE>;
   static std::once_flag once[64];
   int dev = 0;
@@ -675,6 +682,8 @@ void launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, const TcArgs& g, in
 long round_up(long x, long m) { return (x + m - 1) / m * m; }
 
 }  // namespace
+
+void tc_set_test_starve(int on) { g_tc_starve = on ? 1 : 0; }
 
 static int g_tc_enabled = 1;
 void tc_set_enabled(int on) { g_tc_enabled = on < 0 ? 0 : (on > 2 ? 2 : on); }

@@ -60,6 +60,7 @@ struct KrylovResult {
   int iters = 0;
   int unconverged = 0;  // columns not converged (limit or breakdown)
   long long spmm = 0;
+  double bytes = 0.0;   // algorithmic HBM bytes of the solve (see krylov_bicgstab)
 };
 
 // Preconditioner of a solve: 0 none, 1 Jacobi, 2 ILU(0).

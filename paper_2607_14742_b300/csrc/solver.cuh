@@ -48,8 +48,13 @@ struct Ctx {
   int tc_maxdim = 0;
   bool tc_used = false;
   int lowp = 0;  // low-precision tensor-core Grams of the shift generation: 0 off, 1 TF32, 2 BF16
+  long long lowp_calls = 0;
   double tc_ms = 0.0, tc_gflop = 0.0;  // device time and FP64-equivalent GFLOP of the sliced products
   long long tc_calls = 0;
+  // device time (CUDA events around each block Krylov solve) and its algorithmic bytes
+  double kry_ms = 0.0, kry_gbyte = 0.0;
+  cudaEvent_t ke0 = nullptr, ke1 = nullptr;
+  long long host_syncs = 0;  // stream synchronisations of the host control
   bool counting() const { return ar.counting(); }
   Ctx() = default;
   Ctx(const Ctx&) = delete;
@@ -57,6 +62,8 @@ struct Ctx {
   ~Ctx() {
     if (ge0) cudaEventDestroy(ge0);
     if (ge1) cudaEventDestroy(ge1);
+    if (ke0) cudaEventDestroy(ke0);
+    if (ke1) cudaEventDestroy(ke1);
     for (const PendingTiming& t : tpend) {
       cudaEventDestroy(t.e0);
       cudaEventDestroy(t.e1);
@@ -138,8 +145,11 @@ inline void gemm_c(Ctx& c, long n, int a, int b, double alpha, const Ti* X, int 
 
 // host <-> device helpers for small matrices
 const double* upload(Ctx& c, const std::vector<double>& h);
+// lowp: the Gram may run on the tensor cores in TF32 / BF16 (Ctx::lowp) -- only for
+// products whose use tolerates ~1e-3 relative error (shift generation)
 template <class T>
-std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, const T* Y, int ldy);
+std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, const T* Y, int ldy,
+                           bool lowp = false);
 
 // Rank-revealing orthonormalisation X (n x cols) -> Q (in place, n x rank) with
 // X = Q T (T rank x cols, row-major).  Column-scaled eigendecomposition of the
@@ -161,7 +171,7 @@ struct OrthOut {
 template <class T>
 OrthOut orth_rr(Ctx& c, long n, int cols, T* X, int ldx, T* buf, int ldb, double drop_rel,
                 const std::vector<double>* colfloor2, bool second_pass, int max_rank, T* out, int ldo,
-                bool defer_rinv = false);
+                bool defer_rinv = false, bool lowp_gram = false);
 
 // X (n x cols) -= Q (Q^T X) twice (classical Gram-Schmidt with
 // reorthogonalisation); returns the r x cols coefficients.

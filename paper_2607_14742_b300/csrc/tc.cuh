@@ -2,11 +2,11 @@
 //
 // Two arithmetic modes share one kernel:
 //  * FP64-accurate (slices): every FP64 operand row is scaled by a power of two
-//    2^-e (its largest entry below 1), rounded to a 49-bit fixed-point integer and
-//    split exactly into 7 signed 7-bit slices (round-to-nearest digits, |s_0| <= 128,
+//    2^-e (its largest entry below 1), rounded to a 56-bit fixed-point integer and
+//    split exactly into 8 signed 7-bit slices (round-to-nearest digits, |s_0| <= 128,
 //    |s_a| <= 64 for a >= 1), each stored in BF16 as s_a 2^-7(a+1) (exact: at most
 //    8 significant bits).  The slice products s_a t_b 2^-7(a+b+2) are exact in the
-//    tensor core; the 34 pairs with a + b <= 7 are accumulated in FP32 in TMEM.
+//    tensor core; the 43 pairs with a + b <= 8 are accumulated in FP32 in TMEM.
 //    Pairs with a + b <= 4 go to one accumulator per a + b ("exact groups"): over a
 //    chunk of 128 K-rows their sums are integers below 2^22 in units of
 //    2^-7(a+b+2), so FP32 holds them exactly in any summation order; after every
@@ -14,11 +14,12 @@
 //    fixed-point accumulator per output entry (exact).  Pairs with a + b >= 5 carry
 //    weights below 2^-35 of the leading term and go to a single FP32 tail
 //    accumulator.  The result (int64 * 2^-42 + tail) * 2^(e_i + f_j) differs from
-//    the exact product of the FP64 inputs by the 49-bit input rounding (relative to
-//    each row's largest entry), the dropped pairs (below 2^-56) and the tail's FP32
-//    rounding: FP64-class accuracy on the BF16 tensor pipe.  This is the splitting
-//    idea of Ozaki et al. (Numer. Algorithms 59, 2012), realised with exact
-//    integer chunk sums because B300 has neither a fast FP64 nor INT8 tensor path.
+//    the exact product of the FP64 inputs by the 56-bit input rounding (2^-57
+//    relative to each row's largest entry), the dropped pairs (below 2^-63 of it)
+//    and the tail's FP32 rounding, while the leading sums are exact: no larger than
+//    the accumulation error of an FP64 dot product.  This is the splitting idea of
+//    Ozaki et al. (Numer. Algorithms 59, 2012), realised with exact integer chunk
+//    sums because B300 has neither a fast FP64 nor INT8 tensor path.
 //  * TF32 / BF16 (plain): FP32 inputs rounded by the tensor core (kind::tf32) or
 //    converted to BF16 (kind::f16), FP32 accumulation in TMEM.
 //
@@ -82,6 +83,10 @@ void tc_gemm_ts_f64(long n, int a, int b, double alpha, const double* X, int ldx
 // or BF16 (kind = 2) inputs and FP32 accumulation on the tensor cores.
 void tc_gram_lowp(int kind, long n, int a, int b, const float* X, int ldx, const float* Y, int ldy, double* G,
                   int ldg, const TcScratch& sc, int maxdim, cudaStream_t s);
+
+// Test hook: while on, the product kernels issue no operand copies, so their first
+// bounded wait expires and they return through the error path.
+void tc_set_test_starve(int on);
 
 // Reads and clears the device error word (synchronises s).  Returns the code.
 int tc_check(const TcScratch& sc, cudaStream_t s);

@@ -152,3 +152,18 @@ def test_care_solve_with_every_fp64_product_on_tensor_cores(pb, prec):
     assert np.linalg.norm(Z @ Z.T - X) <= 1e-8 * np.linalg.norm(X)
     R = od.riccati_residual(prob.A.to_dense(), prob.B, prob.C, Z @ Z.T)
     assert np.linalg.norm(R) <= 1e-12 * np.linalg.norm(prob.C.T @ prob.C) * 10
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+def test_care_solve_lowp_shift_grams(pb, prec):
+    """CARE_PREC_MIXED_TF32 / _BF16: the Grams of the shift generation run on the tensor
+    cores in TF32 / BF16; the refinement still reaches residual 1e-12 and the oracle's
+    X* to 1e-8 (the shifts only steer the convergence of LR-ADI)."""
+    prob = ci.config_small_fdm()
+    X = od.newton_care(prob.A.to_dense(), prob.B, prob.C)["X"]
+    A = pb.CSR.from_arrays(prob.A.n, prob.A.rowptr, prob.A.colind, prob.A.val)
+    Z, info = pb.care_solve(A, prob.B, prob.C, tol=1e-12, prec=prec, r_cap=256)
+    assert info["status"] == "CARE_OK", info
+    assert info["lowp_gram_calls"] > 0
+    Z = Z.cpu().numpy()
+    assert np.linalg.norm(Z @ Z.T - X) <= 1e-8 * np.linalg.norm(X)
