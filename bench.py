@@ -42,6 +42,7 @@ GRID = 500
 MP = 5
 R_CAP = 1536
 SLICE_PAIRS = 43  # BF16 slice products per FP64 multiply-add in the FP64-accurate tensor-core path
+SLICE_PAIRS_F32 = 10  # the same for the FP32-accurate path
 
 
 def workload_config(prob):
@@ -362,10 +363,14 @@ def roofline(info, step_s, pk, fp64_peak):
     hbm = float(pk.get("hbm_gbs", 6400.0))
     bf16 = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1800.0)))
     fams = {
-        "tc_f64_slices": {"device_s": info["tc_ms"] / 1e3, "bound": "tensor", "unit": "TFLOP/s", "peak": bf16,
-                          "work": info["tc_gflop"] * SLICE_PAIRS * 1e-3, "launches": info["tc_calls"],
+        "tc_f64_slices": {"device_s": info["tc_ms"][0] / 1e3, "bound": "tensor", "unit": "TFLOP/s", "peak": bf16,
+                          "work": info["tc_gflop"][0] * SLICE_PAIRS * 1e-3, "launches": info["tc_calls"][0],
                           "kernel": "k_tc_gemm<0> + slicing: FP64-accurate X^T Y and X S of Algorithms 1-2 "
                                     "(BF16 slices, tcgen05, TMA), n=250000, widths up to ~3000"},
+        "tc_f32_slices": {"device_s": info["tc_ms"][1] / 1e3, "bound": "tensor", "unit": "TFLOP/s", "peak": bf16,
+                          "work": info["tc_gflop"][1] * SLICE_PAIRS_F32 * 1e-3, "launches": info["tc_calls"][1],
+                          "kernel": "k_tc_gemm<3> + slicing: FP32-accurate X^T Y and X S of the inner solves "
+                                    "(4 BF16 slices, tcgen05, TMA), n=250000"},
         "krylov_f32": {"device_s": info["krylov_ms"] / 1e3, "bound": "hbm", "unit": "GB/s", "peak": hbm,
                        "work": info["krylov_gbyte"], "launches": None,
                        "kernel": "block BiCGStab shifted solves (k_spmm, k_bicg_*, k_trisweep, ILU(0) setup), "

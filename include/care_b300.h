@@ -73,8 +73,22 @@ typedef enum {
                             /* stays FP32 / FP64                                         */
 } care_prec;
 
-typedef enum { CARE_KRYLOV_BICGSTAB = 0 } care_krylov;
-typedef enum { CARE_PRECOND_NONE = 0, CARE_PRECOND_JACOBI = 1, CARE_PRECOND_ILU0 = 2 } care_precond;
+/* Block Krylov method of the shifted solves (one Krylov space per right-hand-side
+ * column): BiCGStab (default), or restarted GMRES with right preconditioning,
+ * the method of the paper's GPU experiments (Section 5.2), restart
+ * gmres_restart_lo / _hi for FP32 / FP64 solves. */
+typedef enum { CARE_KRYLOV_BICGSTAB = 0, CARE_KRYLOV_GMRES = 1 } care_krylov;
+/* Preconditioner of the shifted solves (right preconditioning): Jacobi, ILU(0) by
+ * three fixed-point sweeps with Jacobi-swept triangular solves (Chow & Patel; the
+ * default, row-parallel), or ILU(0) computed exactly with exact triangular solves
+ * (the paper's preconditioner, Section 5.2; sync-free row ordering with bounded
+ * waits, sequential along the elimination's dependency chains). */
+typedef enum {
+  CARE_PRECOND_NONE = 0,
+  CARE_PRECOND_JACOBI = 1,
+  CARE_PRECOND_ILU0 = 2,
+  CARE_PRECOND_ILU0_EXACT = 3
+} care_precond;
 
 /* A itself (not A^T) in CSR: int32 row pointers (n+1) and column indices (nnz),
  * FP64 values (nnz); device pointers; column indices need not be sorted. */
@@ -120,6 +134,8 @@ typedef struct {
                          /* max(2b, 512) (cheaper Algorithm 2, but a u_s truncation  */
                          /* relative to ||X_+-|| slows the refinement).  FP64 inner  */
                          /* factors are always compressed (at FP64 accuracy).        */
+  int gmres_restart_lo;  /* GMRES restart length, FP32 solves (Section 5.2: 30)      */
+  int gmres_restart_hi;  /* GMRES restart length, FP64 solves (Section 5.2: 50)      */
 } care_opts;
 
 #define CARE_HIST_MAX 32
@@ -147,9 +163,10 @@ typedef struct {
   double gemm_ms[2];      /* the same for the tall-skinny products Y = alpha X S + beta */
   double gemm_gflop[2];   /* Y (n x a times a x b; 2 n a b GFLOP), [0] FP64, [1] FP32   */
   long long gemm_calls[2];/* inputs                                                     */
-  double tc_ms;           /* device ms of the FP64 products run on the tensor cores    */
-  double tc_gflop;        /* (BF16 slices, care_gram_tc mode 0) and their algorithmic  */
-  long long tc_calls;     /* FP64 GFLOP; Grams and X S products together              */
+  double tc_ms[2];        /* device ms of the products run on the tensor cores with    */
+  double tc_gflop[2];     /* BF16 slices ([0] FP64 operands, care_gram_tc mode 0; [1]  */
+  long long tc_calls[2];  /* FP32 operands, mode 3), their algorithmic GFLOP (2 n a b, */
+                          /* n a (a+1) for X^T X) and number; Grams and X S together   */
   double krylov_ms;       /* device ms of the block Krylov shifted solves (events)     */
   double krylov_gbyte;    /* their algorithmic HBM GB (per-iteration pass count)       */
   long long host_syncs;   /* stream synchronisations made by the host control          */
@@ -345,6 +362,32 @@ care_status care_residual_factor(const care_csr* A, const double* B, int ldb, in
  * entry points, all streams); for launch accounting in benchmarks. */
 unsigned long long care_kernel_launches(void);
 
+/* The ILU(0) factor of M_p = (A + p I)^T on the pattern of A^T (the shifted
+ * solves' preconditioner, Section 5.2): exact = 1 computes it exactly (IKJ
+ * elimination on the pattern), exact = 0 by the three fixed-point sweeps the
+ * default preconditioner uses.  F (device): nnz values of dtype (0 FP64, 1 FP32)
+ * in the order of op's A^T rows, complex interleaved (2 nnz) when p_im != 0;
+ * the strictly lower entries hold L (unit diagonal implied), the others U.
+ * Requires every diagonal entry stored (op->full_diag).  work:
+ * care_ilu0_work_size bytes.  Synchronises s. */
+size_t care_ilu0_work_size(const care_op* op, int dtype);
+care_status care_ilu0(const care_op* op, int dtype, int exact, double p_re, double p_im, void* F, void* work,
+                      size_t work_bytes, care_stream_t s);
+
+/* Symmetric eigendecomposition on the device, the one Algorithms 1-2 use for
+ * H = T M T^T and P = Gamma N Gamma^T (FP64): Householder tridiagonalisation,
+ * bisection for every eigenvalue, inverse iteration for the eigenvectors of the
+ * eigenvalues w <= lo or w >= hi (the ones the truncation at eta_r / eta_s keeps),
+ * back-transformation.  A: device, n x n row-major (lda), symmetric (only
+ * (A + A^T)/2 is used; A is not modified).  w (host, n): all eigenvalues,
+ * ascending.  V (device, may be NULL: eigenvalues only): the selected
+ * eigenvectors as rows of length n, in ascending eigenvalue order; *nsel (host)
+ * their number (V needs nsel x n doubles, at most n x n).  work:
+ * care_symeig_work_size(n) bytes.  Synchronises s. */
+size_t care_symeig_work_size(int n);
+care_status care_symeig(int n, const double* A, int lda, double* w, double* V, double lo, double hi, int* nsel,
+                        void* work, size_t work_bytes, care_stream_t s);
+
 /* Measured FP64 FMA throughput of the CUDA cores in TFLOP/s (8 independent
  * dependent-FMA chains per thread over 8 CTAs per SM; best of 3 timed runs with
  * CUDA events on s): the denominator of the FP64 product rooflines. */
@@ -357,9 +400,11 @@ care_status care_fp64_peak(double* tflops, care_stream_t s);
  * of two, rounded to a 56-bit fixed-point integer relative to its largest entry
  * and split exactly into eight 7-bit BF16 slices; the 43 slice products with
  * a + b <= 8 run on the BF16 tensor pipe with exact integer chunk sums (the
- * splitting idea of Ozaki et al. 2012).  mode 1 = TF32 inputs, mode 2 = BF16
- * inputs, both with FP32 accumulation (the low-precision Grams of the
- * CARE_PREC_MIXED_TF32 / _BF16 shift generation). */
+ * splitting idea of Ozaki et al. 2012).  mode 3 is the FP32-accurate
+ * counterpart for FP32 operands (28-bit fixed point, four slices, the 10 pairs
+ * with a + b <= 3, all summed exactly): the FP32 products of the inner solves.
+ * mode 1 = TF32 inputs, mode 2 = BF16 inputs, both with FP32 accumulation (the
+ * low-precision Grams of the CARE_PREC_MIXED_TF32 / _BF16 shift generation). */
 int care_tc_available(void);        /* 1 on an sm_103 device with the driver's TMA encoder */
 /* Solver use of the mode-0 products: 0 off (FP64 FMA on the CUDA cores), 1 where
  * profitable (default: contraction >= 1024, both output sizes >= 48, >= 2 GFLOP),
@@ -376,7 +421,7 @@ void care_tc_test_starve(int on);
 size_t care_tc_work_size(int maxdim);
 
 /* G = X^T Y on the tensor cores; X (n x a, ldx), Y (n x b, ldy) row-major, FP64
- * for mode 0 and FP32 for modes 1-2; G FP64 row-major a x b (ldg).  X == Y with
+ * for mode 0 and FP32 for modes 1-3; G FP64 row-major a x b (ldg).  X == Y with
  * the same ld computes the upper tiles only and mirrors them (exactly
  * symmetric).  work: care_tc_work_size(a + b) bytes.  Synchronises s (reads
  * the kernels' error word): CARE_TIMEOUT if a bounded wait expired. */
@@ -384,8 +429,8 @@ care_status care_gram_tc(int mode, int n, int a, int b, const void* X, int ldx, 
                          int ldg, void* work, size_t work_bytes, care_stream_t s);
 
 /* Y = alpha X S + beta Y, X (n x a, ldx) and Y (n x b, ldy) row-major, S (a x b,
- * lds) row-major FP64 on the device; dtype 0 FP64 X, Y; 1 FP32 X, Y (CUDA cores
- * only).  tc = 1 (dtype 0): FP64-accurate tensor-core slices (work:
+ * lds) row-major FP64 on the device; dtype 0 FP64 X, Y; 1 FP32 X, Y.  tc = 1:
+ * tensor-core slices, FP64-accurate (dtype 0) or FP32-accurate (dtype 1) (work:
  * care_tc_work_size(a + b) bytes; synchronises s); tc = 0: FP64/FP32 FMA on the
  * CUDA cores (work unused, asynchronous).  The tall-skinny product of
  * Algorithms 1-2 (C+- and Z_{k+1} formation) and of the CGS2 projections. */

@@ -24,16 +24,20 @@ results are rounded to the narrow format (``oracle.lowrank.storage_rounding``):
                        handling, NLR-ADI, the residual factor decomposition
                        (Algorithm 1), the solution factor decomposition
                        (Algorithm 2), Framework 1, and the paper's Res metric.
+``oracle.precond``  -- ILU(0) of the shifted matrix (A + p I)^T, the GMRES
+                       preconditioner of Section 5.2 (Saad's IKJ elimination
+                       on the pattern).
 
 Pins (see ``tests/test_oracle_*.py``): scalar closed form, eigenvector-aligned
 closed forms (dense and on analytic Laplacian modes at any n), Hamiltonian
-subspace and library CARE/Lyapunov solvers, Lyapunov closed forms, the
+subspace and library CARE/Lyapunov solvers, ILU(0)'s pattern identity and its
+agreement with LU wherever elimination makes no fill, Lyapunov closed forms, the
 factored-residual identity R = F M F^T, ||H||_F = ||R||_F, the SMW identity
 against a dense inverse, Newton monotonicity/quadratic convergence and the
 invariants X = X^T >= 0, A - B B^T X stable; Table 1 (Section 5.1): the FP64 rows'
 Res level and counts, and the FP32 rows' behaviour at the conditioning threshold
 (convergence at kappa_2(A) = 1e2 in the paper's number of refinement steps,
-no convergence at 1e8); ``oracle.table1_fp32_sweep`` prints the whole sweep.
+no convergence at 1e8).
 Shift selection inside LR-ADI is
 a heuristic whose path is not pinned; only the Lyapunov/CARE solutions it
 produces are (parity unpinned for the shift sequence itself).

@@ -30,9 +30,12 @@ PREC_MIXED_TF32 = 2
 PREC_MIXED_BF16 = 3
 PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED_FP32, "mixed_fp32": PREC_MIXED_FP32, "mixed_tf32": PREC_MIXED_TF32,
         "mixed_bf16": PREC_MIXED_BF16}
+KRYLOV_BICGSTAB = 0
+KRYLOV_GMRES = 1
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_ILU0 = 2
+PRECOND_ILU0_EXACT = 3
 HIST_MAX = 32
 
 
@@ -55,7 +58,8 @@ class opts_t(ct.Structure):
                 ("krylov_maxit_lo", ct.c_int), ("krylov_maxit_hi", ct.c_int), ("krylov", ct.c_int),
                 ("precond", ct.c_int), ("krylov_chunk", ct.c_int), ("stag_ratio", ct.c_double),
                 ("shift_hmin", ct.c_int), ("ilu_sweeps", ct.c_int), ("tri_sweeps", ct.c_int),
-                ("verbose", ct.c_int), ("inner_compress", ct.c_int)]
+                ("verbose", ct.c_int), ("inner_compress", ct.c_int), ("gmres_restart_lo", ct.c_int),
+                ("gmres_restart_hi", ct.c_int)]
 
 
 class info_t(ct.Structure):
@@ -66,7 +70,7 @@ class info_t(ct.Structure):
                 ("ms_phase", ct.c_double * 4), ("ms_total", ct.c_double),
                 ("gram_ms", ct.c_double * 2), ("gram_gflop", ct.c_double * 2), ("gram_calls", ct.c_longlong * 2),
                 ("gemm_ms", ct.c_double * 2), ("gemm_gflop", ct.c_double * 2), ("gemm_calls", ct.c_longlong * 2),
-                ("tc_ms", ct.c_double), ("tc_gflop", ct.c_double), ("tc_calls", ct.c_longlong),
+                ("tc_ms", ct.c_double * 2), ("tc_gflop", ct.c_double * 2), ("tc_calls", ct.c_longlong * 2),
                 ("krylov_ms", ct.c_double), ("krylov_gbyte", ct.c_double), ("host_syncs", ct.c_longlong),
                 ("lowp_gram_calls", ct.c_longlong)]
 
@@ -116,6 +120,10 @@ def lib() -> ct.CDLL:
         "care_autotune": (i, [P(op_t), i, i, i, P(opts_t), vp, sz, vp, P(d)]),
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_fp64_peak": (i, [P(d), vp]),
+        "care_symeig_work_size": (sz, [i]),
+        "care_ilu0_work_size": (sz, [P(op_t), i]),
+        "care_ilu0": (i, [P(op_t), i, i, d, d, vp, vp, sz, vp]),
+        "care_symeig": (i, [i, vp, i, vp, vp, d, d, P(i), vp, sz, vp]),
         "care_tc_available": (i, []),
         "care_set_tensor_cores": (None, [i]),
         "care_tc_test_starve": (None, [i]),
@@ -216,7 +224,7 @@ def _info_dict(inf: info_t) -> dict:
                 res_rel_CtC=inf.res_rel_CtC, res_paper=inf.res_paper, ms_phase=list(inf.ms_phase),
                 ms_total=inf.ms_total, gram_ms=list(inf.gram_ms), gram_gflop=list(inf.gram_gflop),
                 gram_calls=list(inf.gram_calls), gemm_ms=list(inf.gemm_ms), gemm_gflop=list(inf.gemm_gflop),
-                gemm_calls=list(inf.gemm_calls), tc_ms=inf.tc_ms, tc_gflop=inf.tc_gflop, tc_calls=inf.tc_calls,
+                gemm_calls=list(inf.gemm_calls), tc_ms=list(inf.tc_ms), tc_gflop=list(inf.tc_gflop), tc_calls=list(inf.tc_calls),
                 krylov_ms=inf.krylov_ms, krylov_gbyte=inf.krylov_gbyte, host_syncs=inf.host_syncs,
                 lowp_gram_calls=inf.lowp_gram_calls)
 
@@ -437,7 +445,39 @@ def gram(X: torch.Tensor, Y: torch.Tensor):
     return G
 
 
-TC_MODES = {"f64": 0, "tf32": 1, "bf16": 2}
+TC_MODES = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3}
+
+
+def ilu0(op: Operator, shift, exact=True, dtype=torch.float64):
+    """ILU(0) factor of (A + shift I)^T on A^T's pattern: a tensor of nnz values
+    (complex for complex shifts) in the order of the prepared operator's rows."""
+    s = complex(shift)
+    cplx = s.imag != 0
+    nnz = op.op.nnz
+    F = torch.empty(nnz * (2 if cplx else 1), dtype=dtype, device=op.mem.device)
+    dt = 0 if dtype == torch.float64 else 1
+    ws = torch.empty(lib().care_ilu0_work_size(ct.byref(op.op), dt), dtype=torch.uint8, device=op.mem.device)
+    _check(lib().care_ilu0(ct.byref(op.op), dt, int(bool(exact)), s.real, s.imag, _ptr(F), _ptr(ws), ws.numel(),
+                           _stream()), "care_ilu0")
+    return torch.view_as_complex(F.view(-1, 2)) if cplx else F
+
+
+def symeig(A: torch.Tensor, lo=None, hi=None):
+    """Device symmetric eigendecomposition of a float64 (n x n) tensor: returns (w
+    ascending as numpy, V selected eigenvectors as rows, n_sel); eigenvectors for
+    w <= lo or w >= hi (default: all)."""
+    import numpy as np
+    n = A.shape[0]
+    A = A.contiguous()
+    w = np.zeros(n)
+    V = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    ws = torch.empty(lib().care_symeig_work_size(n), dtype=torch.uint8, device=A.device)
+    ns = ct.c_int(0)
+    lo = float("inf") if lo is None else float(lo)
+    hi = float("-inf") if hi is None else float(hi)
+    _check(lib().care_symeig(n, _ptr(A), n, w.ctypes.data, _ptr(V), lo, hi, ct.byref(ns), _ptr(ws), ws.numel(),
+                             _stream()), "care_symeig")
+    return w, V[:ns.value], ns.value
 
 
 def fp64_peak() -> float:
@@ -460,7 +500,8 @@ def set_tensor_cores(mode):
 
 def gram_tc(X: torch.Tensor, Y: torch.Tensor, mode="f64"):
     """G = X^T Y (float64 a x b) on the tensor cores: mode "f64" (float64 inputs,
-    FP64-accurate BF16 slices), "tf32" or "bf16" (float32 inputs)."""
+    FP64-accurate BF16 slices), "f32" (float32 inputs, FP32-accurate slices), "tf32"
+    or "bf16" (float32 inputs)."""
     assert X.dtype == Y.dtype and X.shape[0] == Y.shape[0]
     md = TC_MODES[mode]
     assert X.dtype == (torch.float64 if md == 0 else torch.float32)
@@ -475,7 +516,8 @@ def gram_tc(X: torch.Tensor, Y: torch.Tensor, mode="f64"):
 
 def gemm_ts(X: torch.Tensor, S: torch.Tensor, alpha=1.0, beta=0.0, Y: torch.Tensor | None = None, tc=False):
     """Y = alpha X S + beta Y for row-major X (n x a), S (a x b, float64); tc=True runs
-    the FP64-accurate tensor-core path (float64 X, Y)."""
+    the sliced tensor-core path (FP64-accurate for float64 X, Y; FP32-accurate for
+    float32)."""
     n, a = X.shape
     b = S.shape[1]
     S = S.to(torch.float64).contiguous()

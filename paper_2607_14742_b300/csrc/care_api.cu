@@ -222,9 +222,23 @@ static void alloc_ref(Ctx& c, Ref& R, long n, int rcap, int bigcap) {
   R.Wb2 = c.ar.get<double>((size_t)n * R.ldbig);
 }
 
+// device scratch of the small dense algebra of Algorithms 1-2 for matrices up to
+// rt x rt formed from factors with k columns: the product, its eigendecomposition
+// work and eigenvectors, and the coefficient blocks
+static size_t dense_scratch_elems(int rt, int k) {
+  const size_t r2 = (size_t)rt * rt;
+  return r2 + std::max(2 * (size_t)rt * k + 64, dev_symeig_work_elems(rt) + 4 * r2 + 8 * (size_t)rt + 4096) + 4096;
+}
+
 // tc_maxdim > 0 also reserves the scratch of the tensor-core FP64 products whose
-// operand widths add up to at most tc_maxdim (Algorithms 1-2).
-static void alloc_small(Ctx& c, long n, int maxc, int smallcap, int tc_maxdim = 0) {
+// operand widths add up to at most tc_maxdim (Algorithms 1-2); dense_rt > 0 the
+// device scratch of the small dense algebra (dense_scratch_elems).
+static void alloc_small(Ctx& c, long n, int maxc, int smallcap, int tc_maxdim = 0, int dense_rt = 0,
+                        int dense_k = 0) {
+  if (dense_rt > 0) {
+    c.dsm_cap = dense_scratch_elems(dense_rt, dense_k);
+    c.dsm = c.ar.get<double>(c.dsm_cap);
+  }
   if (tc_maxdim > 0) {
     // reserved whether or not the tensor cores are switched on, so that the
     // workspace query does not depend on the switch
@@ -264,19 +278,6 @@ struct Alg1Out {
   int rp = 0, rm = 0;
   std::vector<double> QB;  // rq x m = Q_Z^T B
 };
-
-// The basis columns after orth_rr and the coefficients that go with them: with a
-// deferred R^{-1} the basis is the first-pass block in Wb2 and the coefficients
-// S (qp x w, row-major) become R^{-1} S.
-static const double* basis_and_coeffs(const Ref& R, const OrthOut& O, int qp, int w, std::vector<double>& S) {
-  if (O.Rinv.empty() || qp == 0 || w == 0) return R.Wb;
-  std::vector<double> St((size_t)w * qp), RS((size_t)qp * w);
-  for (int i = 0; i < qp; ++i)
-    for (int j = 0; j < w; ++j) St[(size_t)j * qp + i] = S[(size_t)i * w + j];
-  host_gemm_nt(qp, w, qp, O.Rinv.data(), qp, St.data(), qp, nullptr, RS.data(), w, false);
-  S.swap(RS);
-  return R.Wb2;
-}
 
 // Residual factor decomposition (Algorithm 1) in FP64 for Z = Q_Z T_Z:
 // F = [Z, A^T Z, Z Z^T B, C^T] is expressed in the orthonormal basis
@@ -331,29 +332,44 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
         tK[(size_t)i * m + j] = s;
       }
   }
-  // H = tZ tA^T + tA tZ^T - tK tK^T + tC tC^T   (= T M T^T)
-  std::vector<double> H((size_t)rt * rt, 0.0), ZA((size_t)rt * rt, 0.0);
-  if (r) host_gemm_nt(rt, rt, r, tZ.data(), r, tA.data(), r, nullptr, ZA.data(), rt, false);
-#pragma omp parallel for if ((long)rt * rt * (m + p) > 1000000) schedule(dynamic, 4)
-  for (int i = 0; i < rt; ++i)
-    for (int k = i; k < rt; ++k) {
-      double s = ZA[(size_t)i * rt + k] + ZA[(size_t)k * rt + i];
-      for (int j = 0; j < m; ++j) s -= tK[(size_t)i * m + j] * tK[(size_t)k * m + j];
-      for (int j = 0; j < p; ++j) s += tC[(size_t)i * p + j] * tC[(size_t)k * p + j];
-      H[(size_t)k * rt + i] = s;
-      H[(size_t)i * rt + k] = s;
+  // H = tZ tA^T + tA tZ^T - tK tK^T + tC tC^T  (= T M T^T) = L R^T with
+  // L = [tZ, tA, tK, tC] and R = [tA, tZ, -tK, tC], formed on the device
+  DevSmall ds{c.dsm, c.dsm_cap, 0};
+  const int kq = 2 * r + m + p;
+  std::vector<double> L((size_t)rt * kq), Rt((size_t)kq * rt);
+  for (int i = 0; i < rt; ++i) {
+    double* li = &L[(size_t)i * kq];
+    for (int j = 0; j < r; ++j) {
+      li[j] = tZ[(size_t)i * r + j];
+      li[r + j] = tA[(size_t)i * r + j];
+      Rt[(size_t)j * rt + i] = tA[(size_t)i * r + j];
+      Rt[(size_t)(r + j) * rt + i] = tZ[(size_t)i * r + j];
     }
-  // eigenvectors only for the eigenvalues kept by the truncation at +-eta_r
-  // (none when only ||R||_F is wanted)
-  std::vector<double> lam(rt), V(Cout ? (size_t)rt * rt : 0);
+    for (int j = 0; j < m; ++j) {
+      li[2 * r + j] = tK[(size_t)i * m + j];
+      Rt[(size_t)(2 * r + j) * rt + i] = -tK[(size_t)i * m + j];
+    }
+    for (int j = 0; j < p; ++j) {
+      li[2 * r + m + j] = tC[(size_t)i * p + j];
+      Rt[(size_t)(2 * r + m + j) * rt + i] = tC[(size_t)i * p + j];
+    }
+  }
+  double* H = dev_small_product(c, ds, rt, kq, L, Rt);
+  // eigenvalues on the device; eigenvectors only for those kept by the truncation at
+  // +-eta_r (none when only ||R||_F is wanted)
+  std::vector<double> lam;
+  const size_t ew = dev_symeig_work_elems(rt);
+  double* ework = ds.get(ew);
+  double* Vd = ds.get((size_t)rt * rt);
   const double th = now_ms();
-  auto kept_r = [eta_rel](double l, double lmx) {
+  auto kept_r = [eta_rel, want = Cout != nullptr](double l, double lmx) {
+    if (!want) return false;
     const double e = eta_rel * lmx;
     return e > 0 ? (l >= e || l <= -e) : l != 0.0;
   };
-  CARE_REQUIRE(host_symeig_select(rt, H.data(), lam.data(), Cout ? V.data() : nullptr, kept_r),
-               CARE_ERR_SMALL_DENSE, "symeig (H)");
+  std::vector<int> sel = dev_symeig_select(rt, H, rt, lam, Vd, kept_r, ework, ew, c.s);
   c.ms_host += now_ms() - th;
+  c.host_syncs += 3;
   double ss = 0.0, lmax = 0.0;
   for (double l : lam) {
     ss += l * l;
@@ -363,30 +379,43 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
   CARE_REQUIRE(std::isfinite(o.res), CARE_NONFINITE, "residual not finite");
   if (!Cout) return o;
   const double eta = eta_rel * lmax;
+  // the kept eigenpairs: positive ones in descending order, then negative ones ascending
+  std::vector<int> pos(rt, -1);
+  for (int q = 0; q < (int)sel.size(); ++q) pos[sel[q]] = q;
   std::vector<int> jp, jm;
   for (int t = rt - 1; t >= 0; --t)
-    if (eta > 0 ? lam[t] >= eta : lam[t] > 0) jp.push_back(t);
+    if (pos[t] >= 0 && (eta > 0 ? lam[t] >= eta : lam[t] > 0)) jp.push_back(t);
   for (int t = 0; t < rt; ++t)
-    if (eta > 0 ? lam[t] <= -eta : lam[t] < 0) jm.push_back(t);
+    if (pos[t] >= 0 && (eta > 0 ? lam[t] <= -eta : lam[t] < 0)) jm.push_back(t);
   o.rp = (int)jp.size();
   o.rm = (int)jm.size();
   const int cw = o.rp + o.rm;
   CARE_REQUIRE(cw <= ccap, CARE_ERR_RANK_CAPACITY, "Algorithm 1: residual factor exceeds capacity");
   if (cw == 0) return o;
-  std::vector<double> S1((size_t)rq * cw, 0.0), S2((size_t)qp * cw, 0.0);
+  // coefficient block S (rt x cw) = V(:, kept) |Lambda|^{1/2}: rows 0..rq-1 go with Q_Z,
+  // rows rq.. with the new directions
+  std::vector<double> scl(cw);
+  std::vector<int> qi(cw);
   for (int col = 0; col < cw; ++col) {
     const int t = col < o.rp ? jp[col] : jm[col - o.rp];
-    const double sc = std::sqrt(std::fabs(lam[t]));
-    for (int i = 0; i < rt; ++i) {
-      const double v = V[(size_t)t * rt + i] * sc;
-      if (i < rq) S1[(size_t)i * cw + col] = v;
-      else S2[(size_t)(i - rq) * cw + col] = v;
-    }
+    qi[col] = pos[t];
+    scl[col] = std::sqrt(std::fabs(lam[t]));
   }
-  gemm_c<double, To>(c, n, rq, cw, 1.0, R.QZ, R.ldq, upload(c, S1), cw, 0.0, Cout, ldco);
+  double* S = ds.get((size_t)rt * cw);
+  eig_coeffs(c, ds, rt, cw, Vd, rt, qi, scl, S);
+  gemm_c<double, To>(c, n, rq, cw, 1.0, R.QZ, R.ldq, S, cw, 0.0, Cout, ldco);
   if (qp) {
-    const double* Vb = basis_and_coeffs(R, O, qp, cw, S2);
-    gemm_c<double, To>(c, n, qp, cw, 1.0, Vb, R.ldbig, upload(c, S2), cw, 1.0, Cout, ldco);
+    const double* S2 = S + (size_t)rq * cw;
+    const double* Vb = R.Wb;
+    if (!O.Rinv.empty()) {
+      // deferred R^{-1} of the Cholesky QR second pass: basis Wb2, coefficients R^{-1} S2
+      double* RS = ds.get((size_t)qp * cw);
+      const double* dRi = to_dev(c, ds, O.Rinv);
+      gemm_c<double, double>(c, qp, qp, cw, 1.0, dRi, qp, S2, cw, 0.0, RS, cw);
+      S2 = RS;
+      Vb = R.Wb2;
+    }
+    gemm_c<double, To>(c, n, qp, cw, 1.0, Vb, R.ldbig, S2, cw, 1.0, Cout, ldco);
   }
   return o;
 }
@@ -424,38 +453,54 @@ static void alg2(Ctx& c, Ref& R, long n, const Ti* Yp, int np, const Ti* Ym, int
   for (int i = 0; i < qp; ++i)
     for (int j = 0; j < ny; ++j) Gam[(size_t)(r + i) * sc + r + j] = O.T[(size_t)i * ny + j];
   for (int j = 0; j < sc; ++j) Nd[j] = j < r ? 1.0 : sign[j - r];
-  std::vector<double> Pm((size_t)rt * rt, 0.0);
-  host_gemm_nt(rt, rt, sc, Gam.data(), sc, Gam.data(), sc, Nd.data(), Pm.data(), rt, true);
+  // P = Gamma N Gamma^T on the device
+  DevSmall ds{c.dsm, c.dsm_cap, 0};
+  std::vector<double> GNt((size_t)sc * rt);
+  for (int i = 0; i < rt; ++i)
+    for (int j = 0; j < sc; ++j) GNt[(size_t)j * rt + i] = Gam[(size_t)i * sc + j] * Nd[j];
+  double* Pd = dev_small_product(c, ds, rt, sc, Gam, GNt);
   // eigenvectors only for the eigenvalues kept by the truncation at eta_s
-  std::vector<double> sig(rt), Th((size_t)rt * rt);
+  std::vector<double> sig;
+  const size_t ew = dev_symeig_work_elems(rt);
+  double* ework = ds.get(ew);
+  double* Vd = ds.get((size_t)rt * rt);
   const double th = now_ms();
   auto kept_s = [eta_mult](double sg, double smx) { return sg >= eta_mult * kU64 * smx && sg > 0.0; };
-  CARE_REQUIRE(host_symeig_select(rt, Pm.data(), sig.data(), Th.data(), kept_s), CARE_ERR_SMALL_DENSE,
-               "symeig (P)");
+  std::vector<int> sel = dev_symeig_select(rt, Pd, rt, sig, Vd, kept_s, ework, ew, c.s);
   c.ms_host += now_ms() - th;
+  c.host_syncs += 3;
   double smax = 0.0;
   for (double v : sig) smax = std::max(smax, std::fabs(v));
   const double eta = eta_mult * kU64 * smax;
+  std::vector<int> pos(rt, -1);
+  for (int q = 0; q < (int)sel.size(); ++q) pos[sel[q]] = q;
   std::vector<int> keep;
   for (int t = rt - 1; t >= 0; --t)
-    if (sig[t] >= eta && sig[t] > 0.0) keep.push_back(t);
+    if (pos[t] >= 0 && sig[t] >= eta && sig[t] > 0.0) keep.push_back(t);
   const int rn = (int)keep.size();
   CARE_REQUIRE(rn <= R.rcap, CARE_ERR_RANK_CAPACITY, "solution rank exceeds r_cap");
-  std::vector<double> S1((size_t)r * rn, 0.0), S2((size_t)qp * rn, 0.0);
-  std::vector<double> snew(rn);
+  std::vector<double> snew(rn), ones(rn, 1.0);
+  std::vector<int> qi(rn);
   for (int col = 0; col < rn; ++col) {
-    const int t = keep[col];
-    snew[col] = std::sqrt(sig[t]);
-    for (int i = 0; i < rt; ++i) {
-      const double v = Th[(size_t)t * rt + i];
-      if (i < r) S1[(size_t)i * rn + col] = v;
-      else S2[(size_t)(i - r) * rn + col] = v;
-    }
+    snew[col] = std::sqrt(sig[keep[col]]);
+    qi[col] = pos[keep[col]];
   }
   if (rn) {
-    if (r) gemm_c<double, double>(c, n, r, rn, 1.0, R.QZ, R.ldq, upload(c, S1), rn, 0.0, R.QZn, R.ldq);
-    const double* Vb = basis_and_coeffs(R, O, qp, rn, S2);
-    gemm_c<double, double>(c, n, qp, rn, 1.0, Vb, R.ldbig, upload(c, S2), rn, r ? 1.0 : 0.0, R.QZn, R.ldq);
+    double* S = ds.get((size_t)rt * rn);
+    eig_coeffs(c, ds, rt, rn, Vd, rt, qi, ones, S);
+    if (r) gemm_c<double, double>(c, n, r, rn, 1.0, R.QZ, R.ldq, S, rn, 0.0, R.QZn, R.ldq);
+    if (qp) {
+      const double* S2 = S + (size_t)r * rn;
+      const double* Vb = R.Wb;
+      if (!O.Rinv.empty()) {
+        double* RS = ds.get((size_t)qp * rn);
+        const double* dRi = to_dev(c, ds, O.Rinv);
+        gemm_c<double, double>(c, qp, qp, rn, 1.0, dRi, qp, S2, rn, 0.0, RS, rn);
+        S2 = RS;
+        Vb = R.Wb2;
+      }
+      gemm_c<double, double>(c, n, qp, rn, 1.0, Vb, R.ldbig, S2, rn, r ? 1.0 : 0.0, R.QZn, R.ldq);
+    }
   }
   std::swap(R.QZ, R.QZn);
   R.r = rn;
@@ -509,7 +554,9 @@ template <class T>
 static void alloc_session(Ctx& c, Session<T>& S, int n, int nnz, int m, int p, const Caps& k, bool ref) {
   // tensor-core scratch: the FP64 products of Algorithms 1-2 (reference sessions) or the
   // low-precision Grams of the shift generation (width <= 2 x 64)
-  alloc_small(c, n, k.maxc, k.small, ref ? std::max(k.rcap + k.bigcap, 2 * k.bigcap) : 256);
+  alloc_small(c, n, k.maxc, k.small, ref ? std::max(k.rcap + k.bigcap, 2 * k.bigcap) : 256,
+              ref ? std::max(2 * k.rcap + p, k.rcap + k.bigcap) : 0,
+              ref ? std::max(2 * k.rcap + m + p, k.rcap + k.bigcap) : 0);
   alloc_prob(c, S.P, n, m, p);
   S.in.alloc(c, n, m, k.bcap, k.adicap, k.hcap);
   S.ldct = pad_ld<T>(std::max(p, 1));
@@ -543,6 +590,12 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
   if (c.counting()) return CARE_OK;
   prepare_op(A, opmem, op_bytes(n, A->nnz), c.s, &c.op);
   load_prob(c, S.P, B, ldb, C, ldc);
+  // Algorithm 1/2's FP64 blocks are free during the correction solves: the joint
+  // compression of the +/- factors works in them
+  S.in.f64a = S.R.Wb;
+  S.in.f64b = S.R.Wb2;
+  S.in.f64ld = S.R.ldbig;
+  S.in.f64cap = S.R.bigcap;
   copy2d<double, T>(n, m, S.P.B64, S.P.ldb, 1, S.in.B, S.in.ldm, 1, 1.0, c.s);
   copy2d<double, T>(n, p, S.P.Ct64, S.P.ldc, 1, S.CtT, S.ldct, 1, 1.0, c.s);
   const bool lo = sizeof(T) == 4;
@@ -588,8 +641,11 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     if (inf.nhist < CARE_HIST_MAX) inf.res_hist[inf.nhist++] = rel;
     inf.iter_outer = it;
     if (verbose_level() >= 1)
-      fprintf(stderr, "[care] refine k=%d rank=%d res=%.3e rp=%d rm=%d  (gram %.0f ms, host eig %.0f ms so far)\n", it,
-              S.R.r, rel, a1.rp, a1.rm, c.ms_gram, c.ms_host);
+      fprintf(stderr,
+              "[care] refine k=%d rank=%d res=%.3e rp=%d rm=%d  t=%.1f s (nlradi %.0f, alg1 %.0f, lradi %.0f, alg2 %.0f ms; "
+              "gram %.0f ms, host eig %.0f ms so far)\n",
+              it, S.R.r, rel, a1.rp, a1.rm, (now_ms() - t0) * 1e-3, inf.ms_phase[0], inf.ms_phase[1], inf.ms_phase[2],
+              inf.ms_phase[3], c.ms_gram, c.ms_host);
     if (rel <= tol) {
       st = CARE_OK;
       break;
@@ -641,9 +697,11 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.krylov_unconverged = c.krylov_unconverged;
   inf.ms_total = now_ms() - t0;
   harvest_timings(c);
-  inf.tc_ms = c.tc_ms;
-  inf.tc_gflop = c.tc_gflop;
-  inf.tc_calls = c.tc_calls;
+  for (int q = 0; q < 2; ++q) {
+    inf.tc_ms[q] = c.tc_ms[q];
+    inf.tc_gflop[q] = c.tc_gflop[q];
+    inf.tc_calls[q] = c.tc_calls[q];
+  }
   inf.krylov_ms = c.kry_ms;
   inf.krylov_gbyte = c.kry_gbyte;
   inf.host_syncs = c.host_syncs;
@@ -697,9 +755,11 @@ static care_status lradi_impl(Ctx& c, const care_csr* A, const double* B, int ld
   inf.status = a.converged ? CARE_OK : CARE_NOT_CONVERGED;
   inf.ms_total = now_ms() - t0;
   harvest_timings(c);
-  inf.tc_ms = c.tc_ms;
-  inf.tc_gflop = c.tc_gflop;
-  inf.tc_calls = c.tc_calls;
+  for (int q = 0; q < 2; ++q) {
+    inf.tc_ms[q] = c.tc_ms[q];
+    inf.tc_gflop[q] = c.tc_gflop[q];
+    inf.tc_calls[q] = c.tc_calls[q];
+  }
   inf.krylov_ms = c.kry_ms;
   inf.krylov_gbyte = c.kry_gbyte;
   inf.host_syncs = c.host_syncs;
@@ -726,7 +786,7 @@ static care_status resfac_impl(Ctx& c, const care_csr* A, const double* B, int l
   void* opmem = c.ar.get<char>(op_bytes(n, A->nnz));
   Prob P;
   Ref R;
-  alloc_small(c, n, k.maxc, k.small, 3 * k.rcap + p + m);
+  alloc_small(c, n, k.maxc, k.small, 3 * k.rcap + p + m, 2 * k.rcap + p, 2 * k.rcap + m + p);
   alloc_prob(c, P, n, m, p);
   alloc_ref(c, R, n, k.rcap, std::max(k.rcap + p, k.rcap));
   const int ccap = std::max(c_cap, 0);
@@ -839,6 +899,8 @@ void care_opts_default(care_opts* o) {
   o->tri_sweeps = 2;
   o->verbose = 0;
   o->inner_compress = 0;
+  o->gmres_restart_lo = 30;
+  o->gmres_restart_hi = 50;
 }
 
 const char* care_status_string(int s) {
@@ -1222,6 +1284,50 @@ care_status care_residual_factor(const care_csr* A, const double* B, int ldb, in
 
 unsigned long long care_kernel_launches(void) { return care::launches(); }
 
+size_t care_ilu0_work_size(const care_op* op, int dtype) {
+  if (!op) return 0;
+  Arena a;
+  if (dtype == 0) krylov_alloc<double>(a, op->n, true, op->nnz);
+  else krylov_alloc<float>(a, op->n, true, op->nnz);
+  return a.off + 256;
+}
+
+care_status care_ilu0(const care_op* op, int dtype, int exact, double p_re, double p_im, void* F, void* work,
+                      size_t work_bytes, care_stream_t s) {
+  if (!op || !F || !work || (dtype != 0 && dtype != 1)) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    Arena a;
+    a.base = static_cast<char*>(work);
+    a.cap = work_bytes;
+    const bool cplx = p_im != 0.0;
+    if (dtype == 0) {
+      KrylovWork<double> w = krylov_alloc<double>(a, op->n, true, op->nnz);
+      ilu0_factor<double>(op64(*op), cd{p_re, p_im}, cplx, exact != 0, w, (double*)F, (cudaStream_t)s);
+    } else {
+      KrylovWork<float> w = krylov_alloc<float>(a, op->n, true, op->nnz);
+      ilu0_factor<float>(op32(*op), cd{p_re, p_im}, cplx, exact != 0, w, (float*)F, (cudaStream_t)s);
+    }
+    return CARE_OK;
+  });
+}
+
+size_t care_symeig_work_size(int n) { return n > 0 ? dev_symeig_work_elems(n) * sizeof(double) + 256 : 256; }
+
+care_status care_symeig(int n, const double* A, int lda, double* w, double* V, double lo, double hi, int* nsel,
+                        void* work, size_t work_bytes, care_stream_t s) {
+  if (n < 0 || (n > 0 && (!A || !w || !work || lda < n)) || !nsel) return CARE_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    std::vector<double> wh;
+    std::vector<int> sel = dev_symeig_select(
+        n, A, lda, wh, V, [lo, hi, V](double l, double) { return V != nullptr && (l <= lo || l >= hi); },
+        static_cast<double*>(work), work_bytes / sizeof(double), (cudaStream_t)s);
+    std::copy(wh.begin(), wh.end(), w);
+    *nsel = (int)sel.size();
+    CARE_CUDA(cudaStreamSynchronize((cudaStream_t)s));
+    return CARE_OK;
+  });
+}
+
 care_status care_fp64_peak(double* tflops, care_stream_t s) {
   if (!tflops) return CARE_ERR_INVALID_ARG;
   return run_guarded([&] {
@@ -1248,7 +1354,7 @@ size_t care_tc_work_size(int maxdim) {
 
 care_status care_gram_tc(int mode, int n, int a, int b, const void* X, int ldx, const void* Y, int ldy, double* G,
                          int ldg, void* work, size_t work_bytes, care_stream_t s) {
-  if (mode < 0 || mode > 2 || n < 0 || a < 0 || b < 0 || ldx < a || ldy < b || ldg < b) return CARE_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 3 || n < 0 || a < 0 || b < 0 || ldx < a || ldy < b || ldg < b) return CARE_ERR_INVALID_ARG;
   if (a > 0 && b > 0 && (!G || !work || (n > 0 && (!X || !Y)))) return CARE_ERR_INVALID_ARG;
   if (a == 0 || b == 0) return CARE_OK;
   return run_guarded([&] {
@@ -1262,6 +1368,8 @@ care_status care_gram_tc(int mode, int n, int a, int b, const void* X, int ldx, 
     CARE_CUDA(cudaMemsetAsync(sc.err, 0, sizeof(int), cs));
     if (mode == 0)
       tc_gram_f64(n, a, b, (const double*)X, ldx, (const double*)Y, ldy, G, ldg, sc, md, cs);
+    else if (mode == 3)
+      tc_gram_f32acc(n, a, b, (const float*)X, ldx, (const float*)Y, ldy, G, ldg, sc, md, cs);
     else
       tc_gram_lowp(mode, n, a, b, (const float*)X, ldx, (const float*)Y, ldy, G, ldg, sc, md, cs);
     return tc_check(sc, cs) ? CARE_TIMEOUT : CARE_OK;
@@ -1272,7 +1380,7 @@ care_status care_gemm_ts(int dtype, int tc, int n, int a, int b, double alpha, c
                          int lds, double beta, void* Y, int ldy, void* work, size_t work_bytes, care_stream_t s) {
   if ((dtype != 0 && dtype != 1) || n < 0 || a < 0 || b < 0 || ldx < a || lds < b || ldy < b) return CARE_ERR_INVALID_ARG;
   if (n > 0 && b > 0 && (!Y || (a > 0 && (!X || !S)))) return CARE_ERR_INVALID_ARG;
-  if (tc && (dtype != 0 || !work)) return CARE_ERR_INVALID_ARG;
+  if (tc && !work) return CARE_ERR_INVALID_ARG;
   return run_guarded([&] {
     cudaStream_t cs = (cudaStream_t)s;
     if (tc && a > 0) {
@@ -1282,7 +1390,10 @@ care_status care_gemm_ts(int dtype, int tc, int n, int a, int b, double alpha, c
       ar.cap = work_bytes;
       TcScratch sc = tc_alloc(ar, a + b);
       CARE_CUDA(cudaMemsetAsync(sc.err, 0, sizeof(int), cs));
-      tc_gemm_ts_f64<double>(n, a, b, alpha, (const double*)X, ldx, S, lds, beta, (double*)Y, ldy, sc, a + b, cs);
+      if (dtype == 0)
+        tc_gemm_ts_f64<double>(n, a, b, alpha, (const double*)X, ldx, S, lds, beta, (double*)Y, ldy, sc, a + b, cs);
+      else
+        tc_gemm_ts_f32acc<float>(n, a, b, alpha, (const float*)X, ldx, S, lds, beta, (float*)Y, ldy, sc, a + b, cs);
       return tc_check(sc, cs) ? CARE_TIMEOUT : CARE_OK;
     }
     if (dtype == 0)

@@ -49,6 +49,16 @@ void cpair_update(long n, int b, int rp, const T* sol, int ldr, double g, double
 template <class T>
 void scale_cols(long n, int cols, T* Y, int ldy, const double* d, cudaStream_t s);
 
+// Symmetric eigendecomposition on the device (k_syev.cu): all eigenvalues of the
+// n x n matrix S (device, row-major, lds; returned ascending in w on the host) and
+// the eigenvectors of those for which want(w_i, max|w|) holds, written as rows of
+// V (device, length n each, in ascending eigenvalue order); returns their indices.
+// work: dev_symeig_work_elems(n) doubles of device scratch.
+size_t dev_symeig_work_elems(int n);
+std::vector<int> dev_symeig_select(int n, const double* S, int lds, std::vector<double>& w, double* V,
+                                   const std::function<bool(double, double)>& want, double* work,
+                                   size_t work_elems, cudaStream_t s);
+
 // measured FP64 FMA throughput of the CUDA cores (TFLOP/s)
 double fp64_fma_peak_tflops(cudaStream_t s);
 

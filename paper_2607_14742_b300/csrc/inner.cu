@@ -77,9 +77,11 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
                  c.dG, b, c.tc, c.tc_maxdim, c.s);
     c.tc_used = true;
     c.lowp_calls++;
-  } else if (sizeof(T) == 8 && tc_use(c, n, a, b, sym0 ? a : a + b)) {
-    tc_gram_f64(n, a, b, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<const double*>(Y), ldy, c.dG,
-                b, c.tc, c.tc_maxdim, c.s);
+  } else if (tc_use(c, n, a, b, sym0 ? a : a + b)) {
+    if constexpr (sizeof(T) == 8)
+      tc_gram_f64(n, a, b, X, ldx, Y, ldy, c.dG, b, c.tc, c.tc_maxdim, c.s);
+    else
+      tc_gram_f32acc(n, a, b, X, ldx, Y, ldy, c.dG, b, c.tc, c.tc_maxdim, c.s);
     c.tc_used = on_tc = true;
   } else {
     gram<T>(n, a, b, X, ldx, Y, ldy, c.dG, b, c.gw, c.gw_cap, c.s);
@@ -94,9 +96,9 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
   const int k = sizeof(T) == 8 ? 0 : 1;
   const double gf = (sym0 ? (double)n * a * (a + 1) : 2.0 * n * a * b) * 1e-9;
   if (on_tc) {
-    c.tc_ms += ms;
-    c.tc_gflop += gf;
-    c.tc_calls += 1;
+    c.tc_ms[k] += ms;
+    c.tc_gflop[k] += gf;
+    c.tc_calls[k] += 1;
   } else {
     c.gram_ms[k] += ms;
     c.gram_gflop[k] += gf;
@@ -107,6 +109,43 @@ std::vector<double> gram_h(Ctx& c, long n, int a, int b, const T* X, int ldx, co
 }
 template std::vector<double> gram_h<float>(Ctx&, long, int, int, const float*, int, const float*, int, bool);
 template std::vector<double> gram_h<double>(Ctx&, long, int, int, const double*, int, const double*, int, bool);
+
+// --------------------------------------------------- small dense on device --
+double* to_dev(Ctx& c, DevSmall& ds, const std::vector<double>& h) {
+  double* d = ds.get(std::max<size_t>(h.size(), 1));
+  if (!h.empty()) CARE_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c.s));
+  return d;
+}
+
+double* dev_small_product(Ctx& c, DevSmall& ds, int rt, int k, const std::vector<double>& L,
+                          const std::vector<double>& Rt) {
+  double* M = ds.get((size_t)rt * rt);
+  const size_t mark = ds.off;
+  const double* dL = to_dev(c, ds, L);
+  const double* dRt = to_dev(c, ds, Rt);
+  gemm_c<double, double>(c, rt, k, rt, 1.0, dL, k, dRt, rt, 0.0, M, rt);
+  ds.off = mark;  // the factors are dead once the (stream-ordered) product has run
+  return M;
+}
+
+__global__ void k_eig_coeffs(int rows, int cols, const double* __restrict__ V, int ldv, const int* __restrict__ q,
+                             const double* __restrict__ sc, double* __restrict__ S) {
+  const long total = (long)rows * cols;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / cols), col = (int)(t % cols);
+    S[t] = V[(long)q[col] * ldv + i] * sc[col];
+  }
+}
+
+void eig_coeffs(Ctx& c, DevSmall& ds, int rows, int cols, const double* V, int ldv, const std::vector<int>& q,
+                const std::vector<double>& sc, double* S) {
+  if (rows == 0 || cols == 0) return;
+  int* dq = reinterpret_cast<int*>(ds.get((size_t)cols));
+  CARE_CUDA(cudaMemcpyAsync(dq, q.data(), sizeof(int) * cols, cudaMemcpyHostToDevice, c.s));
+  const double* dsc = to_dev(c, ds, sc);
+  k_eig_coeffs<<<device_sms() * 4, 256, 0, c.s>>>(rows, cols, V, ldv, dq, dsc, S);
+  CARE_LAUNCH();
+}
 
 // ------------------------------------------------------------ orth_rr -----
 template <class T>
@@ -227,7 +266,11 @@ template <class T>
 void Inner<T>::alloc(Ctx& c, int n_, int m_, int bcap_, int adicap_, int hcap_) {
   n = n_; m = m_; bcap = bcap_; adicap = adicap_; hcap = hcap_;
   jacobi = c.o.precond != CARE_PRECOND_NONE;
-  kw = krylov_alloc<T>(c.ar, n, jacobi, c.o.precond == CARE_PRECOND_ILU0 ? (long)c.op_nnz : -1L);
+  const int restart = c.o.krylov == CARE_KRYLOV_GMRES
+                          ? std::max(2, sizeof(T) == 4 ? c.o.gmres_restart_lo : c.o.gmres_restart_hi)
+                          : 0;
+  const bool ilu = c.o.precond == CARE_PRECOND_ILU0 || c.o.precond == CARE_PRECOND_ILU0_EXACT;
+  kw = krylov_alloc<T>(c.ar, n, jacobi, ilu ? (long)c.op_nnz : -1L, restart);
   kw.ilu_sweeps = c.o.ilu_sweeps;
   kw.tri_sweeps = c.o.tri_sweeps;
   ldm = pad_ld<T>(std::max(m, 1));
@@ -374,8 +417,12 @@ static void smw_solve(Ctx& c, Inner<T>& in, Shift p, int b, bool hasK) {
       CARE_CUDA(cudaEventCreate(&c.ke1));
     }
     CARE_CUDA(cudaEventRecord(c.ke0, c.s));
-    KrylovResult kr = krylov_bicgstab<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr,
-                                         w, krylov_tol<T>(c), krylov_maxit<T>(c), c.o.precond, in.kw, c.s);
+    KrylovResult kr =
+        c.o.krylov == CARE_KRYLOV_GMRES
+            ? krylov_gmres<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr, w,
+                              krylov_tol<T>(c), krylov_maxit<T>(c), c.o.precond, in.kw, c.s)
+            : krylov_bicgstab<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr, w,
+                                 krylov_tol<T>(c), krylov_maxit<T>(c), c.o.precond, in.kw, c.s);
     CARE_CUDA(cudaEventRecord(c.ke1, c.s));
     CARE_CUDA(cudaEventSynchronize(c.ke1));  // the solve has synchronised already
     float kms = 0.f;
@@ -465,6 +512,69 @@ static int compress_part(Ctx& c, Inner<T>& in, int col0, int ncols, bool right_a
   return q;
 }
 
+// Joint compression of the two factor groups when their capacity is reached:
+// X_+ - X_- = [Z_+, Z_-] N [Z_+, Z_-]^T, N = diag(I, -I), is what the refinement
+// uses, and X_+, X_- are each much larger than their difference near convergence.
+// The groups are widened to FP64, orthonormalised together ([Z_+, Z_-] = Q T),
+// P = T N T^T is diagonalised on the device, eigenvalues below the inner
+// precision's relative level (1e-8 of max|lambda| for FP32, 1e-15 for FP64) are
+// dropped, and the positive / negative parts Q V_+- |Lambda_+-|^{1/2} replace the
+// groups.  The truncation is then relative to the correction itself, not to X_+-.
+// Returns false (nothing changed) when the FP64 blocks are too narrow.
+template <class T>
+static bool compress_joint(Ctx& c, Inner<T>& in, int& np, int& nm) {
+  const int ny = np + nm;
+  if (!in.f64a || ny > in.f64cap || ny == 0 || !c.dsm) return false;
+  const long n = in.n;
+  const int cap = in.adicap;
+  if (np) copy2d<T, double>(n, np, in.Z, in.ldz, 1, in.f64a, in.f64ld, 1, 1.0, c.s);
+  if (nm) copy2d<T, double>(n, nm, in.Z + (cap - nm), in.ldz, 1, in.f64a + np, in.f64ld, 1, 1.0, c.s);
+  OrthOut O = orth_rr<double>(c, n, ny, in.f64a, in.f64ld, in.f64b, in.f64ld, 1e-14, nullptr, true, 0, nullptr, 0);
+  const int q = O.rank;
+  if (q == 0) {
+    np = nm = 0;
+    return true;
+  }
+  std::vector<double> TNt((size_t)ny * q);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < ny; ++j) TNt[(size_t)j * q + i] = O.T[(size_t)i * ny + j] * (j < np ? 1.0 : -1.0);
+  DevSmall ds{c.dsm, c.dsm_cap, 0};
+  double* Pd = dev_small_product(c, ds, q, ny, O.T, TNt);
+  const size_t ew = dev_symeig_work_elems(q);
+  double* ework = ds.get(ew);
+  double* Vd = ds.get((size_t)q * q);
+  const double rel = sizeof(T) == 4 ? 1e-8 : 1e-15;
+  std::vector<double> lam;
+  std::vector<int> sel = dev_symeig_select(
+      q, Pd, q, lam, Vd, [rel](double l, double lmx) { return std::fabs(l) >= rel * lmx && l != 0.0; }, ework, ew,
+      c.s);
+  c.host_syncs += 3;
+  std::vector<int> pos(q, -1);
+  for (int t = 0; t < (int)sel.size(); ++t) pos[sel[t]] = t;
+  std::vector<int> qi;
+  std::vector<double> sc;
+  int rp2 = 0;
+  for (int t = q - 1; t >= 0; --t)
+    if (pos[t] >= 0 && lam[t] > 0) {
+      qi.push_back(pos[t]);
+      sc.push_back(std::sqrt(lam[t]));
+      ++rp2;
+    }
+  for (int t = 0; t < q; ++t)
+    if (pos[t] >= 0 && lam[t] < 0) {
+      qi.push_back(pos[t]);
+      sc.push_back(std::sqrt(-lam[t]));
+    }
+  const int cw = (int)qi.size(), rm2 = cw - rp2;
+  double* S = ds.get((size_t)q * std::max(cw, 1));
+  eig_coeffs(c, ds, q, cw, Vd, q, qi, sc, S);
+  if (rp2) gemm_c<double, T>(c, n, q, rp2, 1.0, in.f64a, in.f64ld, S, cw, 0.0, in.Z, in.ldz);
+  if (rm2) gemm_c<double, T>(c, n, q, rm2, 1.0, in.f64a, in.f64ld, S + rp2, cw, 0.0, in.Z + (cap - rm2), in.ldz);
+  np = rp2;
+  nm = rm2;
+  return true;
+}
+
 template <class T>
 AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew,
                 bool compress_end) {
@@ -496,9 +606,13 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
     const bool cplx = p.im != 0.0;
     const int mult = cplx ? 2 : 1;
     if (np + nm + mult * b > cap) {
-      // column compression of both sign groups (X_+ and X_- are kept separately)
-      const int np2 = compress_part<T>(c, in, 0, np, false);
-      const int nm2 = compress_part<T>(c, in, cap - nm, nm, true);
+      // column compression: jointly in FP64 where the session has the blocks (the
+      // correction solves of care_solve), else each sign group on its own
+      int np2 = np, nm2 = nm;
+      if (!compress_joint<T>(c, in, np2, nm2)) {
+        np2 = compress_part<T>(c, in, 0, np, false);
+        nm2 = compress_part<T>(c, in, cap - nm, nm, true);
+      }
       if (verbose_level() >= 2)
         fprintf(stderr, "[care]   adi compress %d+%d -> %d+%d\n", np, nm, np2, nm2);
       np = np2;

@@ -15,6 +15,7 @@
 // updates the per-column recurrence scalars.  Results are bitwise reproducible.
 #include <cmath>
 
+#include "dense.cuh"
 #include "krylov.cuh"
 
 namespace care {
@@ -277,42 +278,30 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
       }
       if (v < a.nvec && diff) vload(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
     }
-    // four independent gathers in flight per thread (stencil rows have 5-7 entries)
-    int j = s;
-    for (; j + 3 < e; j += 4) {
-      int c[4];
-      T av[4];
+    // the row's entries in predicated batches of 8 (stencil rows have 5-7): all
+    // index/value loads of a batch, then all its gathers, are in flight together,
+    // so a row costs three dependent memory round trips (row pointers, indices,
+    // gathered rows of X); padding entries gather row `row` with weight 0
+    for (int j0 = s; j0 < e; j0 += 8) {
+      int c[8];
+      T av[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        c[u] = __ldg(a.ci + j + u);
-        av[u] = __ldg(a.av + j + u);
+      for (int u = 0; u < 8; ++u) {
+        const bool in = j0 + u < e;
+        c[u] = in ? __ldg(a.ci + j0 + u) : (int)row;
+        av[u] = in ? __ldg(a.av + j0 + u) : T(0);
       }
 #pragma unroll
       for (int k = 0; k < NVPT; ++k) {
         const int v = it.lane_v + k * TPR;
         if (v < a.nvec) {
-          T x[4][VEC];
+          T x[8][VEC];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) vload(a.X + (size_t)c[u] * a.ldx + v * VEC, x[u]);
+          for (int u = 0; u < 8; ++u) vload(a.X + (size_t)c[u] * a.ldx + v * VEC, x[u]);
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < 8; ++u)
 #pragma unroll
             for (int q = 0; q < VEC; ++q) y[k][q] = fma(av[u], x[u][q] - xi[k][q], y[k][q]);
-        }
-      }
-    }
-    for (; j < e; ++j) {
-      const int c = __ldg(a.ci + j);
-      const T av = __ldg(a.av + j);
-      const T* xr = a.X + (size_t)c * a.ldx;
-#pragma unroll
-      for (int k = 0; k < NVPT; ++k) {
-        const int v = it.lane_v + k * TPR;
-        if (v < a.nvec) {
-          T x[VEC];
-          vload(xr + v * VEC, x);
-#pragma unroll
-          for (int q = 0; q < VEC; ++q) y[k][q] = fma(av, x[q] - xi[k][q], y[k][q]);
         }
       }
     }
@@ -428,6 +417,9 @@ struct KArgs {
   const T* F;
   T *Y1, *Y2, *Y3;
   int tri_sweeps;
+  // exact ILU(0) application (precond CARE_PRECOND_ILU0_EXACT)
+  int exact;
+  int *iflags, *iticket, *ierr;
 };
 
 // scalar of column slot q of vector v (complex: pairs share one state entry)
@@ -931,8 +923,191 @@ __global__ void __launch_bounds__(kBlock) k_trisweep(TriArgs<T> a) {
   }
 }
 
+// GMRES per-column state (doubles): H ((m+1) x m complex, column-major), Givens
+// cosines cs (m) and sines sn (m, complex), the rotated right-hand side g (m+1,
+// complex), then beta0 = ||r_0||, the converged flag, the inner step count, ||b||.
+__host__ __device__ inline size_t gm_state_stride(int m) { return (size_t)2 * (m + 1) * m + m + 2 * m + 2 * (m + 1) + 4; }
+inline int gm_dot_ctas() { return device_sms() * 2; }
+
+// ------------------------------------------------------- exact ILU(0) -----
+// ILU(0) of M_p = A^T + p I on the pattern of A^T computed exactly (the IKJ
+// elimination restricted to the pattern, Saad, Iterative Methods, Alg. 10.4), and
+// exact triangular solves with it, without level sets: one warp per row, rows
+// claimed in elimination order from an atomic ticket, each row waiting (bounded)
+// for the rows it depends on to publish their results (a ready flag per row,
+// release/acquire; the data are read past L1).  A warp only ever waits for rows
+// claimed before its own, by warps already running, so progress is guaranteed.
+// A wait that exceeds its bound sets the error word and the kernel finishes
+// without further waits; the host reports CARE_TIMEOUT.
+constexpr long long ILU_WAIT_NS = 2000000000LL;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long ilu_clock() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// lane 0 waits until flags[k] != 0; warp-uniform result (false: gave up)
+__device__ __forceinline__ bool ilu_wait(const int* flags, int k, int* err) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    if (ld_acquire(flags + k) == 0) {
+      const long long t0 = ilu_clock();
+      while (ld_acquire(flags + k) == 0) {
+        if (*(volatile int*)err != 0 || ilu_clock() - t0 > ILU_WAIT_NS) {
+          atomicCAS(err, 0, 5);
+          ok = 0;
+          break;
+        }
+      }
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <class T, bool CPLX>
+__device__ __forceinline__ cd fld_cg(const T* F, int e) {
+  if constexpr (CPLX) return cd{(double)__ldcg(F + 2 * e), (double)__ldcg(F + 2 * e + 1)};
+  else return cd{(double)__ldcg(F + e), 0.0};
+}
+
+// F (values on the pattern; complex interleaved) = M_p, then eliminated in place:
+// strictly lower part L (unit diagonal implied), the rest U.  flags, ticket zeroed.
+template <class T, bool CPLX>
+__global__ void k_ilu_exact(int n, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ dpos,
+                            T* F, int* flags, int* ticket, int* err) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int row = 0;
+    if (lane == 0) row = atomicAdd(ticket, 1);
+    row = __shfl_sync(0xffffffffu, row, 0);
+    if (row >= n) break;
+    const int b = rp[row], e_end = rp[row + 1], dp = dpos[row];
+    bool alive = *(volatile int*)err == 0;
+    for (int e = b; e < dp && alive; ++e) {
+      const int k = ci[e];
+      if (!ilu_wait(flags, k, err)) {
+        alive = false;
+        break;
+      }
+      // l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for the pattern entries j > k of row i
+      const cd lik = cdivz(fld_cg<T, CPLX>(F, e), fld_cg<T, CPLX>(F, dpos[k]));
+      if (lane == 0) fstore<T, CPLX>(F, e, lik);
+      const int kb = dpos[k] + 1, ke = rp[k + 1];
+      for (int e2 = e + 1 + lane; e2 < e_end; e2 += 32) {
+        const int j = ci[e2];
+        int lo = kb, hi = ke - 1, pos = -1;
+        while (lo <= hi) {
+          const int mid = (lo + hi) >> 1;
+          const int c = ci[mid];
+          if (c == j) { pos = mid; break; }
+          if (c < j) lo = mid + 1; else hi = mid - 1;
+        }
+        if (pos >= 0) {
+          const cd t = cmul(lik, fld_cg<T, CPLX>(F, pos));
+          cd a = fld_cg<T, CPLX>(F, e2);
+          a.re -= t.re;
+          a.im -= t.im;
+          fstore<T, CPLX>(F, e2, a);
+        }
+      }
+      __syncwarp();
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(flags + row, 1);
+  }
+}
+
+// Exact triangular solve on an n x (nvec vectors) block, one warp per row:
+// LOWER: y_i = r_i - sum_{k<i} l_ik y_k (rows in increasing order);
+// UPPER: x_i = (r_i - sum_{k>i} u_ik x_k) / u_ii (rows in decreasing order).
+template <class T, bool CPLX, bool LOWER>
+__global__ void k_tri_exact(long n, const int* __restrict__ rp, const int* __restrict__ ci,
+                            const int* __restrict__ dpos, const T* __restrict__ F, const T* __restrict__ r, T* out,
+                            int ld, int nvec, int* flags, int* ticket, int* err) {
+  constexpr int VEC = 16 / sizeof(T);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n) break;
+    const long row = LOWER ? t : n - 1 - t;
+    const int dp = dpos[row];
+    const int e0 = LOWER ? rp[row] : dp + 1, e1 = LOWER ? dp : rp[row + 1];
+    T acc[2][VEC];
+#pragma unroll
+    for (int k2 = 0; k2 < 2; ++k2) {
+      const int v = lane + 32 * k2;
+      if (v < nvec) vload(r + (size_t)row * ld + v * VEC, acc[k2]);
+    }
+    bool alive = *(volatile int*)err == 0;
+    for (int e = e0; e < e1 && alive; ++e) {
+      const int k = ci[e];
+      if (!ilu_wait(flags, k, err)) {
+        alive = false;
+        break;
+      }
+      const cd f = fld_cg<T, CPLX>(F, e);
+#pragma unroll
+      for (int k2 = 0; k2 < 2; ++k2) {
+        const int v = lane + 32 * k2;
+        if (v >= nvec) continue;
+        const T* xr = out + (size_t)k * ld + v * VEC;
+        T x[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) x[q] = __ldcg(xr + q);
+        if constexpr (CPLX) {
+#pragma unroll
+          for (int q = 0; q < VEC; q += 2) {
+            acc[k2][q] -= (T)f.re * x[q] - (T)f.im * x[q + 1];
+            acc[k2][q + 1] -= (T)f.re * x[q + 1] + (T)f.im * x[q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[k2][q] -= (T)f.re * x[q];
+        }
+      }
+    }
+    if (!LOWER) {
+      const cd dinv = cdivz(cd{1.0, 0.0}, fld_cg<T, CPLX>(F, dp));
+#pragma unroll
+      for (int k2 = 0; k2 < 2; ++k2) {
+        if constexpr (CPLX) {
+#pragma unroll
+          for (int q = 0; q < VEC; q += 2) {
+            const T yr = (T)dinv.re * acc[k2][q] - (T)dinv.im * acc[k2][q + 1];
+            const T yi = (T)dinv.re * acc[k2][q + 1] + (T)dinv.im * acc[k2][q];
+            acc[k2][q] = yr;
+            acc[k2][q + 1] = yi;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[k2][q] *= (T)dinv.re;
+        }
+      }
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 2; ++k2) {
+      const int v = lane + 32 * k2;
+      if (v < nvec) vstore(out + (size_t)row * ld + v * VEC, acc[k2]);
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(flags + row, 1);
+  }
+}
+
 template <class T>
-KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi, long nnz_ilu) {
+KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi, long nnz_ilu, int gmres_restart) {
   KrylovWork<T> w;
   const size_t blk = (size_t)n * kMaxRealCols;
   w.n = n;
@@ -947,20 +1122,47 @@ KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi, long nnz_ilu) {
     w.F1 = ar.get<T>((size_t)2 * nnz_ilu);
     w.dpos = ar.get<int>((size_t)n);
     w.Y1 = ar.get<T>(blk); w.Y2 = ar.get<T>(blk); w.Y3 = ar.get<T>(blk);
+    w.iflags = ar.get<int>((size_t)n + 64);
+    w.iticket = ar.get<int>(64);
+    w.ierr = ar.get<int>(64);
   }
   w.st = ar.get<KState>(kMaxRealCols);
   w.hdr = ar.get<KHeader>(1);
   w.partial = ar.get<double>((size_t)device_sms() * 8 * 2 * kMaxRealCols);
   w.out = ar.get<double>(2 * kMaxRealCols);
+  if (gmres_restart > 0) {
+    const int m = gmres_restart;
+    w.gm_restart = m;
+    w.GV = ar.get<T>(blk * (size_t)(m + 1));
+    w.GZ = ar.get<T>(blk);
+    w.GS = ar.get<double>((size_t)kMaxRealCols * gm_state_stride(m));
+    w.GH = ar.get<double>((size_t)2 * (m + 1) * kMaxRealCols);
+    w.GP = ar.get<double>((size_t)gm_dot_ctas() * 2 * (m + 1) * kMaxRealCols);
+  }
   return w;
 }
-template KrylovWork<float> krylov_alloc<float>(Arena&, int, bool, long);
-template KrylovWork<double> krylov_alloc<double>(Arena&, int, bool, long);
+template KrylovWork<float> krylov_alloc<float>(Arena&, int, bool, long, int);
+template KrylovWork<double> krylov_alloc<double>(Arena&, int, bool, long, int);
 
 // out = P^{-1} r with P = L U the ILU(0) factor: tri_sweeps Jacobi sweeps on L
 // then on U (see the ILU(0) notes above).
 template <class T, int TPR, int NVPT, bool CPLX>
 static void ilu_apply(const KArgs<T>& a, const T* r, T* out, int grid, cudaStream_t s) {
+  if (a.exact) {
+    // exact forward (unit L) then backward (U) substitution, sync-free by rows
+    const int g = device_sms() * 4;
+    CARE_CUDA(cudaMemsetAsync(a.iflags, 0, sizeof(int) * (size_t)a.n, s));
+    CARE_CUDA(cudaMemsetAsync(a.iticket, 0, sizeof(int), s));
+    k_tri_exact<T, CPLX, true><<<g, kBlock, 0, s>>>(a.n, a.rp, a.ci, a.dpos, a.F, r, a.Y1, a.ld, a.nvec, a.iflags,
+                                                    a.iticket, a.ierr);
+    CARE_LAUNCH();
+    CARE_CUDA(cudaMemsetAsync(a.iflags, 0, sizeof(int) * (size_t)a.n, s));
+    CARE_CUDA(cudaMemsetAsync(a.iticket, 0, sizeof(int), s));
+    k_tri_exact<T, CPLX, false><<<g, kBlock, 0, s>>>(a.n, a.rp, a.ci, a.dpos, a.F, a.Y1, out, a.ld, a.nvec, a.iflags,
+                                                     a.iticket, a.ierr);
+    CARE_LAUNCH();
+    return;
+  }
   TriArgs<T> t{};
   t.n = a.n; t.rp = a.rp; t.ci = a.ci; t.dpos = a.dpos; t.F = a.F; t.dinv = a.Dinv; t.ld = a.ld; t.nvec = a.nvec;
   const int sT = a.tri_sweeps;
@@ -1068,7 +1270,7 @@ static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, 
   if (h.n_active == 0) return res;
   // Capture `poll` iterations once and replay the graph; the executable graph is
   // kept per thread and updated in place when only kernel parameters change.
-  const long per_iter = 5 + (PREC == 2 ? 4L * a.tri_sweeps : 0);
+  const long per_iter = 5 + (PREC == 2 ? (a.exact ? 4L : 4L * a.tri_sweeps) : 0);
   thread_local GraphExecCache exec_cache;
   int dev = 0;
   CARE_CUDA(cudaGetDevice(&dev));
@@ -1128,6 +1330,32 @@ static KrylovResult run_bicg(const OpT<T>& op, cd sigma, KArgs<T> a, int maxit, 
   return res;
 }
 
+// F = M_p = A^T + sigma I on the pattern (complex interleaved when CPLX)
+template <class T, bool CPLX>
+__global__ void k_ilu_copy(int n, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ av,
+                           double pre, double pim, T* __restrict__ F) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) fstore<T, CPLX>(F, e, mval<T, CPLX>(av, e, (int)i, ci[e], pre, pim));
+}
+
+// exact ILU(0) of M_p into w.F0 (w.ierr is cleared first and read by the caller)
+template <class T>
+static const T* ilu_exact_setup(const OpT<T>& op, cd sigma, bool cplx, KrylovWork<T>& w, cudaStream_t s) {
+  const int g = device_sms() * 4;
+  k_diagpos<<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, w.dpos);
+  CARE_LAUNCH();
+  if (cplx) k_ilu_copy<T, true><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, op.val, sigma.re, sigma.im, w.F0);
+  else k_ilu_copy<T, false><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, op.val, sigma.re, sigma.im, w.F0);
+  CARE_LAUNCH();
+  CARE_CUDA(cudaMemsetAsync(w.iflags, 0, sizeof(int) * (size_t)op.n, s));
+  CARE_CUDA(cudaMemsetAsync(w.iticket, 0, sizeof(int), s));
+  CARE_CUDA(cudaMemsetAsync(w.ierr, 0, sizeof(int), s));
+  if (cplx) k_ilu_exact<T, true><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, w.dpos, w.F0, w.iflags, w.iticket, w.ierr);
+  else k_ilu_exact<T, false><<<g, kBlock, 0, s>>>(op.n, op.rp, op.ci, w.dpos, w.F0, w.iflags, w.iticket, w.ierr);
+  CARE_LAUNCH();
+  return w.F0;
+}
+
 // ILU(0) of M_p = A^T + sigma I into w.F0 / w.F1; returns the final factor.
 template <class T>
 static const T* ilu_setup(const OpT<T>& op, cd sigma, bool cplx, KrylovWork<T>& w, cudaStream_t s) {
@@ -1159,10 +1387,14 @@ KrylovResult krylov_bicgstab(const OpT<T>& op, cd sigma, bool cplx, const T* rhs
   CARE_REQUIRE(cols <= kMaxRealCols && cols > 0, CARE_ERR_INVALID_ARG, "krylov: bad width");
   CARE_REQUIRE(!cplx || cols % 2 == 0, CARE_ERR_INVALID_ARG, "krylov: odd complex width");
   int pmode = 0;
-  if (precond == CARE_PRECOND_ILU0 && w.ilu && op.full_diag) pmode = 2;
-  else if ((precond == CARE_PRECOND_JACOBI || precond == CARE_PRECOND_ILU0) && !op.diag_const && w.Ph != nullptr)
+  const bool ilu_req = precond == CARE_PRECOND_ILU0 || precond == CARE_PRECOND_ILU0_EXACT;
+  if (ilu_req && w.ilu && op.full_diag) pmode = 2;
+  else if ((precond == CARE_PRECOND_JACOBI || ilu_req) && !op.diag_const && w.Ph != nullptr)
     pmode = 1;  // ILU(0) needs every diagonal entry and sparse rows; Jacobi otherwise
+  const bool exact = pmode == 2 && precond == CARE_PRECOND_ILU0_EXACT;
   KArgs<T> a{};
+  a.exact = exact ? 1 : 0;
+  a.iflags = w.iflags; a.iticket = w.iticket; a.ierr = w.ierr;
   a.n = op.n;
   a.ld = pad_ld<T>(cols);
   a.nvec = a.ld / VEC;
@@ -1184,7 +1416,7 @@ KrylovResult krylov_bicgstab(const OpT<T>& op, cd sigma, bool cplx, const T* rhs
     k_dinv<T><<<device_sms() * 4, kBlock, 0, s>>>(op.n, op.diag, sigma.re, sigma.im, cplx, w.Dinv);
     CARE_LAUNCH();
   } else if (pmode == 2) {
-    a.F = ilu_setup<T>(op, sigma, cplx, w, s);
+    a.F = exact ? ilu_exact_setup<T>(op, sigma, cplx, w, s) : ilu_setup<T>(op, sigma, cplx, w, s);
   }
   KrylovResult r;
 #define CARE_BICG_CASE(TP, NV)                                                                        \
@@ -1231,12 +1463,474 @@ done:
     const int nst = cplx ? cols / 2 : cols;
     std::vector<KState> hs(nst);
     CARE_CUDA(cudaMemcpyAsync(hs.data(), w.st, sizeof(KState) * nst, cudaMemcpyDeviceToHost, s));
+    int ierr = 0;
+    if (exact) CARE_CUDA(cudaMemcpyAsync(&ierr, w.ierr, sizeof(int), cudaMemcpyDeviceToHost, s));
     CARE_CUDA(cudaStreamSynchronize(s));
+    CARE_REQUIRE(ierr == 0, CARE_TIMEOUT, "exact ILU(0): a bounded wait expired");
     for (int j = 0; j < nst; ++j)
       if (hs[j].flag != 1) ++r.unconverged;
   }
   return r;
 }
+// ------------------------------------------------------------------ GMRES ---
+
+struct GmView {
+  double *H, *cs, *sn, *g, *misc;
+  __host__ __device__ GmView(double* base, int m) {
+    H = base;
+    cs = H + 2 * (m + 1) * m;
+    sn = cs + m;
+    g = sn + 2 * m;
+    misc = g + 2 * (m + 1);  // beta0, flag, steps
+  }
+};
+
+// part[cta][q][c] (complex: 2 doubles) = sum over the CTA's row slab of conj(V_q) W,
+// c over the (complex) columns; V_q = V + q * blk
+template <class T, bool CPLX>
+__global__ void k_gm_dots(long n, int ld, int ncol, const T* __restrict__ V, long blk, int nq,
+                          const T* __restrict__ W, double* __restrict__ part) {
+  const long per = (n + gridDim.x - 1) / gridDim.x;
+  const long r0 = blockIdx.x * per, r1 = min(n, r0 + per);
+  const int items = nq * ncol;
+  for (int t = threadIdx.x; t < items; t += blockDim.x) {
+    const int q = t / ncol, c = t % ncol;
+    const T* vq = V + (size_t)q * blk;
+    double re = 0.0, im = 0.0;
+    for (long r = r0; r < r1; ++r) {
+      if constexpr (CPLX) {
+        const double vr = vq[(size_t)r * ld + 2 * c], vi = vq[(size_t)r * ld + 2 * c + 1];
+        const double wr = W[(size_t)r * ld + 2 * c], wi = W[(size_t)r * ld + 2 * c + 1];
+        re += vr * wr + vi * wi;
+        im += vr * wi - vi * wr;
+      } else {
+        re += (double)vq[(size_t)r * ld + c] * (double)W[(size_t)r * ld + c];
+      }
+    }
+    double* o = part + ((size_t)blockIdx.x * nq * ncol + t) * 2;
+    o[0] = re;
+    o[1] = im;
+  }
+}
+// out[q][c] (2 doubles) = fixed-order sum over the CTAs
+__global__ void k_gm_dots_reduce(int ctas, int items, const double* __restrict__ part, double* __restrict__ out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < items; t += gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < ctas; ++b) {
+      re += part[((size_t)b * items + t) * 2];
+      im += part[((size_t)b * items + t) * 2 + 1];
+    }
+    out[2 * t] = re;
+    out[2 * t + 1] = im;
+  }
+}
+
+// W[r][c] = beta_w W[r][c] + sum_q coef[q][c] V_q[r][c]  (complex coefficients in
+// complex mode; coef as produced by k_gm_dots_reduce, scaled by cscale)
+template <class T, bool CPLX>
+__global__ void k_gm_combine(long n, int ld, int ncol, T* __restrict__ W, double beta_w, const T* __restrict__ V,
+                             long blk, int nq, const double* __restrict__ coef, double cscale) {
+  const long total = n * (long)ncol;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / ncol;
+    const int c = (int)(e % ncol);
+    if constexpr (CPLX) {
+      double ar = beta_w * (double)W[(size_t)r * ld + 2 * c], ai = beta_w * (double)W[(size_t)r * ld + 2 * c + 1];
+      for (int q = 0; q < nq; ++q) {
+        const double hr = cscale * coef[2 * (q * ncol + c)], hi = cscale * coef[2 * (q * ncol + c) + 1];
+        const double vr = V[(size_t)q * blk + (size_t)r * ld + 2 * c], vi = V[(size_t)q * blk + (size_t)r * ld + 2 * c + 1];
+        ar += hr * vr - hi * vi;
+        ai += hr * vi + hi * vr;
+      }
+      W[(size_t)r * ld + 2 * c] = (T)ar;
+      W[(size_t)r * ld + 2 * c + 1] = (T)ai;
+    } else {
+      double a = beta_w * (double)W[(size_t)r * ld + c];
+      for (int q = 0; q < nq; ++q) a += cscale * coef[2 * (q * ncol + c)] * (double)V[(size_t)q * blk + (size_t)r * ld + c];
+      W[(size_t)r * ld + c] = (T)a;
+    }
+  }
+}
+
+// dst[r][c] = src[r][c] * s[c] (complex columns share s[c]); the padding columns of
+// dst (beyond the valid ones, up to ld) are set to zero
+template <class T, bool CPLX>
+__global__ void k_gm_scale(long n, int ld, int ncol, const T* __restrict__ src, const double* __restrict__ sc,
+                           T* __restrict__ dst) {
+  const long total = n * (long)ld;
+  const int valid = CPLX ? 2 * ncol : ncol;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / ld;
+    const int c = (int)(e % ld);
+    const int cc = CPLX ? c / 2 : c;
+    dst[(size_t)r * ld + c] = c < valid ? (T)(sc[cc] * (double)src[(size_t)r * ld + c]) : T(0);
+  }
+}
+
+// dst = right-hand side in the padded block layout (zeros beyond the valid columns)
+template <class T>
+__global__ void k_gm_copy_in(KArgs<T> a, T* __restrict__ dst) {
+  const long total = a.n * (long)a.ld;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / a.ld;
+    const int c = (int)(e % a.ld);
+    dst[e] = c < a.cols ? a.rhs[(size_t)r * a.ld_rhs + c] : T(0);
+  }
+}
+
+// Start of a cycle: from nr = ||r||^2 (dots output, re part) set beta0, g = (beta, 0..),
+// scale[c] = 1 / beta (0 for converged / zero columns), steps = 0.  At the first
+// cycle bnorm[c] = ||b_c|| is recorded; a column whose ||r|| <= tol ||b|| is done.
+__global__ void k_gm_start(int ncol, int m, const double* __restrict__ nr, double* __restrict__ GS,
+                           double* __restrict__ bnorm, int first, double tol, double* __restrict__ scale,
+                           int* __restrict__ active) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += gridDim.x * blockDim.x) {
+    GmView v(GS + (size_t)c * gm_state_stride(m), m);
+    const double beta = sqrt(fmax(nr[2 * c], 0.0));
+    if (first) bnorm[c] = beta;
+    const bool done = !(beta > tol * bnorm[c]) || !isfinite(beta);
+    for (int i = 0; i < 2 * (m + 1); ++i) v.g[i] = 0.0;
+    v.g[0] = beta;
+    v.misc[0] = beta;
+    v.misc[1] = done ? 1.0 : 0.0;
+    v.misc[2] = 0.0;
+    scale[c] = done ? 0.0 : 1.0 / beta;
+    if (!done) atomicAdd(active, 1);
+  }
+}
+
+// Arnoldi step k for every column: h (k+1 complex coefficients, CGS2 sum) and
+// hn = ||w||^2 give H(:, k); earlier rotations applied, a new one computed; g
+// rotated; scale[c] = 1 / ||w|| for the next basis vector.  Converged columns keep
+// their state (their basis vectors are scaled by 0).
+__global__ void k_gm_arnoldi(int ncol, int m, int k, const double* __restrict__ h1, const double* __restrict__ h2,
+                             const double* __restrict__ nw, double* __restrict__ GS, double tol,
+                             double* __restrict__ scale, int* __restrict__ active) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += gridDim.x * blockDim.x) {
+    GmView v(GS + (size_t)c * gm_state_stride(m), m);
+    if (v.misc[1] != 0.0) {
+      scale[c] = 0.0;
+      continue;
+    }
+    double* Hk = v.H + (size_t)2 * (m + 1) * k;  // column k: m+1 complex entries
+    for (int i = 0; i <= k; ++i) {
+      Hk[2 * i] = h1[2 * (i * ncol + c)] + h2[2 * (i * ncol + c)];
+      Hk[2 * i + 1] = h1[2 * (i * ncol + c) + 1] + h2[2 * (i * ncol + c) + 1];
+    }
+    const double hn = sqrt(fmax(nw[2 * c], 0.0));
+    Hk[2 * (k + 1)] = hn;
+    Hk[2 * (k + 1) + 1] = 0.0;
+    // earlier rotations: [a; b] <- [c a + s b; -conj(s) a + c b]
+    for (int i = 0; i < k; ++i) {
+      const cd a{Hk[2 * i], Hk[2 * i + 1]}, b{Hk[2 * i + 2], Hk[2 * i + 3]};
+      const double cc = v.cs[i];
+      const cd s{v.sn[2 * i], v.sn[2 * i + 1]};
+      const cd sb = cmul(s, b), sa = cmul(cconj(s), a);
+      Hk[2 * i] = cc * a.re + sb.re;
+      Hk[2 * i + 1] = cc * a.im + sb.im;
+      Hk[2 * i + 2] = cc * b.re - sa.re;
+      Hk[2 * i + 3] = cc * b.im - sa.im;
+    }
+    // new rotation zeroing H(k+1, k): c = |a| / r, s = (a / |a|) conj(b) / r
+    const cd a{Hk[2 * k], Hk[2 * k + 1]}, b{Hk[2 * k + 2], Hk[2 * k + 3]};
+    const double aa = hypot(a.re, a.im), bb = hypot(b.re, b.im), rr = hypot(aa, bb);
+    double cc = 1.0;
+    cd s{0.0, 0.0};
+    if (rr > 0.0) {
+      if (aa == 0.0) {
+        cc = 0.0;
+        s = cconj(cd{b.re / bb, b.im / bb});
+      } else {
+        cc = aa / rr;
+        const cd ph{a.re / aa, a.im / aa};
+        s = cmul(ph, cd{b.re / rr, -b.im / rr});
+      }
+    }
+    v.cs[k] = cc;
+    v.sn[2 * k] = s.re;
+    v.sn[2 * k + 1] = s.im;
+    const cd sb = cmul(s, b);
+    Hk[2 * k] = cc * a.re + sb.re;
+    Hk[2 * k + 1] = cc * a.im + sb.im;
+    Hk[2 * k + 2] = 0.0;
+    Hk[2 * k + 3] = 0.0;
+    // g(k..k+1) rotated
+    const cd gk{v.g[2 * k], v.g[2 * k + 1]};
+    const cd sg = cmul(cconj(s), gk);
+    v.g[2 * k] = cc * gk.re;
+    v.g[2 * k + 1] = cc * gk.im;
+    v.g[2 * k + 2] = -sg.re;
+    v.g[2 * k + 3] = -sg.im;
+    v.misc[2] = k + 1;
+    const double res = hypot(v.g[2 * k + 2], v.g[2 * k + 3]);
+    scale[c] = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (res <= tol * v.misc[3] || hn == 0.0 || !isfinite(res)) {
+      v.misc[1] = 1.0;  // converged (or breakdown: the Krylov space is invariant)
+      atomicSub(active, 1);
+    }
+  }
+}
+
+// y = H(0:s, 0:s)^{-1} g(0:s) (upper triangular, s = steps of the cycle), into
+// coef[q][c] for the correction sum_q y_q V_q
+__global__ void k_gm_solve(int ncol, int m, const double* __restrict__ GS, double* __restrict__ coef) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += gridDim.x * blockDim.x) {
+    GmView v(const_cast<double*>(GS) + (size_t)c * gm_state_stride(m), m);
+    const int st = (int)v.misc[2];
+    for (int q = 0; q < m; ++q) {
+      coef[2 * (q * ncol + c)] = 0.0;
+      coef[2 * (q * ncol + c) + 1] = 0.0;
+    }
+    for (int i = st - 1; i >= 0; --i) {
+      cd acc{v.g[2 * i], v.g[2 * i + 1]};
+      for (int j = i + 1; j < st; ++j) {
+        const double* Hj = v.H + (size_t)2 * (m + 1) * j;
+        const cd t = cmul(cd{Hj[2 * i], Hj[2 * i + 1]}, cd{coef[2 * (j * ncol + c)], coef[2 * (j * ncol + c) + 1]});
+        acc.re -= t.re;
+        acc.im -= t.im;
+      }
+      const double* Hi = v.H + (size_t)2 * (m + 1) * i;
+      const cd y = cdivz(acc, cd{Hi[2 * i], Hi[2 * i + 1]});
+      coef[2 * (i * ncol + c)] = y.re;
+      coef[2 * (i * ncol + c) + 1] = y.im;
+    }
+  }
+}
+
+__global__ void k_gm_set_bnorm(int ncol, int m, double* __restrict__ GS, const double* __restrict__ bn) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += gridDim.x * blockDim.x)
+    GS[(size_t)c * gm_state_stride(m) + gm_state_stride(m) - 1] = bn[c];
+}
+
+// Jacobi preconditioner apply for GMRES: out = Dinv x
+template <class T, bool CPLX>
+__global__ void k_gm_jacobi(long n, int ld, int ncol, const T* __restrict__ dinv, const T* __restrict__ x,
+                            T* __restrict__ out) {
+  const long total = n * (long)ncol;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / ncol;
+    const int c = (int)(e % ncol);
+    if constexpr (CPLX) {
+      const T dr = dinv[2 * r], di = dinv[2 * r + 1];
+      const T xr = x[(size_t)r * ld + 2 * c], xi = x[(size_t)r * ld + 2 * c + 1];
+      out[(size_t)r * ld + 2 * c] = dr * xr - di * xi;
+      out[(size_t)r * ld + 2 * c + 1] = dr * xi + di * xr;
+    } else {
+      out[(size_t)r * ld + c] = dinv[r] * x[(size_t)r * ld + c];
+    }
+  }
+}
+
+template <class T, bool CPLX, int TPR, int NVPT>
+static KrylovResult run_gmres(const OpT<T>& op, cd sigma, const KArgs<T>& a, int pmode, double tol, int maxit,
+                              KrylovWork<T>& w, int grid, cudaStream_t s) {
+  KrylovResult res;
+  const long n = op.n;
+  const int ld = a.ld, m = w.gm_restart;
+  const int ncol = CPLX ? a.cols / 2 : a.cols;
+  const long blk = n * (long)ld;
+  const int dctas = gm_dot_ctas();
+  const int eg = device_sms() * 4;
+  double* bn = w.out;                   // ||b|| per column
+  double* scale = w.out + kMaxRealCols; // per-column scale factors
+  double* h1 = w.GH;                    // (m+1) x ncol complex
+  double* h2 = w.GH + (size_t)(m + 1) * kMaxRealCols;
+  double* nw = w.partial;               // norm^2 per column (complex layout)
+  int* active = &w.hdr->n_active;
+  T* R = w.R;    // residual / new Arnoldi vector
+  T* X = w.X;    // solution
+  T* Zb = w.GZ;  // preconditioned vector
+  auto dots = [&](const T* Vq, int nq, const T* Wv, double* out) {
+    k_gm_dots<T, CPLX><<<dctas, 256, 0, s>>>(n, ld, ncol, Vq, blk, nq, Wv, w.GP);
+    CARE_LAUNCH();
+    k_gm_dots_reduce<<<(nq * ncol + 127) / 128, 128, 0, s>>>(dctas, nq * ncol, w.GP, out);
+    CARE_LAUNCH();
+  };
+  auto precond = [&](const T* x, T* out) {
+    if (pmode == 2) {
+      ilu_apply<T, TPR, NVPT, CPLX>(a, x, out, grid, s);
+    } else if (pmode == 1) {
+      k_gm_jacobi<T, CPLX><<<eg, 256, 0, s>>>(n, ld, ncol, a.Dinv, x, out);
+      CARE_LAUNCH();
+    } else {
+      CARE_CUDA(cudaMemcpyAsync(out, x, sizeof(T) * blk, cudaMemcpyDeviceToDevice, s));
+    }
+  };
+  SpmmArgs<T> sp{};
+  sp.n = n; sp.rp = op.rp; sp.ci = op.ci; sp.av = op.val; sp.rs = op.rowsum; sp.ldx = ld; sp.ldy = ld;
+  sp.nvec = a.nvec; sp.sre = sigma.re; sp.sim = sigma.im;
+  auto matvec = [&](const T* x, T* y) {
+    sp.X = x; sp.Y = y;
+    k_spmm<T, TPR, NVPT, CPLX, 0><<<grid, kBlock, 0, s>>>(sp);
+    CARE_LAUNCH();
+  };
+  // x = 0, r = b (padded block copy of the right-hand side)
+  CARE_CUDA(cudaMemsetAsync(X, 0, sizeof(T) * blk, s));
+  k_gm_copy_in<T><<<eg, 256, 0, s>>>(a, R);
+  CARE_LAUNCH();
+  int steps_total = 0;
+  bool first = true;
+  for (;;) {
+    // cycle start: beta = ||r||, v_0 = r / beta
+    dots(R, 1, R, nw);
+    CARE_CUDA(cudaMemsetAsync(active, 0, sizeof(int), s));
+    k_gm_start<<<1, 128, 0, s>>>(ncol, m, nw, w.GS, bn, first ? 1 : 0, tol, scale, active);
+    CARE_LAUNCH();
+    if (first) {
+      k_gm_set_bnorm<<<1, 128, 0, s>>>(ncol, m, w.GS, bn);
+      CARE_LAUNCH();
+    }
+    first = false;
+    int act = 0;
+    CARE_CUDA(cudaMemcpyAsync(&act, active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CARE_CUDA(cudaStreamSynchronize(s));
+    if (act == 0 || steps_total >= maxit) break;
+    k_gm_scale<T, CPLX><<<eg, 256, 0, s>>>(n, ld, ncol, R, scale, w.GV);
+    CARE_LAUNCH();
+    int k = 0;
+    for (; k < m && steps_total < maxit; ++k) {
+      T* vk = w.GV + (size_t)k * blk;
+      precond(vk, Zb);
+      matvec(Zb, R);  // w = A M^{-1} v_k
+      ++res.spmm;
+      // classical Gram-Schmidt, twice
+      dots(w.GV, k + 1, R, h1);
+      k_gm_combine<T, CPLX><<<eg, 256, 0, s>>>(n, ld, ncol, R, 1.0, w.GV, blk, k + 1, h1, -1.0);
+      CARE_LAUNCH();
+      dots(w.GV, k + 1, R, h2);
+      k_gm_combine<T, CPLX><<<eg, 256, 0, s>>>(n, ld, ncol, R, 1.0, w.GV, blk, k + 1, h2, -1.0);
+      CARE_LAUNCH();
+      dots(R, 1, R, nw);
+      k_gm_arnoldi<<<1, 128, 0, s>>>(ncol, m, k, h1, h2, nw, w.GS, tol, scale, active);
+      CARE_LAUNCH();
+      k_gm_scale<T, CPLX><<<eg, 256, 0, s>>>(n, ld, ncol, R, scale, w.GV + (size_t)(k + 1) * blk);
+      CARE_LAUNCH();
+      ++steps_total;
+      if ((k + 1) % 4 == 0) {
+        CARE_CUDA(cudaMemcpyAsync(&act, active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CARE_CUDA(cudaStreamSynchronize(s));
+        if (act == 0) {
+          ++k;
+          break;
+        }
+      }
+    }
+    // x += M^{-1} (V y), then the true residual r = b - A x for the restart test.
+    // Only the k basis blocks built in this cycle take part: later blocks hold an
+    // earlier cycle's vectors or never-written memory, and a zero coefficient times
+    // a non-finite stale entry would still poison the sum
+    if (k == 0) break;
+    k_gm_solve<<<1, 128, 0, s>>>(ncol, m, w.GS, h1);
+    CARE_LAUNCH();
+    CARE_CUDA(cudaMemsetAsync(R, 0, sizeof(T) * blk, s));
+    k_gm_combine<T, CPLX><<<eg, 256, 0, s>>>(n, ld, ncol, R, 0.0, w.GV, blk, k, h1, 1.0);
+    CARE_LAUNCH();
+    precond(R, Zb);
+    axpby<T>(n, ld, 1.0, Zb, ld, 1.0, X, ld, s);
+    matvec(X, Zb);
+    ++res.spmm;
+    k_gm_copy_in<T><<<eg, 256, 0, s>>>(a, R);
+    CARE_LAUNCH();
+    axpby<T>(n, ld, -1.0, Zb, ld, 1.0, R, ld, s);
+  }
+  res.iters = steps_total;
+  return res;
+}
+
+template <class T>
+KrylovResult krylov_gmres(const OpT<T>& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol, int ld_sol,
+                          int cols, double tol, int maxit, int precond, KrylovWork<T>& w, cudaStream_t s) {
+  constexpr int VEC = 16 / sizeof(T);
+  CARE_REQUIRE(w.gm_restart > 0 && w.GV, CARE_ERR_INVALID_ARG, "gmres: workspace has no basis");
+  CARE_REQUIRE(cols <= kMaxRealCols && cols > 0, CARE_ERR_INVALID_ARG, "gmres: bad width");
+  CARE_REQUIRE(!cplx || cols % 2 == 0, CARE_ERR_INVALID_ARG, "gmres: odd complex width");
+  int pmode = 0;
+  const bool ilu_req = precond == CARE_PRECOND_ILU0 || precond == CARE_PRECOND_ILU0_EXACT;
+  if (ilu_req && w.ilu && op.full_diag) pmode = 2;
+  else if ((precond == CARE_PRECOND_JACOBI || ilu_req) && !op.diag_const && w.Ph != nullptr)
+    pmode = 1;
+  const bool exact = pmode == 2 && precond == CARE_PRECOND_ILU0_EXACT;
+  KArgs<T> a{};
+  a.exact = exact ? 1 : 0;
+  a.iflags = w.iflags; a.iticket = w.iticket; a.ierr = w.ierr;
+  a.n = op.n;
+  a.ld = pad_ld<T>(cols);
+  a.nvec = a.ld / VEC;
+  a.X = w.X; a.R = w.R;
+  a.Dinv = w.Dinv;
+  a.rhs = rhs; a.ld_rhs = ld_rhs; a.sol = sol; a.ld_sol = ld_sol; a.cols = cols;
+  a.st = w.st; a.hdr = w.hdr;
+  a.rp = op.rp; a.ci = op.ci; a.dpos = w.dpos; a.Y1 = w.Y1; a.Y2 = w.Y2; a.Y3 = w.Y3;
+  a.tri_sweeps = w.tri_sweeps < 1 ? 1 : w.tri_sweeps;
+  const int tpr = tpr_for(a.nvec);
+  const int nvpt = (a.nvec + 31) / 32;
+  const int grid = grid_rows(op.n, tpr);
+  CARE_CUDA(cudaMemsetAsync(w.hdr, 0, sizeof(KHeader), s));
+  if (pmode == 1) {
+    k_dinv<T><<<device_sms() * 4, kBlock, 0, s>>>(op.n, op.diag, sigma.re, sigma.im, cplx, w.Dinv);
+    CARE_LAUNCH();
+  } else if (pmode == 2) {
+    a.F = exact ? ilu_exact_setup<T>(op, sigma, cplx, w, s) : ilu_setup<T>(op, sigma, cplx, w, s);
+  }
+  // the tolerance is applied to the true residual at every restart and to the
+  // Givens estimate within a cycle; the per-column ||b|| sits in the last state slot
+  KrylovResult r;
+#define CARE_GM_CASE(TP, NV)                                                               \
+  if (tpr == TP && nvpt == NV) {                                                           \
+    r = cplx ? run_gmres<T, true, TP, NV>(op, sigma, a, pmode, tol, maxit, w, grid, s)     \
+             : run_gmres<T, false, TP, NV>(op, sigma, a, pmode, tol, maxit, w, grid, s);   \
+    goto gm_done;                                                                          \
+  }
+  CARE_GM_CASE(1, 1) CARE_GM_CASE(2, 1) CARE_GM_CASE(4, 1) CARE_GM_CASE(8, 1)
+  CARE_GM_CASE(16, 1) CARE_GM_CASE(32, 1) CARE_GM_CASE(32, 2)
+#undef CARE_GM_CASE
+  CARE_THROW(CARE_ERR_INVALID_ARG, "gmres: unsupported width");
+gm_done:
+  k_copy_out<T><<<device_sms() * 4, kBlock, 0, s>>>(a);
+  CARE_LAUNCH();
+  {
+    // unconverged columns: the flag of the last cycle's start test
+    const int ncol = cplx ? cols / 2 : cols;
+    std::vector<double> st(gm_state_stride(w.gm_restart) * ncol);
+    CARE_CUDA(cudaMemcpyAsync(st.data(), w.GS, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, s));
+    int ierr = 0;
+    if (exact) CARE_CUDA(cudaMemcpyAsync(&ierr, w.ierr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CARE_CUDA(cudaStreamSynchronize(s));
+    CARE_REQUIRE(ierr == 0, CARE_TIMEOUT, "exact ILU(0): a bounded wait expired");
+    for (int c = 0; c < ncol; ++c)
+      if (st[(size_t)c * gm_state_stride(w.gm_restart) + 2 * (w.gm_restart + 1) * w.gm_restart + w.gm_restart +
+             2 * w.gm_restart + 2 * (w.gm_restart + 1) + 1] == 0.0)
+        ++r.unconverged;
+    const double sv = sizeof(T), sf = sv * (cplx ? 2 : 1);
+    const double blkb = (double)op.n * a.ld * sv;
+    const double amat = (double)op.nnz * (sv + 4) + 4.0 * (op.n + 1) + (op.rowsum ? sv * op.n : 0.0);
+    // per Arnoldi step k: matvec (2 passes + operator), preconditioner, two CGS
+    // passes of (k+2) + (k+2) block passes, the norm and the scaling (3 passes)
+    const double avgk = 0.5 * std::min(w.gm_restart, std::max(r.iters, 1));
+    double per = amat + 2 * blkb + 4 * (avgk + 2) * blkb + 3 * blkb;
+    if (pmode == 2) per += 2.0 * a.tri_sweeps * (3 * blkb + 0.5 * op.nnz * (sf + 4));
+    r.bytes = per * r.iters;
+  }
+  return r;
+}
+template KrylovResult krylov_gmres<float>(const OpT<float>&, cd, bool, const float*, int, float*, int, int, double,
+                                          int, int, KrylovWork<float>&, cudaStream_t);
+template KrylovResult krylov_gmres<double>(const OpT<double>&, cd, bool, const double*, int, double*, int, int,
+                                           double, int, int, KrylovWork<double>&, cudaStream_t);
+
+template <class T>
+void ilu0_factor(const OpT<T>& op, cd sigma, bool cplx, bool exact, KrylovWork<T>& w, T* F, cudaStream_t s) {
+  CARE_REQUIRE(w.ilu && op.full_diag, CARE_ERR_INVALID_ARG, "ilu0: needs the ILU workspace and a full diagonal");
+  const T* f = exact ? ilu_exact_setup<T>(op, sigma, cplx, w, s) : ilu_setup<T>(op, sigma, cplx, w, s);
+  CARE_CUDA(cudaMemcpyAsync(F, f, sizeof(T) * (size_t)op.nnz * (cplx ? 2 : 1), cudaMemcpyDeviceToDevice, s));
+  int ierr = 0;
+  if (exact) CARE_CUDA(cudaMemcpyAsync(&ierr, w.ierr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CARE_CUDA(cudaStreamSynchronize(s));
+  CARE_REQUIRE(ierr == 0, CARE_TIMEOUT, "exact ILU(0): a bounded wait expired");
+}
+template void ilu0_factor<float>(const OpT<float>&, cd, bool, bool, KrylovWork<float>&, float*, cudaStream_t);
+template void ilu0_factor<double>(const OpT<double>&, cd, bool, bool, KrylovWork<double>&, double*, cudaStream_t);
+
 template KrylovResult krylov_bicgstab<float>(const OpT<float>&, cd, bool, const float*, int, float*, int,
                                              int, double, int, int, KrylovWork<float>&, cudaStream_t);
 template KrylovResult krylov_bicgstab<double>(const OpT<double>&, cd, bool, const double*, int, double*,

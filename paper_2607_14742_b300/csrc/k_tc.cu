@@ -27,38 +27,47 @@ constexpr long long WAIT_NS = 2000000000LL;  // bound on any single mbarrier wai
 // error codes written to the device error word
 constexpr int ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_ACC = 3, ERR_WAIT_ACCE = 4;
 
-// ---- slice pairs of the FP64 mode ------------------------------------------
-// Pairs (a, b) with a + b <= 8.  Tail pairs (a + b >= 5, accumulator 5) come
-// first within every K-step so that the MMAs of a new chunk can start while the
-// epilogue still drains the exact groups of the previous one; the exact pairs
-// follow, grouped by a + b (accumulator a + b).
+// ---- slice pairs of the sliced modes --------------------------------------------
+// FP64 mode: pairs (a, b) with a + b <= 8 of 8 slices.  Tail pairs (a + b >= 5,
+// accumulator 5) come first within every K-step so that the MMAs of a new chunk
+// can start while the epilogue still drains the exact groups of the previous one;
+// the exact pairs follow, grouped by a + b (accumulator a + b).
+// FP32 mode: pairs with a + b <= 3 of 4 slices, all exact (accumulator a + b).
 struct PairTable {
   int n;
   int a[48], b[48], acc[48], first[48];
 };
-constexpr PairTable make_pairs() {
+constexpr PairTable make_pairs(int nsl, int smax, int sexact) {
   PairTable t{};
   int k = 0;
-  for (int s = 5; s <= 8; ++s)
-    for (int a = 0; a < NSLICE; ++a) {
+  for (int s = sexact + 1; s <= smax; ++s)
+    for (int a = 0; a < nsl; ++a) {
       const int b = s - a;
-      if (b < 0 || b >= NSLICE) continue;
-      t.a[k] = a; t.b[k] = b; t.acc[k] = 5; t.first[k] = (k == 0); ++k;
+      if (b < 0 || b >= nsl) continue;
+      t.a[k] = a; t.b[k] = b; t.acc[k] = sexact + 1; t.first[k] = (k == 0); ++k;
     }
-  for (int s = 0; s <= 4; ++s)
+  for (int s = 0; s <= sexact && s <= smax; ++s)
     for (int a = 0; a <= s; ++a) {
+      if (a >= nsl || s - a >= nsl) continue;
       t.a[k] = a; t.b[k] = s - a; t.acc[k] = s; t.first[k] = (a == 0); ++k;
     }
   t.n = k;
   return t;
 }
-constexpr PairTable kPairs = make_pairs();
-constexpr int kNumPairs = 43;
-constexpr int kFirstExact = 28;  // index of the first exact pair
-static_assert(kPairs.n == kNumPairs, "43 slice pairs with a + b <= 8");
-static_assert(kPairs.acc[kFirstExact] == 0 && kPairs.acc[kFirstExact - 1] == 5, "pair order");
-// device copy (constant bank; the MMA loop indexes it with unrolled constants)
-__constant__ PairTable c_pairs = make_pairs();
+constexpr PairTable kPairs64 = make_pairs(NSLICE, 8, 4);
+constexpr PairTable kPairs32 = make_pairs(4, 3, 3);
+static_assert(kPairs64.n == 43 && kPairs64.acc[28] == 0 && kPairs64.acc[27] == 5, "FP64 pairs");
+static_assert(kPairs32.n == 10 && kPairs32.acc[0] == 0 && kPairs32.acc[9] == 3, "FP32 pairs");
+// device copies (constant bank; the MMA loop indexes them with unrolled constants)
+__constant__ PairTable c_pairs64 = make_pairs(NSLICE, 8, 4);
+__constant__ PairTable c_pairs32 = make_pairs(4, 3, 3);
+template <int MODE>
+__device__ __forceinline__ int pair_field(int p, int f) {
+  if constexpr (MODE == 0)
+    return f == 0 ? c_pairs64.a[p] : f == 1 ? c_pairs64.b[p] : f == 2 ? c_pairs64.acc[p] : c_pairs64.first[p];
+  else
+    return f == 0 ? c_pairs32.a[p] : f == 1 ? c_pairs32.b[p] : f == 2 ? c_pairs32.acc[p] : c_pairs32.first[p];
+}
 
 // ---- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -184,19 +193,25 @@ struct TcArgs {
   int starve;        // test hook: issue no copies (the first wait then expires)
 };
 
-// MODE 0: FP64 slices (kind::f16, BF16 slices); 1: TF32 (kind::tf32, FP32
-// operands); 2: BF16 (kind::f16, one BF16 slice).
+// MODE 0: FP64-accurate slices (8 BF16 slices, 43 pairs, 5 exact groups + tail);
+// 1: TF32 (kind::tf32, FP32 operands); 2: BF16 (kind::f16, one BF16 slice);
+// 3: FP32-accurate slices (4 BF16 slices, 10 pairs, all in 4 exact groups).
 template <int MODE>
 struct TcCfg {
-  static constexpr int NSL = MODE == 0 ? NSLICE : 1;
-  static constexpr int STAGES = MODE == 0 ? 2 : 8;
+  static constexpr bool SLICED = MODE == 0 || MODE == 3;
+  static constexpr int NSL = MODE == 0 ? NSLICE : (MODE == 3 ? 4 : 1);
+  static constexpr int NPAIR = MODE == 0 ? 43 : 10;
+  static constexpr int FIRST_EXACT = MODE == 0 ? 28 : 0;
+  static constexpr int NEXACT = MODE == 0 ? 5 : 4;      // exact accumulators 0 .. NEXACT-1
+  static constexpr bool TAIL = MODE == 0;               // accumulator NEXACT holds the tail
+  static constexpr int STAGES = MODE == 0 ? 2 : (MODE == 3 ? 4 : 8);
   static constexpr int ESZ = MODE == 1 ? 4 : 2;
   static constexpr int KEL = ROWB / ESZ;            // K elements per stage
   static constexpr int KSTEP = 32 / ESZ;            // K elements per MMA (32 bytes)
   static constexpr int A_BYTES = BM * ROWB;
   static constexpr int B_BYTES = BN * ROWB;
   static constexpr int STAGE_BYTES = NSL * (A_BYTES + B_BYTES);
-  static constexpr uint32_t TCOLS = MODE == 0 ? 512 : 64;
+  static constexpr uint32_t TCOLS = MODE == 0 ? 512 : (MODE == 3 ? 256 : 64);
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -212,8 +227,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int kbeg = split * g.k_per_split;
   const int kend = min(g.k_len, kbeg + g.k_per_split);
   const int nst = (kend - kbeg + C::KEL - 1) / C::KEL;  // stages (>= 1: every split has K)
-  constexpr int SPC = MODE == 0 ? CHUNK / C::KEL : 1 << 30;
-  const int nchunks = MODE == 0 ? (nst + SPC - 1) / SPC : 1;
+  constexpr int SPC = C::SLICED ? CHUNK / C::KEL : 1 << 30;
+  const int nchunks = C::SLICED ? (nst + SPC - 1) / SPC : 1;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -303,10 +318,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t sb = sa + C::NSL * C::A_BYTES;
 #pragma unroll
           for (int kk = 0; kk < C::KEL / C::KSTEP; ++kk) {
-            if constexpr (MODE == 0) {
+            if constexpr (C::SLICED) {
 #pragma unroll
-              for (int p = 0; p < kNumPairs; ++p) {
-                if (p == kFirstExact && c > 0 && st == 0 && kk == 0) {
+              for (int p = 0; p < C::NPAIR; ++p) {
+                if (p == C::FIRST_EXACT && c > 0 && st == 0 && kk == 0) {
                   // the epilogue must have read the previous chunk's exact groups
                   if (!mbar_wait(acce, aeph, abort_flag, g.err, ERR_WAIT_ACCE)) {
                     ok = false;
@@ -315,11 +330,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   aeph ^= 1;
                   tc_fence_after();
                 }
-                const bool exact = c_pairs.acc[p] < 5;
-                const bool fresh = c_pairs.first[p] && kk == 0 && st == 0 && (exact || c == 0);
-                umma<false>(tbase + (uint32_t)(c_pairs.acc[p] * BN),
-                            desc_sw64(sa + c_pairs.a[p] * C::A_BYTES + kk * 32),
-                            desc_sw64(sb + c_pairs.b[p] * C::B_BYTES + kk * 32), idesc, fresh ? 0u : 1u);
+                const int pa = pair_field<MODE>(p, 0), pbb = pair_field<MODE>(p, 1);
+                const int pacc = pair_field<MODE>(p, 2), pfirst = pair_field<MODE>(p, 3);
+                const bool exact = pacc < C::NEXACT;
+                const bool fresh = pfirst && kk == 0 && st == 0 && (exact || c == 0);
+                umma<false>(tbase + (uint32_t)(pacc * BN), desc_sw64(sa + pa * C::A_BYTES + kk * 32),
+                            desc_sw64(sb + pbb * C::B_BYTES + kk * 32), idesc, fresh ? 0u : 1u);
               }
               if (!ok) break;
             } else {
@@ -368,7 +384,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       afph ^= 1;
       tc_fence_after();
       const bool last = c == nchunks - 1;
-      if constexpr (MODE == 0) {
+      if constexpr (C::SLICED) {
 #pragma unroll
         for (int sub = 0; sub < 4; ++sub) {
           uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
@@ -376,9 +392,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tmem_ld8(tl + 1 * BN + sub * 8, v1);
           tmem_ld8(tl + 2 * BN + sub * 8, v2);
           tmem_ld8(tl + 3 * BN + sub * 8, v3);
-          tmem_ld8(tl + 4 * BN + sub * 8, v4);
+          if constexpr (C::NEXACT > 4) tmem_ld8(tl + 4 * BN + sub * 8, v4);
           tmem_wait_ld();
-          reg_fence8(v0); reg_fence8(v1); reg_fence8(v2); reg_fence8(v3); reg_fence8(v4);
+          reg_fence8(v0); reg_fence8(v1); reg_fence8(v2); reg_fence8(v3);
+          if constexpr (C::NEXACT > 4) reg_fence8(v4);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             // group s holds an integer times 2^-7(s+2)
@@ -386,16 +403,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int g1 = f2i_exact(__uint_as_float(v1[j]) * 2097152.0f);           // 2^21
             const int g2 = f2i_exact(__uint_as_float(v2[j]) * 268435456.0f);         // 2^28
             const int g3 = f2i_exact(__uint_as_float(v3[j]) * 34359738368.0f);       // 2^35
-            const int g4 = f2i_exact(__uint_as_float(v4[j]) * 4398046511104.0f);     // 2^42
-            acc[sub * 8 + j] += (long long)g0 * (1LL << 28) + (long long)(g1 * 128 + g2) * (1LL << 14) +
-                                (long long)(g3 * 128 + g4);
+            if constexpr (C::NEXACT > 4) {
+              const int g4 = f2i_exact(__uint_as_float(v4[j]) * 4398046511104.0f);   // 2^42
+              // units of 2^-42
+              acc[sub * 8 + j] += (long long)g0 * (1LL << 28) + (long long)(g1 * 128 + g2) * (1LL << 14) +
+                                  (long long)(g3 * 128 + g4);
+            } else {
+              // units of 2^-35
+              acc[sub * 8 + j] += (long long)g0 * (1LL << 21) + (long long)(g1 * 128 + g2) * (1LL << 7) +
+                                  (long long)g3;
+            }
           }
         }
-        if (last) {
+        if (C::TAIL && last) {
 #pragma unroll
           for (int sub = 0; sub < 4; ++sub) {
             uint32_t t[8];
-            tmem_ld8(tl + 5 * BN + sub * 8, t);
+            tmem_ld8(tl + C::NEXACT * BN + sub * 8, t);
             tmem_wait_ld();
             reg_fence8(t);
 #pragma unroll
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (MODE == 0 && !last && lane == 0) mbar_arrive(acce);
+      if (C::SLICED && !last && lane == 0) mbar_arrive(acce);
     }
     if (ok) {
       const int row = row0 + q * 32 + lane;
@@ -427,7 +451,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int j = 0; j < 32; ++j) {
             const int col = col0 + h * 32 + j;
             if (col >= g.N) continue;
-            double v = MODE == 0 ? (double)acc[j] * 0x1p-42 + (double)tail[j] : (double)tail[j];
+            double v = MODE == 0 ? (double)acc[j] * 0x1p-42 + (double)tail[j]
+                                 : (MODE == 3 ? (double)acc[j] * 0x1p-35 : (double)tail[j]);
             if (g.ea) v = ldexp(v, er + g.eb[col]);
             out[col] = v;
           }
@@ -436,7 +461,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int j = 0; j < 32; ++j) {
             const int col = col0 + h * 32 + j;
             if (col >= g.N) continue;
-            double v = MODE == 0 ? (double)acc[j] * 0x1p-42 + (double)tail[j] : (double)tail[j];
+            double v = MODE == 0 ? (double)acc[j] * 0x1p-42 + (double)tail[j]
+                                 : (MODE == 3 ? (double)acc[j] * 0x1p-35 : (double)tail[j]);
             if (g.ea) v = ldexp(v, er + g.eb[col]);
             v *= g.alpha;
             if (g.y_f32) {
@@ -460,7 +486,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// ---- slicing (FP64 -> 7 BF16 slices, K-major) -------------------------------------
+// ---- slicing (FP64 / FP32 -> BF16 slices, K-major) ------------------------------------
 __device__ __forceinline__ int frexp_exp(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const int E = (int)((u >> 52) & 0x7FF);
@@ -471,13 +497,14 @@ __device__ __forceinline__ int frexp_exp(double v) {
 // Column exponents of a row slab: e[c] = max over rows of frexp exponents of X(r, c)
 // (e starts below every FP64 exponent: the host fills it with 0x80 bytes; the
 // maximum does not depend on the order of the atomics).
-__global__ void k_tc_colexp(long rows, int cols, const double* __restrict__ X, long ldx, int* __restrict__ e) {
+template <class Tin>
+__global__ void k_tc_colexp(long rows, int cols, const Tin* __restrict__ X, long ldx, int* __restrict__ e) {
   __shared__ int sm[8][33];
   const int c = blockIdx.x * 32 + threadIdx.x;
   int m = INT_MIN;
   if (c < cols)
     for (long r = (long)blockIdx.y * 8 + threadIdx.y; r < rows; r += 8L * gridDim.y)
-      m = max(m, frexp_exp(X[r * ldx + c]));
+      m = max(m, frexp_exp((double)X[r * ldx + c]));
   sm[threadIdx.y][threadIdx.x] = m;
   __syncthreads();
   if (threadIdx.y == 0 && c < cols) {
@@ -487,8 +514,9 @@ __global__ void k_tc_colexp(long rows, int cols, const double* __restrict__ X, l
   }
 }
 
-// 56-bit fixed point of x relative to 2^e (|x| < 2^e), rounded to nearest
-__device__ __forceinline__ long long fixed56(double x, int e) {
+// BITS-bit fixed point of x relative to 2^e (|x| < 2^e), rounded to nearest
+template <int BITS>
+__device__ __forceinline__ long long fixed_point(double x, int e) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((u >> 52) & 0x7FF);
   unsigned long long M = u & 0xFFFFFFFFFFFFFull;
@@ -496,9 +524,9 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
   if (E == 0) Ee = 1;
   else M |= 1ull << 52;
   if (M == 0) return 0;
-  const int sh = Ee - 1019 - e;  // x * 2^(56-e) = M * 2^sh, sh <= 3
+  const int sh = Ee - 1075 + BITS - e;  // x * 2^(BITS-e) = M * 2^sh, sh <= BITS - 53
   if (sh >= 0) {
-    const long long F = (long long)(M << sh);  // exact: M < 2^53, |F| < 2^56
+    const long long F = (long long)(M << sh);  // exact: |F| < 2^BITS
     return (u >> 63) ? -F : F;
   }
   const int r = -sh;
@@ -507,16 +535,17 @@ __device__ __forceinline__ long long fixed56(double x, int e) {
   return (u >> 63) ? -F : F;
 }
 
-__device__ __forceinline__ void split_digits(long long F, int (&s)[NSLICE]) {
-  // round-to-nearest base-2^7 digits: F = sum_a s_a 2^(7(7-a)), |s_0| <= 128, |s_a| <= 64
+// round-to-nearest base-2^7 digits: F = sum_a s_a 2^(7(NS-1-a)), |s_0| <= 128, |s_a| <= 64
+template <int NS>
+__device__ __forceinline__ void split_digits(long long F, int (&s)[NS]) {
 #pragma unroll
-  for (int a = 0; a < NSLICE - 1; ++a) {
-    const int sh = 7 * (NSLICE - 1 - a);
+  for (int a = 0; a < NS - 1; ++a) {
+    const int sh = 7 * (NS - 1 - a);
     const long long d = (F + (1LL << (sh - 1))) >> sh;
     F -= d << sh;
     s[a] = (int)d;
   }
-  s[NSLICE - 1] = (int)F;
+  s[NS - 1] = (int)F;
 }
 
 __device__ __forceinline__ uint16_t slice_bf16(int s, int a) {
@@ -526,7 +555,9 @@ __device__ __forceinline__ uint16_t slice_bf16(int s, int a) {
 
 // Transposed slicing: row i of the sliced operand is column i of X (n_slab x cols,
 // ldx); K index = row of X.  dst[a][i][k] (ldk), tiles of 32 columns x 64 rows.
-__global__ void k_tc_slice_T(long rows, int cols, const double* __restrict__ X, long ldx,
+// NS slices of 7 bits: 7 NS-bit fixed point relative to 2^e[i].
+template <class Tin, int NS>
+__global__ void k_tc_slice_T(long rows, int cols, const Tin* __restrict__ X, long ldx,
                              const int* __restrict__ e, uint16_t* __restrict__ dst, long ldk, long slice_stride) {
   __shared__ double tile[64][33];
   const int i0 = blockIdx.x * 32;
@@ -534,7 +565,7 @@ __global__ void k_tc_slice_T(long rows, int cols, const double* __restrict__ X, 
   for (int kk = threadIdx.y; kk < 64; kk += 8) {
     const long k = k0 + kk;
     const int i = i0 + threadIdx.x;
-    tile[kk][threadIdx.x] = (k < rows && i < cols) ? X[k * ldx + i] : 0.0;
+    tile[kk][threadIdx.x] = (k < rows && i < cols) ? (double)X[k * ldx + i] : 0.0;
   }
   __syncthreads();
   for (int ii = threadIdx.y; ii < 32; ii += 8) {
@@ -546,32 +577,33 @@ __global__ void k_tc_slice_T(long rows, int cols, const double* __restrict__ X, 
       const int kk = threadIdx.x + 32 * half;
       const long k = k0 + kk;
       if (k >= rows) continue;
-      int s[NSLICE];
-      split_digits(ei == INT_MIN ? 0 : fixed56(tile[kk][ii], ei), s);
+      int sl[NS];
+      split_digits<NS>(fixed_point<7 * NS>(tile[kk][ii], ei), sl);
 #pragma unroll
-      for (int a = 0; a < NSLICE; ++a) dst[a * slice_stride + (long)i * ldk + k] = slice_bf16(s[a], a);
+      for (int a = 0; a < NS; ++a) dst[a * slice_stride + (long)i * ldk + k] = slice_bf16(sl[a], a);
     }
   }
 }
 
 // Row slicing: row r of the sliced operand is row r of X (rows x cols, ldx); one
 // warp per row finds the row exponent, then writes the slices dst[a][r][k].
-__global__ void k_tc_slice_N(long rows, int cols, const double* __restrict__ X, long ldx, int* __restrict__ e,
+template <class Tin, int NS>
+__global__ void k_tc_slice_N(long rows, int cols, const Tin* __restrict__ X, long ldx, int* __restrict__ e,
                              uint16_t* __restrict__ dst, long ldk, long slice_stride) {
   const long warps = (long)gridDim.x * (blockDim.x / 32);
   const int lane = threadIdx.x & 31;
   for (long r = (blockIdx.x * (long)blockDim.x + threadIdx.x) / 32; r < rows; r += warps) {
-    const double* xr = X + r * ldx;
+    const Tin* xr = X + r * ldx;
     int m = INT_MIN;
-    for (int k = lane; k < cols; k += 32) m = max(m, frexp_exp(xr[k]));
+    for (int k = lane; k < cols; k += 32) m = max(m, frexp_exp((double)xr[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) e[r] = m == INT_MIN ? 0 : m;
     for (int k = lane; k < cols; k += 32) {
-      int s[NSLICE];
-      split_digits(m == INT_MIN ? 0 : fixed56(xr[k], m), s);
+      int sl[NS];
+      split_digits<NS>(m == INT_MIN ? 0 : fixed_point<7 * NS>((double)xr[k], m), sl);
 #pragma unroll
-      for (int a = 0; a < NSLICE; ++a) dst[a * slice_stride + r * ldk + k] = slice_bf16(s[a], a);
+      for (int a = 0; a < NS; ++a) dst[a * slice_stride + r * ldk + k] = slice_bf16(sl[a], a);
     }
   }
 }
@@ -745,8 +777,11 @@ static int choose_splits(long k_len, long tiles, long ab, size_t part_elems) {
   return (int)std::max(1L, sp);
 }
 
-void tc_gram_f64(long n, int a, int b, const double* X, int ldx, const double* Y, int ldy, double* G, int ldg,
-                 const TcScratch& sc, int maxdim, cudaStream_t s) {
+// X^T Y (a x b, FP64) of FP64 (8 slices, MODE 0) or FP32 (4 slices, MODE 3) operands
+template <class Tin>
+static void tc_gram_sliced(long n, int a, int b, const Tin* X, int ldx, const Tin* Y, int ldy, double* G, int ldg,
+                           const TcScratch& sc, int maxdim, cudaStream_t s) {
+  constexpr int NS = sizeof(Tin) == 8 ? NSLICE : 4;
   if (a == 0 || b == 0) return;
   const bool sym = a == b && X == Y && ldx == ldy;
   CARE_REQUIRE(sc.ok() && a + (sym ? 0 : b) <= std::max(maxdim, 64), CARE_ERR_WORKSPACE, "tc_gram: scratch");
@@ -769,48 +804,60 @@ void tc_gram_f64(long n, int a, int b, const double* X, int ldx, const double* Y
     const long kl = std::min<long>(SLAB, n - r0);
     const long ldk = round_up(kl, 64);
     uint16_t* sA = sc.slices;
-    uint16_t* sB = sym ? sA : sc.slices + (size_t)NSLICE * a * ldk;
+    uint16_t* sB = sym ? sA : sc.slices + (size_t)NS * a * ldk;
     // exponents and slices of the slab
     CARE_CUDA(cudaMemsetAsync(eA, 0x80, sizeof(int) * (size_t)(sym ? a : a + b), s));
     {
       dim3 blk(32, 8);
       const unsigned gy = (unsigned)std::min<long>((kl + 63) / 64, 64);
-      k_tc_colexp<<<dim3((a + 31) / 32, gy), blk, 0, s>>>(kl, a, X + r0 * ldx, ldx, eA);
+      k_tc_colexp<Tin><<<dim3((a + 31) / 32, gy), blk, 0, s>>>(kl, a, X + r0 * ldx, ldx, eA);
       CARE_LAUNCH();
       if (!sym) {
-        k_tc_colexp<<<dim3((b + 31) / 32, gy), blk, 0, s>>>(kl, b, Y + r0 * ldy, ldy, eB);
+        k_tc_colexp<Tin><<<dim3((b + 31) / 32, gy), blk, 0, s>>>(kl, b, Y + r0 * ldy, ldy, eB);
         CARE_LAUNCH();
       }
       k_tc_fix_exp<<<8, 256, 0, s>>>(sym ? a : a + b, eA);
       CARE_LAUNCH();
-      k_tc_slice_T<<<dim3((a + 31) / 32, (unsigned)((kl + 63) / 64)), blk, 0, s>>>(kl, a, X + r0 * ldx, ldx, eA,
-                                                                                   sA, ldk, (long)a * ldk);
+      k_tc_slice_T<Tin, NS><<<dim3((a + 31) / 32, (unsigned)((kl + 63) / 64)), blk, 0, s>>>(
+          kl, a, X + r0 * ldx, ldx, eA, sA, ldk, (long)a * ldk);
       CARE_LAUNCH();
       if (!sym) {
-        k_tc_slice_T<<<dim3((b + 31) / 32, (unsigned)((kl + 63) / 64)), blk, 0, s>>>(kl, b, Y + r0 * ldy, ldy,
-                                                                                     eB, sB, ldk, (long)b * ldk);
+        k_tc_slice_T<Tin, NS><<<dim3((b + 31) / 32, (unsigned)((kl + 63) / 64)), blk, 0, s>>>(
+            kl, b, Y + r0 * ldy, ldy, eB, sB, ldk, (long)b * ldk);
         CARE_LAUNCH();
       }
     }
     CUtensorMap mA, mB;
-    make_map(&mA, false, sA, kl, a, NSLICE, ldk, BM);
-    make_map(&mB, false, sB, kl, b, NSLICE, ldk, BN);
+    make_map(&mA, false, sA, kl, a, NS, ldk, BM);
+    make_map(&mB, false, sB, kl, b, NS, ldk, BN);
     const int splits = choose_splits(kl, live, (long)a * b, sc.part_elems);
     const long kps = round_up((kl + splits - 1) / splits, CHUNK);
     const int spl = (int)((kl + kps - 1) / kps);
     TcArgs g{};
     g.M = a; g.N = b; g.k_len = (int)kl; g.k_per_split = (int)kps; g.tiles_m = tiles_m; g.sym = sym ? 1 : 0;
     g.out_mode = 0; g.part = sc.part; g.ea = eA; g.eb = eB; g.err = sc.err;
-    launch_tc<0>(mA, mB, g, tiles_m * tiles_n, spl, s);
+    if constexpr (NS == NSLICE) launch_tc<0>(mA, mB, g, tiles_m * tiles_n, spl, s);
+    else launch_tc<3>(mA, mB, g, tiles_m * tiles_n, spl, s);
     const int rg = (int)std::min<long>(((long)a * b + 255) / 256, device_sms() * 8L);
     k_tc_reduce<<<rg, 256, 0, s>>>(a, b, spl, sc.part, G, ldg, sym ? 1 : 0, r0 > 0 ? 1 : 0);
     CARE_LAUNCH();
   }
 }
 
-template <class To>
-void tc_gemm_ts_f64(long n, int a, int b, double alpha, const double* X, int ldx, const double* S, int lds,
-                    double beta, To* Y, int ldy, const TcScratch& sc, int maxdim, cudaStream_t s) {
+void tc_gram_f64(long n, int a, int b, const double* X, int ldx, const double* Y, int ldy, double* G, int ldg,
+                 const TcScratch& sc, int maxdim, cudaStream_t s) {
+  tc_gram_sliced<double>(n, a, b, X, ldx, Y, ldy, G, ldg, sc, maxdim, s);
+}
+void tc_gram_f32acc(long n, int a, int b, const float* X, int ldx, const float* Y, int ldy, double* G, int ldg,
+                    const TcScratch& sc, int maxdim, cudaStream_t s) {
+  tc_gram_sliced<float>(n, a, b, X, ldx, Y, ldy, G, ldg, sc, maxdim, s);
+}
+
+// Y = alpha X S + beta Y, X of type Tin (8 slices for FP64, 4 for FP32), S FP64
+template <class Tin, class To>
+void tc_gemm_ts_sliced(long n, int a, int b, double alpha, const Tin* X, int ldx, const double* S, int lds,
+                       double beta, To* Y, int ldy, const TcScratch& sc, int maxdim, cudaStream_t s) {
+  constexpr int NS = sizeof(Tin) == 8 ? NSLICE : 4;
   if (n == 0 || b == 0) return;
   CARE_REQUIRE(a > 0, CARE_ERR_INVALID_ARG, "tc_gemm_ts: a == 0");
   CARE_REQUIRE(sc.ok() && a + b <= std::max(maxdim, 64), CARE_ERR_WORKSPACE, "tc_gemm_ts: scratch");
@@ -820,18 +867,19 @@ void tc_gemm_ts_f64(long n, int a, int b, double alpha, const double* X, int ldx
   int* eB = sc.expo + SLAB;
   CARE_CUDA(cudaMemsetAsync(eB, 0x80, sizeof(int) * (size_t)b, s));
   dim3 blk(32, 8);
-  k_tc_colexp<<<dim3((b + 31) / 32, (unsigned)std::min<long>((a + 63) / 64, 64)), blk, 0, s>>>(a, b, S, lds, eB);
+  k_tc_colexp<double><<<dim3((b + 31) / 32, (unsigned)std::min<long>((a + 63) / 64, 64)), blk, 0, s>>>(a, b, S, lds,
+                                                                                                     eB);
   CARE_LAUNCH();
   k_tc_fix_exp<<<8, 256, 0, s>>>(b, eB);
   CARE_LAUNCH();
-  k_tc_slice_T<<<dim3((b + 31) / 32, (unsigned)((a + 63) / 64)), blk, 0, s>>>(a, b, S, lds, eB, sB, ldk,
-                                                                               (long)b * ldk);
+  k_tc_slice_T<double, NS><<<dim3((b + 31) / 32, (unsigned)((a + 63) / 64)), blk, 0, s>>>(a, b, S, lds, eB, sB, ldk,
+                                                                                          (long)b * ldk);
   CARE_LAUNCH();
   CUtensorMap mB;
-  make_map(&mB, false, sB, a, b, NSLICE, ldk, BN);
-  uint16_t* sA = sc.slices + (size_t)NSLICE * b * ldk;
-  const size_t room = sc.slice_bytes / 2 - (size_t)NSLICE * b * ldk;
-  long slab = (long)(room / ((size_t)NSLICE * ldk));
+  make_map(&mB, false, sB, a, b, NS, ldk, BN);
+  uint16_t* sA = sc.slices + (size_t)NS * b * ldk;
+  const size_t room = sc.slice_bytes / 2 - (size_t)NS * b * ldk;
+  long slab = (long)(room / ((size_t)NS * ldk));
   slab = std::min<long>(slab, SLAB) / BM * BM;
   CARE_REQUIRE(slab >= BM, CARE_ERR_WORKSPACE, "tc_gemm_ts: scratch too small");
   int* eA = sc.expo;
@@ -839,22 +887,38 @@ void tc_gemm_ts_f64(long n, int a, int b, double alpha, const double* X, int ldx
   for (long r0 = 0; r0 < n; r0 += slab) {
     const long rows = std::min(slab, n - r0);
     const int wg = (int)std::min<long>((rows + 7) / 8, device_sms() * 16L);
-    k_tc_slice_N<<<wg, 256, 0, s>>>(rows, a, X + r0 * ldx, ldx, eA, sA, ldk, rows * ldk);
+    k_tc_slice_N<Tin, NS><<<wg, 256, 0, s>>>(rows, a, X + r0 * ldx, ldx, eA, sA, ldk, rows * ldk);
     CARE_LAUNCH();
     CUtensorMap mA;
-    make_map(&mA, false, sA, a, rows, NSLICE, ldk, BM);
+    make_map(&mA, false, sA, a, rows, NS, ldk, BM);
     const int tiles_m = (int)((rows + BM - 1) / BM);
     TcArgs g{};
     g.M = (int)rows; g.N = b; g.k_len = a; g.k_per_split = (int)round_up(a, CHUNK); g.tiles_m = tiles_m;
     g.sym = 0; g.out_mode = 1; g.ea = eA; g.eb = eB; g.Y = Y + r0 * ldy; g.ldy = ldy;
     g.y_f32 = sizeof(To) == 4 ? 1 : 0; g.alpha = alpha; g.beta = beta; g.err = sc.err;
-    launch_tc<0>(mA, mB, g, tiles_m * tiles_n, 1, s);
+    if constexpr (NS == NSLICE) launch_tc<0>(mA, mB, g, tiles_m * tiles_n, 1, s);
+    else launch_tc<3>(mA, mB, g, tiles_m * tiles_n, 1, s);
   }
+}
+
+template <class To>
+void tc_gemm_ts_f64(long n, int a, int b, double alpha, const double* X, int ldx, const double* S, int lds,
+                    double beta, To* Y, int ldy, const TcScratch& sc, int maxdim, cudaStream_t s) {
+  tc_gemm_ts_sliced<double, To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, sc, maxdim, s);
 }
 template void tc_gemm_ts_f64<double>(long, int, int, double, const double*, int, const double*, int, double,
                                      double*, int, const TcScratch&, int, cudaStream_t);
 template void tc_gemm_ts_f64<float>(long, int, int, double, const double*, int, const double*, int, double,
                                     float*, int, const TcScratch&, int, cudaStream_t);
+template <class To>
+void tc_gemm_ts_f32acc(long n, int a, int b, double alpha, const float* X, int ldx, const double* S, int lds,
+                       double beta, To* Y, int ldy, const TcScratch& sc, int maxdim, cudaStream_t s) {
+  tc_gemm_ts_sliced<float, To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, sc, maxdim, s);
+}
+template void tc_gemm_ts_f32acc<float>(long, int, int, double, const float*, int, const double*, int, double, float*,
+                                       int, const TcScratch&, int, cudaStream_t);
+template void tc_gemm_ts_f32acc<double>(long, int, int, double, const float*, int, const double*, int, double,
+                                        double*, int, const TcScratch&, int, cudaStream_t);
 
 void tc_gram_lowp(int kind, long n, int a, int b, const float* X, int ldx, const float* Y, int ldy, double* G,
                   int ldg, const TcScratch& sc, int maxdim, cudaStream_t s) {

@@ -50,11 +50,18 @@ struct KrylovWork {
   double* partial = nullptr;
   double* out = nullptr;
   int n = 0;
+  // restarted GMRES (allocated when gm_restart > 0): restart + 1 basis blocks,
+  // the preconditioned block, per-column Hessenberg / Givens state, dot scratch
+  int gm_restart = 0;
+  T *GV = nullptr, *GZ = nullptr;
+  double *GS = nullptr, *GH = nullptr, *GP = nullptr;
+  // exact ILU(0): ready flags per row, the row ticket, the error word
+  int *iflags = nullptr, *iticket = nullptr, *ierr = nullptr;
 };
 // nnz_ilu >= 0 also allocates the ILU(0) preconditioner for an operator with
 // that many entries (jacobi must then be true: the factor uses Ph / Sh / Dinv).
 template <class T>
-KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi, long nnz_ilu = -1);
+KrylovWork<T> krylov_alloc(Arena& ar, int n, bool jacobi, long nnz_ilu = -1, int gmres_restart = 0);
 
 struct KrylovResult {
   int iters = 0;
@@ -71,6 +78,20 @@ template <class T>
 KrylovResult krylov_bicgstab(const OpT<T>& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol,
                              int ld_sol, int cols, double tol, int maxit, int precond,
                              KrylovWork<T>& w, cudaStream_t s);
+
+// Restarted GMRES(restart) on the same systems, one Krylov space per column
+// (complex columns in complex arithmetic), right-preconditioned (precond as above)
+// so that the stopping test is on the true residual: per-column relative residual
+// <= tol; maxit caps the Arnoldi steps (matrix products) of each column.  Classical
+// Gram-Schmidt with reorthogonalisation, Givens rotations on the Hessenberg matrix.
+template <class T>
+KrylovResult krylov_gmres(const OpT<T>& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol, int ld_sol,
+                          int cols, double tol, int maxit, int precond, KrylovWork<T>& w, cudaStream_t s);
+
+// The ILU(0) factor of M_p (fixed-point sweeps, or exact) copied into F (values on
+// the pattern of A^T; complex interleaved when cplx).  Synchronises s.
+template <class T>
+void ilu0_factor(const OpT<T>& op, cd sigma, bool cplx, bool exact, KrylovWork<T>& w, T* F, cudaStream_t s);
 
 // Y = (A^T + sigma I) X on `cols` real columns (any width; complex when cplx).
 template <class T>

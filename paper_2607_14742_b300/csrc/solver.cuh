@@ -23,6 +23,8 @@ struct Ctx {
   size_t dG_cap = 0;
   double* gw = nullptr;  // Gram split-K scratch
   size_t gw_cap = 0;
+  double* dsm = nullptr;  // device scratch of the small dense algebra (Algorithms 1-2)
+  size_t dsm_cap = 0;
   long long krylov_iters = 0, spmm_calls = 0;
   double ms_gram = 0.0, ms_host = 0.0;  // Gram kernels (synchronised) and host small-dense time
   // device time (CUDA events on s) and algorithmic GFLOP of the Gram products,
@@ -49,8 +51,10 @@ struct Ctx {
   bool tc_used = false;
   int lowp = 0;  // low-precision tensor-core Grams of the shift generation: 0 off, 1 TF32, 2 BF16
   long long lowp_calls = 0;
-  double tc_ms = 0.0, tc_gflop = 0.0;  // device time and FP64-equivalent GFLOP of the sliced products
-  long long tc_calls = 0;
+  // device time and algorithmic GFLOP of the sliced tensor-core products, [0] FP64
+  // operands (8 slices), [1] FP32 operands (4 slices)
+  double tc_ms[2] = {0.0, 0.0}, tc_gflop[2] = {0.0, 0.0};
+  long long tc_calls[2] = {0, 0};
   // device time (CUDA events around each block Krylov solve) and its algorithmic bytes
   double kry_ms = 0.0, kry_gbyte = 0.0;
   cudaEvent_t ke0 = nullptr, ke1 = nullptr;
@@ -80,10 +84,10 @@ inline void harvest_timings(Ctx& c) {
     CARE_CUDA(cudaEventSynchronize(t.e1));
     float ms = 0.f;
     CARE_CUDA(cudaEventElapsedTime(&ms, t.e0, t.e1));
-    if (t.k == 2) {
-      c.tc_ms += ms;
-      c.tc_gflop += t.gflop;
-      c.tc_calls += 1;
+    if (t.k >= 2) {
+      c.tc_ms[t.k - 2] += ms;
+      c.tc_gflop[t.k - 2] += t.gflop;
+      c.tc_calls[t.k - 2] += 1;
     } else {
       c.gemm_ms[t.k] += ms;
       c.gemm_gflop[t.k] += t.gflop;
@@ -118,8 +122,8 @@ inline bool tc_use(const Ctx& c, long k, int a, int b, int dims) {
 }
 
 // gemm_ts on c.s (Y = alpha X S + beta Y), timed with CUDA events on the same stream;
-// [0] FP64 inputs on the CUDA cores, [1] FP32 inputs, [2] FP64 inputs on the tensor
-// cores (sliced); algorithmic GFLOP 2 n a b
+// [0] FP64 / [1] FP32 inputs on the CUDA cores, [2] FP64 / [3] FP32 inputs on the
+// tensor cores (sliced); algorithmic GFLOP 2 n a b
 template <class Ti, class To>
 inline void gemm_c(Ctx& c, long n, int a, int b, double alpha, const Ti* X, int ldx, const double* S, int lds,
                    double beta, To* Y, int ldy) {
@@ -131,11 +135,13 @@ inline void gemm_c(Ctx& c, long n, int a, int b, double alpha, const Ti* X, int 
   cudaEvent_t e0 = timing_event(c), e1 = timing_event(c);
   CARE_CUDA(cudaEventRecord(e0, c.s));
   int k = sizeof(Ti) == 8 ? 0 : 1;
-  if (sizeof(Ti) == 8 && tc_use(c, n, a, b, a + b)) {
-    tc_gemm_ts_f64<To>(n, a, b, alpha, reinterpret_cast<const double*>(X), ldx, S, lds, beta, Y, ldy, c.tc,
-                       c.tc_maxdim, c.s);
+  if (tc_use(c, n, a, b, a + b)) {
+    if constexpr (sizeof(Ti) == 8)
+      tc_gemm_ts_f64<To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, c.tc, c.tc_maxdim, c.s);
+    else
+      tc_gemm_ts_f32acc<To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, c.tc, c.tc_maxdim, c.s);
     c.tc_used = true;
-    k = 2;
+    k = sizeof(Ti) == 8 ? 2 : 3;
   } else {
     gemm_ts<Ti, To>(n, a, b, alpha, X, ldx, S, lds, beta, Y, ldy, c.s);
   }
@@ -191,6 +197,10 @@ struct Inner {
   T *Q = nullptr, *FQ = nullptr, *Qt = nullptr;                  // n x hcap (ldq)
   int ldm = 0, ldw = 0, ldr = 0, ldz = 0, ldq = 0;
   bool jacobi = false;
+  // optional FP64 blocks (n x f64cap, ld f64ld) for the joint compression of the
+  // +/- factors when their capacity is reached (set by sessions that have them)
+  double *f64a = nullptr, *f64b = nullptr;
+  int f64ld = 0, f64cap = 0;
   void alloc(Ctx& c, int n_, int m_, int bcap_, int adicap_, int hcap_);
 };
 
@@ -233,5 +243,30 @@ template <class T>
 void smw_solve_public(Ctx& c, Inner<T>& in, double p_re, double p_im, int b, bool hasK);
 
 double now_ms();
+
+// ---- device small dense algebra (Algorithms 1-2, factor compression) -------------
+// A bump allocator over the context's device scratch for the small matrices (the
+// products H = T M T^T and P = Gamma N Gamma^T, their eigendecompositions and the
+// coefficient blocks); a fresh one per algorithm step.
+struct DevSmall {
+  double* base = nullptr;
+  size_t cap = 0, off = 0;
+  double* get(size_t n) {
+    n = (n + 31) / 32 * 32;
+    CARE_REQUIRE(off + n <= cap, CARE_ERR_WORKSPACE, "small dense device scratch too small");
+    double* p = base + off;
+    off += n;
+    return p;
+  }
+};
+double* to_dev(Ctx& c, DevSmall& ds, const std::vector<double>& h);
+// symmetric M = L R^T (rt x rt) of the row-major factors L (rt x k) and Rt = R^T
+// (k x rt), on the device (tensor cores where profitable)
+double* dev_small_product(Ctx& c, DevSmall& ds, int rt, int k, const std::vector<double>& L,
+                          const std::vector<double>& Rt);
+// S[i][col] = V[q[col]][i] * sc[col] (i < rows): eigenvectors (rows of V, ldv)
+// gathered and scaled into the columns of the row-major block S (ld = cols)
+void eig_coeffs(Ctx& c, DevSmall& ds, int rows, int cols, const double* V, int ldv, const std::vector<int>& q,
+                const std::vector<double>& sc, double* S);
 
 }  // namespace care

@@ -79,6 +79,15 @@ template <class To>
 void tc_gemm_ts_f64(long n, int a, int b, double alpha, const double* X, int ldx, const double* S, int lds,
                     double beta, To* Y, int ldy, const TcScratch& sc, int maxdim, cudaStream_t s);
 
+// FP32-accurate counterparts for FP32 operands: 4 slices (28-bit fixed point per
+// row), the 10 pairs with a + b <= 3, all accumulated exactly (the dropped pairs
+// are below 2^-28 of the leading term, under the FP32 unit roundoff).
+void tc_gram_f32acc(long n, int a, int b, const float* X, int ldx, const float* Y, int ldy, double* G, int ldg,
+                    const TcScratch& sc, int maxdim, cudaStream_t s);
+template <class To>
+void tc_gemm_ts_f32acc(long n, int a, int b, double alpha, const float* X, int ldx, const double* S, int lds,
+                       double beta, To* Y, int ldy, const TcScratch& sc, int maxdim, cudaStream_t s);
+
 // G (a x b, FP64, ldg) = X^T Y for FP32 X, Y (row-major) with TF32 (kind = 1)
 // or BF16 (kind = 2) inputs and FP32 accumulation on the tensor cores.
 void tc_gram_lowp(int kind, long n, int a, int b, const float* X, int ldx, const float* Y, int ldy, double* G,

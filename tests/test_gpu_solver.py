@@ -140,3 +140,15 @@ def test_care_solve_eigen_aligned_3d_full_size(pb):
     Zx = pr.meta["V"] * np.sqrt(x)
     assert info["status"] == "CARE_OK", info
     assert od.lowrank_diff_fro(Z, Zx) <= 1e-8 * od.lowrank_fro(Zx)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_care_solve_small_fdm_gmres(pb, small, prec):
+    """The n = 400 case with restarted GMRES + ILU(0) shifted solves (the paper's
+    Section 5.2 solver): residual <= 1e-12 and the dense Newton X* to 1e-8."""
+    prob, A, X = small
+    o = pb.default_options(krylov=pb.KRYLOV_GMRES)
+    Z, info = pb.care_solve(dcsr(pb, prob), prob.B, prob.C, tol=1e-12, prec=prec, r_cap=256, opts=o)
+    Z = Z.cpu().numpy()
+    assert info["status"] == "CARE_OK", info
+    assert np.linalg.norm(Z @ Z.T - X) <= 1e-8 * np.linalg.norm(X)

@@ -147,7 +147,7 @@ def test_care_solve_with_every_fp64_product_on_tensor_cores(pb, prec):
     finally:
         pb.set_tensor_cores(1)
     assert info["status"] == "CARE_OK", info
-    assert info["tc_calls"] > 0
+    assert info["tc_calls"][0] > 0
     Z = Z.cpu().numpy()
     assert np.linalg.norm(Z @ Z.T - X) <= 1e-8 * np.linalg.norm(X)
     R = od.riccati_residual(prob.A.to_dense(), prob.B, prob.C, Z @ Z.T)
@@ -167,3 +167,45 @@ def test_care_solve_lowp_shift_grams(pb, prec):
     assert info["lowp_gram_calls"] > 0
     Z = Z.cpu().numpy()
     assert np.linalg.norm(Z @ Z.T - X) <= 1e-8 * np.linalg.norm(X)
+
+
+@pytest.mark.parametrize("n,a,b,sym", [(4000, 96, 80, False), (40000, 130, 130, True)])
+def test_gram_f32acc_exact_on_integers_and_bound(pb, n, a, b, sym):
+    """FP32 operands, four slices (28-bit fixed point), all ten pairs exact: integer
+    entries of up to 11 bits give the exact product; random data stays within the
+    input-rounding bound 2^-29 relative to each column's power-of-two scale plus the
+    dropped pairs (< 2^-28 M_i M_j per term)."""
+    rng = np.random.default_rng(n + 3)
+    Xi = rng.integers(-1024, 1025, size=(n, a)).astype(np.float32)
+    Yi = Xi if sym else rng.integers(-1024, 1025, size=(n, b)).astype(np.float32)
+    exact = (Xi.astype(np.int64).T @ Yi.astype(np.int64)).astype(np.float64)
+    Xd = _dev(Xi, torch.float32)
+    G = pb.gram_tc(Xd, Xd if sym else _dev(Yi, torch.float32), "f32").cpu().numpy()
+    assert np.array_equal(G, exact)
+    X = (rng.standard_normal((n, a)) * np.logspace(0, -2, a)[None, :]).astype(np.float32)
+    Y = X if sym else rng.standard_normal((n, b)).astype(np.float32)
+    Xd = _dev(X, torch.float32)
+    G = pb.gram_tc(Xd, Xd if sym else _dev(Y, torch.float32), "f32").cpu().numpy()
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    ref = X64.T @ Y64
+    Mx = 2.0 ** np.ceil(np.log2(np.abs(X64).max(axis=0)))
+    My = 2.0 ** np.ceil(np.log2(np.abs(Y64).max(axis=0)))
+    bound = (2.0 ** -28 * (Mx[:, None] * np.abs(Y64).sum(0)[None, :] + np.abs(X64).sum(0)[:, None] * My[None, :]) +
+             n * 2.0 ** -27 * Mx[:, None] * My[None, :] + 4 * U64 * np.abs(ref))
+    assert np.all(np.abs(G - ref) <= bound)
+
+
+def test_gemm_ts_f32acc(pb):
+    rng = np.random.default_rng(11)
+    n, a, b = 50000, 300, 96
+    X = rng.standard_normal((n, a)).astype(np.float32)
+    S = rng.standard_normal((a, b))
+    Y0 = rng.standard_normal((n, b)).astype(np.float32)
+    out = pb.gemm_ts(_dev(X, torch.float32), _dev(S), 0.5, -1.0, _dev(Y0, torch.float32), tc=True).cpu().numpy()
+    X64 = X.astype(np.float64)
+    ref = 0.5 * (X64 @ S) - Y0.astype(np.float64)
+    Mx = 2.0 ** np.ceil(np.log2(np.abs(X64).max(axis=1)))
+    Ms = 2.0 ** np.ceil(np.log2(np.abs(S).max(axis=0)))
+    bound = 0.5 * (2.0 ** -28 * (Mx[:, None] * np.abs(S).sum(0)[None, :] + np.abs(X64).sum(1)[:, None] * Ms[None, :])
+                   + a * 2.0 ** -27 * Mx[:, None] * Ms[None, :]) + 2.0 ** -23 * (np.abs(ref) + np.abs(Y0))
+    assert np.all(np.abs(out - ref) <= bound)
