@@ -246,9 +246,12 @@ care_status care_gram(int dtype, int n, int a, int b, const void* X, int ldx, co
  *  - a * b must not exceed CARE_GRAM_NOALLOC_SCRATCH_DOUBLES, else
  *    CARE_ERR_INVALID_ARG; long row ranges are handled with fewer, longer
  *    row slices, so results may differ from care_gram in the last bits.
- *  - The first call on a device looks up the scratch's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The 8 MiB are reserved by the CUDA driver when it loads the library's
+ *    device code on a device.  Under lazy module loading (the CUDA default)
+ *    that happens on the first call into the library on that device, which
+ *    also looks up the scratch's device address (cudaGetSymbolAddress).  So
+ *    make one warm-up call (any shape) at start-up, with the device current,
+ *    before the allocation-free phase and before any stream capture.
  *  - All calls share the one scratch array and it keeps the last call's
  *    contents; every entry a call reads is written by that call first.  Calls
  *    that overlap on the GPU (different streams, or different host threads

@@ -387,8 +387,9 @@ template void scale_cols<double>(long, int, double*, int, const double*, cudaStr
 
 // ------------------------------------------------- allocation-free Gram ----
 // Scratch for care_gram_noalloc: a fixed file-scope device array, so the entry
-// point never allocates.  Every device that loads the library holds it until
-// the process exits.  Host code must not pass the symbol itself to a kernel
+// point never allocates.  The driver reserves it when it loads this module on a
+// device (with lazy loading: at the first call into the library there), and
+// that device holds it until the process exits.  Host code must not pass the symbol itself to a kernel
 // (in host code it names a host-side stand-in); its device address is looked
 // up once per device with cudaGetSymbolAddress.
 static __device__ __align__(256) double g_gram_noalloc_scratch[CARE_GRAM_NOALLOC_SCRATCH_DOUBLES];

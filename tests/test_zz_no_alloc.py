@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import care_inputs as ci
+from oracle.lowrank import gram as oracle_gram
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,26 @@ def test_gram_noalloc_scratch_reuse_across_shapes(pb):
     for _ in range(2):
         assert np.allclose(pb.gram_noalloc(Xa, Xa).cpu().numpy(), ga, rtol=1e-12, atol=1e-9)
         assert np.allclose(pb.gram_noalloc(Xb, Xb).cpu().numpy(), gb, rtol=1e-12, atol=1e-12)
+
+
+def test_gram_noalloc_nonsymmetric_after_symmetric(pb):
+    """A product X^T Y right after X^T X of the same shape: the symmetric call wrote
+    only the upper tiles of the scratch, so the general call must not read any
+    lower tile it left behind.  Checked against the oracle's FP64 product."""
+    n, a = 30000, 96
+    Xh = ci.random_block(n, a, 75)
+    Yh = ci.random_block(n, a, 76)
+    X = torch.tensor(Xh, device="cuda")
+    Y = torch.tensor(Yh, device="cuda")
+    bound = (n + 2) * U64 * (np.abs(Xh).T @ np.abs(Yh))
+    ref_xy = oracle_gram(Xh, Yh)
+    ref_xx = oracle_gram(Xh, Xh)
+    for _ in range(2):
+        Gs = pb.gram_noalloc(X, X).cpu().numpy()
+        assert np.array_equal(Gs, Gs.T)
+        assert np.all(np.abs(Gs - ref_xx) <= (n + 2) * U64 * (np.abs(Xh).T @ np.abs(Xh)))
+        G = pb.gram_noalloc(X, Y).cpu().numpy()
+        assert np.all(np.abs(G - ref_xy) <= bound)
 
 
 def test_gram_noalloc_rejects_oversized_output(pb):
