@@ -73,11 +73,17 @@ typedef enum {
                             /* stays FP32 / FP64                                         */
 } care_prec;
 
-/* Block Krylov method of the shifted solves (one Krylov space per right-hand-side
- * column): BiCGStab (default), or restarted GMRES with right preconditioning,
- * the method of the paper's GPU experiments (Section 5.2), restart
- * gmres_restart_lo / _hi for FP32 / FP64 solves. */
-typedef enum { CARE_KRYLOV_BICGSTAB = 0, CARE_KRYLOV_GMRES = 1 } care_krylov;
+/* Method of the shifted solves.  Block Krylov (one Krylov space per right-hand-
+ * side column): BiCGStab (default), or restarted GMRES with right
+ * preconditioning, the method of the paper's GPU experiments (Section 5.2),
+ * restart gmres_restart_lo / _hi for FP32 / FP64 solves.  Or dense direct:
+ * M_p = (A + p I)^T formed densely and factored by LU with partial pivoting in
+ * the solve's precision for every shift (the solvers of the stability study,
+ * Section 5.1, and Section 4's dense-direct cost class); for n <=
+ * CARE_DENSE_LU_MAX_N, with 2 n^2 values of the inner precision added to the
+ * workspace. */
+typedef enum { CARE_KRYLOV_BICGSTAB = 0, CARE_KRYLOV_GMRES = 1, CARE_KRYLOV_DENSE_LU = 2 } care_krylov;
+#define CARE_DENSE_LU_MAX_N 8192
 /* Preconditioner of the shifted solves (right preconditioning): Jacobi, ILU(0) by
  * three fixed-point sweeps with Jacobi-swept triangular solves (Chow & Patel; the
  * default, row-parallel), or ILU(0) computed exactly with exact triangular solves
@@ -277,19 +283,28 @@ care_status care_shifted_solve(const care_op* op, const double* B, int ldb, cons
                                care_prec prec, const care_opts* opts, double* V, int ldv,
                                void* work, size_t work_bytes, care_stream_t s, int* iters);
 
-/* Autotuner for the shifted solves (no paper counterpart).  Times SMW + block
- * Krylov solves of a b-column right-hand side (deterministic pseudo-random
- * entries) at a mid-spectrum shift p = -0.05 max|a_ii| over the candidate
- * configurations  krylov_chunk in {16, 32, 64} columns, tri_sweeps in {1, 2, 3}
- * (ILU(0) triangular Jacobi sweeps), precond in {ILU0, NONE}, and 4 or 8 CTAs
- * per SM for the row-block kernels; keeps the fastest configuration whose
- * solve converged.  On return opts->krylov_chunk, tri_sweeps and precond hold
- * the choice, the CTAs-per-SM choice is applied process-wide, and *best_ms
- * (host, may be NULL) the best time.  work: device scratch of
+/* Autotuner for the shifted solves (no paper counterpart), in two stages on the
+ * operator at a mid-spectrum shift p = -0.05 max|a_ii|:
+ *  1. SpMM thread shape: 16-byte vectors per thread in {1, 2, 4} (fewer threads
+ *     per row, more gathers in flight per thread) x {4, 8} CTAs per SM for the
+ *     row-block kernels, each timed on a b-column block in the working precision
+ *     (median of 5 launches); the fastest is applied process-wide.
+ *  2. Shifted solves (SMW + block Krylov) of a b-column right-hand side
+ *     (deterministic pseudo-random entries) with that shape over krylov in
+ *     {BiCGStab, GMRES}, precond in {ILU0 with tri_sweeps 1, 2, 3, ILU0_EXACT,
+ *     NONE} and krylov_chunk in {16, 32, 64}; keeps the fastest whose solve
+ *     converged.
+ * On return opts->krylov, precond, tri_sweeps and krylov_chunk hold the choice
+ * and *best_ms (host, may be NULL) its time.  work: device scratch of
  * care_autotune_workspace_size bytes.  Synchronises s. */
 care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_prec prec, size_t* bytes);
 care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_opts* opts, void* work,
                           size_t work_bytes, care_stream_t s, double* best_ms);
+/* The process-wide launch shape (autotuner stage 1): SpMM vectors per thread
+ * (1, 2 or 4) and CTAs per SM (1..8) of the row-block kernels.  set returns
+ * CARE_ERR_INVALID_ARG for other values; get always succeeds (returns 0). */
+int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm);
+care_status care_set_launch_shape(int spmm_vpt, int ctas_per_sm);
 
 /* ---- solver entry points ------------------------------------------------ */
 
@@ -337,6 +352,28 @@ care_status care_solve_batched(int count, const care_csr* const* A, const double
                                care_prec prec, const care_opts* opts, double* const* Z, const int* ldz,
                                const int* r_cap, int workers, void* work, size_t work_bytes, care_stream_t s,
                                care_info* info);
+
+/* Batched Framework 1, serving mode (no paper counterpart): `count` <= 256
+ * independent CAREs, each on its own host thread and CUDA stream with its own
+ * workspace slice, as care_solve_batched, except that the shifted solves of all
+ * instances (Section 4's dominant work) are gathered: when every instance still
+ * solving has a shifted solve pending (or after 2 ms), ONE persistent
+ * cooperative launch runs block BiCGStab (right Jacobi preconditioning) on all
+ * of them over a work list of row tiles of every instance, with per-column
+ * convergence and early exit.  opts->krylov and opts->precond are replaced by
+ * BiCGStab + Jacobi.  Results agree with
+ * care_solve to the solver tolerances, not bitwise (a different preconditioner
+ * and summation order).  batch_launches (host, may be NULL) receives the
+ * number of batched launches.  Other arguments as for care_solve_batched. */
+care_status care_workspace_size_batched_persistent(int count, const care_csr* const* A, const int* m, const int* p,
+                                                   const int* r_cap, care_prec prec, const care_opts* opts,
+                                                   size_t* bytes);
+care_status care_solve_batched_persistent(int count, const care_csr* const* A, const double* const* B,
+                                          const int* ldb, const int* m, const double* const* C, const int* ldc,
+                                          const int* p, double tol, care_prec prec, const care_opts* opts,
+                                          double* const* Z, const int* ldz, const int* r_cap, void* work,
+                                          size_t work_bytes, care_stream_t s, care_info* info,
+                                          long long* batch_launches);
 
 /* LR-ADI (Section 4) for  (A - B K^T)^T X + X (A - B K^T) + W W^T = 0,  X ~ Z Z^T.
  * B, K: FP64 column-major n x m (both NULL or m = 0: no feedback).  W: FP64

@@ -32,6 +32,8 @@ PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED_FP32, "mixed_fp32": PREC_MIXED_FP
         "mixed_bf16": PREC_MIXED_BF16}
 KRYLOV_BICGSTAB = 0
 KRYLOV_GMRES = 1
+KRYLOV_DENSE_LU = 2
+DENSE_LU_MAX_N = 8192
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_ILU0 = 2
@@ -116,11 +118,16 @@ def lib() -> ct.CDLL:
                                      vp, sz, vp]),
         "care_workspace_size_batched": (i, [i, vp, vp, vp, vp, i, P(opts_t), i, P(sz)]),
         "care_solve_batched": (i, [i, vp, vp, vp, vp, vp, vp, vp, d, i, P(opts_t), vp, vp, vp, i, vp, sz, vp, vp]),
+        "care_workspace_size_batched_persistent": (i, [i, vp, vp, vp, vp, i, P(opts_t), P(sz)]),
+        "care_solve_batched_persistent": (i, [i, vp, vp, vp, vp, vp, vp, vp, d, i, P(opts_t), vp, vp, vp, vp, sz,
+                                              vp, vp, P(ct.c_longlong)]),
         "care_autotune_workspace_size": (i, [P(op_t), i, i, i, P(sz)]),
         "care_autotune": (i, [P(op_t), i, i, i, P(opts_t), vp, sz, vp, P(d)]),
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_fp64_peak": (i, [P(d), vp]),
         "care_symeig_work_size": (sz, [i]),
+        "care_get_launch_shape": (i, [P(i), P(i)]),
+        "care_set_launch_shape": (i, [i, i]),
         "care_ilu0_work_size": (sz, [P(op_t), i]),
         "care_ilu0": (i, [P(op_t), i, i, d, d, vp, vp, sz, vp]),
         "care_symeig": (i, [i, vp, i, vp, vp, d, d, P(i), vp, sz, vp]),
@@ -280,9 +287,13 @@ def care_solve(A: CSR, B, C, tol=1e-10, prec="mixed", r_cap=512, opts=None, work
     return Zc[:inf.rank].t(), _info_dict(inf)
 
 
-def care_solve_batched(problems, tol=1e-10, prec="mixed", r_cap=256, opts=None, workers=4, allow=(0,)):
-    """Solve independent CAREs together (care_solve_batched).  problems: list of
-    (A: CSR, B, C).  Returns (list of Z, list of info dicts, status)."""
+def care_solve_batched(problems, tol=1e-10, prec="mixed", r_cap=256, opts=None, workers=4, allow=(0,),
+                       persistent=False, stats=None):
+    """Solve independent CAREs together.  problems: list of (A: CSR, B, C).
+    persistent=False: care_solve_batched (host workers, bitwise equal to single
+    solves); True: care_solve_batched_persistent (shifted solves of all instances
+    in shared persistent launches; stats["batch_launches"] receives their count).
+    Returns (list of Z, list of info dicts, status)."""
     L = lib()
     o = opts or default_options()
     pc = PREC[prec] if isinstance(prec, str) else prec
@@ -309,12 +320,24 @@ def care_solve_batched(problems, tol=1e-10, prec="mixed", r_cap=256, opts=None, 
         Zs.append(Zc)
         Zp[i], ldz[i] = Zc.data_ptr(), A.n
     need = ct.c_size_t(0)
-    _check(L.care_workspace_size_batched(cnt, Ap, ms, ps, rc, pc, ct.byref(o), workers, ct.byref(need)),
-           "care_workspace_size_batched")
+    if persistent:
+        _check(L.care_workspace_size_batched_persistent(cnt, Ap, ms, ps, rc, pc, ct.byref(o), ct.byref(need)),
+               "care_workspace_size_batched_persistent")
+    else:
+        _check(L.care_workspace_size_batched(cnt, Ap, ms, ps, rc, pc, ct.byref(o), workers, ct.byref(need)),
+               "care_workspace_size_batched")
     ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=dev)
     infos = (info_t * cnt)()
-    st = L.care_solve_batched(cnt, Ap, Bp, ldb, ms, Cp, ldc, ps, float(tol), pc, ct.byref(o), Zp, ldz, rc, workers,
-                              _ptr(ws), ws.numel(), _stream(), infos)
+    if persistent:
+        nl = ct.c_longlong(0)
+        st = L.care_solve_batched_persistent(cnt, Ap, Bp, ldb, ms, Cp, ldc, ps, float(tol), pc, ct.byref(o), Zp, ldz,
+                                             rc, _ptr(ws), ws.numel(), _stream(), infos, ct.byref(nl))
+        if stats is not None:
+            stats["batch_launches"] = nl.value
+            stats["workspace_bytes"] = need.value
+    else:
+        st = L.care_solve_batched(cnt, Ap, Bp, ldb, ms, Cp, ldc, ps, float(tol), pc, ct.byref(o), Zp, ldz, rc,
+                                  workers, _ptr(ws), ws.numel(), _stream(), infos)
     _check(st, "care_solve_batched", ok=tuple(allow) + (0,))
     out_info = [_info_dict(infos[i]) for i in range(cnt)]
     return [Zs[i][:infos[i].rank].t() for i in range(cnt)], out_info, st
@@ -448,6 +471,17 @@ def gram(X: torch.Tensor, Y: torch.Tensor):
 TC_MODES = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3}
 
 
+def launch_shape():
+    """(SpMM vectors per thread, CTAs per SM) of the row-block kernels."""
+    v, c = ct.c_int(0), ct.c_int(0)
+    lib().care_get_launch_shape(ct.byref(v), ct.byref(c))
+    return v.value, c.value
+
+
+def set_launch_shape(spmm_vpt: int, ctas_per_sm: int):
+    _check(lib().care_set_launch_shape(int(spmm_vpt), int(ctas_per_sm)), "care_set_launch_shape")
+
+
 def ilu0(op: Operator, shift, exact=True, dtype=torch.float64):
     """ILU(0) factor of (A + shift I)^T on A^T's pattern: a tensor of nnz values
     (complex for complex shifts) in the order of the prepared operator's rows."""
@@ -545,8 +579,9 @@ def gram_noalloc(X: torch.Tensor, Y: torch.Tensor, out: torch.Tensor | None = No
     return G
 
 
-def shifted_solve(op: Operator, W, shift, B=None, K=None, prec="fp64", opts=None):
-    """V = ((A - B K^T)^T + shift I)^{-1} W (SMW + block BiCGStab). Returns (V, iters)."""
+def shifted_solve(op: Operator, W, shift, B=None, K=None, prec="fp64", opts=None, with_status=False):
+    """V = ((A - B K^T)^T + shift I)^{-1} W (SMW + the shifted-solve method of opts).
+    Returns (V, iters), or (V, iters, status) with with_status (0 ok, 7 inner failure)."""
     L = lib()
     dev = op.A.val.device
     o = opts or default_options()
@@ -573,7 +608,7 @@ def shifted_solve(op: Operator, W, shift, B=None, K=None, prec="fp64", opts=None
     st = L.care_shifted_solve(ct.byref(op.op), _ptr(Bc), ldb, _ptr(Kc), ldk, m, s.real, s.imag, _ptr(Wc), ldw, b,
                               pc, ct.byref(o), _ptr(Vc), n, _ptr(ws), ws.numel(), _stream(), ct.byref(it))
     _check(st, "care_shifted_solve", ok=(0, 7))
-    return Vc.t(), it.value
+    return (Vc.t(), it.value, st) if with_status else (Vc.t(), it.value)
 
 
 def host_symeig(A):

@@ -367,7 +367,8 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
     const double e = eta_rel * lmx;
     return e > 0 ? (l >= e || l <= -e) : l != 0.0;
   };
-  std::vector<int> sel = dev_symeig_select(rt, H, rt, lam, Vd, kept_r, ework, ew, c.s);
+  // C+- only enter as factors weighted by |lambda|^(1/2): weighted clustering
+  std::vector<int> sel = dev_symeig_select(rt, H, rt, lam, Vd, kept_r, ework, ew, c.s, true);
   c.ms_host += now_ms() - th;
   c.host_syncs += 3;
   double ss = 0.0, lmax = 0.0;
@@ -1024,16 +1025,26 @@ __global__ void k_fill_hash(long count, double* x) {
   }
 }
 
+// autotuner scratch: right-hand side W (n x b FP64), solution V (n x b complex FP64),
+// the SpMM stage's blocks X, Y (n x (b + 2) FP64 each), then the solver workspace
+static size_t autotune_head_bytes(long n, int b) {
+  return (((size_t)n * b * 8 * 3 + (size_t)n * (b + 2) * 8 * 2) + 4095) & ~size_t(4095);
+}
+
 care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_prec prec, size_t* bytes) {
   if (!op || !bytes || b <= 0 || m < 0) return CARE_ERR_INVALID_ARG;
-  care_opts o;
-  care_opts_default(&o);
-  o.precond = CARE_PRECOND_ILU0;
   size_t s1 = 0;
-  care_status st = care_shifted_solve_workspace_size(op, std::max(m, 1), b, prec, &o, &s1);
-  if (st != CARE_OK) return st;
-  // + right-hand side (n x b FP64) + solution (n x b complex FP64)
-  *bytes = s1 + (size_t)op->n * b * 8 * 3 + 4096;
+  for (int kr = 0; kr < 2; ++kr) {
+    care_opts o;
+    care_opts_default(&o);
+    o.precond = CARE_PRECOND_ILU0_EXACT;  // the ILU workspace of both ILU(0) variants
+    o.krylov = kr == 0 ? CARE_KRYLOV_BICGSTAB : CARE_KRYLOV_GMRES;
+    size_t sk = 0;
+    care_status st = care_shifted_solve_workspace_size(op, std::max(m, 1), b, prec, &o, &sk);
+    if (st != CARE_OK) return st;
+    s1 = std::max(s1, sk);
+  }
+  *bytes = s1 + autotune_head_bytes(op->n, b) + 4096;
   return CARE_OK;
 }
 
@@ -1048,10 +1059,14 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   char* base = static_cast<char*>(work);
   double* W = reinterpret_cast<double*>(base);
   double* V = W + (size_t)n * b;
-  void* sw = base + (((size_t)n * b * 8 * 3 + 4095) & ~size_t(4095));
-  const size_t sw_bytes = work_bytes - (((size_t)n * b * 8 * 3 + 4095) & ~size_t(4095));
+  double* SX = V + (size_t)n * b * 2;
+  double* SY = SX + (size_t)n * (b + 2);
+  const size_t head = autotune_head_bytes(n, b);
+  void* sw = base + head;
+  const size_t sw_bytes = work_bytes - head;
   cudaStream_t cs = (cudaStream_t)s;
   k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * b, W);
+  k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * (b + 2), SX);
   if (cudaGetLastError() != cudaSuccess) return CARE_ERR_CUDA;
   // mid-spectrum shift from the largest diagonal magnitude
   std::vector<double> d(n);
@@ -1064,47 +1079,106 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int prev_ctas = tuned_ctas_per_sm();
-  double best = 1e300;
-  care_opts bestopt = *opts;
-  int best_ctas = prev_ctas;
-  const int chunks[3] = {16, 32, 64}, sweeps[3] = {1, 2, 3}, ctas[2] = {4, 8};
-  for (int ci = 0; ci < 2; ++ci)
-    for (int pc = 0; pc < 2; ++pc)
-      for (int ki = 0; ki < 3; ++ki)
-        for (int si = 0; si < (pc == 0 ? 3 : 1); ++si) {
-          care_opts o = *opts;
-          o.precond = pc == 0 ? CARE_PRECOND_ILU0 : CARE_PRECOND_NONE;
-          o.krylov_chunk = chunks[ki];
-          o.tri_sweeps = sweeps[si];
-          set_tuned_ctas_per_sm(ctas[ci]);
-          int iters = 0;
-          // one untimed run (graph capture, caches), one timed run
-          care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw, sw_bytes, s, &iters);
+  const int prev_ctas = tuned_ctas_per_sm(), prev_vpt = tuned_spmm_vpt();
+  // stage 1: SpMM thread shape (vectors per thread) and CTAs per SM, timed on the
+  // operator at the solve's width and working precision (median of 5 launches)
+  int best_vpt = prev_vpt, best_ctas = prev_ctas;
+  {
+    const bool f64 = prec == CARE_PREC_FP64;
+    const int ld = f64 ? (int)pad_ld<double>(b) : (int)pad_ld<float>(b);
+    double bst = 1e300;
+    const int vpts[3] = {1, 2, 4}, ctas[2] = {4, 8};
+    for (int ci = 0; ci < 2; ++ci)
+      for (int vi = 0; vi < 3; ++vi) {
+        set_tuned_ctas_per_sm(ctas[ci]);
+        set_tuned_spmm_vpt(vpts[vi]);
+        std::vector<float> ms;
+        bool ok = true;
+        for (int r = 0; r < 7 && ok; ++r) {
           cudaEventRecord(e0, cs);
-          care_status r = care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw,
-                                             sw_bytes, s, &iters);
+          const care_status q = run_guarded([&] {
+            if (f64) spmm<double>(op64(*op), cd{p, 0.0}, false, SX, ld, SY, ld, b, cs);
+            else spmm<float>(op32(*op), cd{p, 0.0}, false, reinterpret_cast<const float*>(SX), ld,
+                             reinterpret_cast<float*>(SY), ld, b, cs);
+            return CARE_OK;
+          });
           cudaEventRecord(e1, cs);
           cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (r == CARE_OK && ms < best) {
-            best = ms;
-            bestopt = o;
-            best_ctas = ctas[ci];
-          }
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ok = q == CARE_OK;
+          if (r >= 2) ms.push_back(t);  // two warm-up launches
         }
+        if (!ok) continue;
+        std::sort(ms.begin(), ms.end());
+        const double med = ms[ms.size() / 2];
+        if (med < bst) {
+          bst = med;
+          best_vpt = vpts[vi];
+          best_ctas = ctas[ci];
+        }
+      }
+    set_tuned_ctas_per_sm(best_ctas);
+    set_tuned_spmm_vpt(best_vpt);
+  }
+  // stage 2: shifted-solve configurations with that shape
+  double best = 1e300;
+  care_opts bestopt = *opts;
+  const int chunks[3] = {16, 32, 64};
+  struct Pc {
+    int precond, sweeps;
+  };
+  const Pc pcs[5] = {{CARE_PRECOND_ILU0, 1}, {CARE_PRECOND_ILU0, 2}, {CARE_PRECOND_ILU0, 3},
+                     {CARE_PRECOND_ILU0_EXACT, 1}, {CARE_PRECOND_NONE, 1}};
+  for (int kr = 0; kr < 2; ++kr)
+    for (int pc = 0; pc < 5; ++pc)
+      for (int ki = 0; ki < 3; ++ki) {
+        care_opts o = *opts;
+        o.krylov = kr == 0 ? CARE_KRYLOV_BICGSTAB : CARE_KRYLOV_GMRES;
+        o.precond = pcs[pc].precond;
+        o.tri_sweeps = pcs[pc].sweeps;
+        o.krylov_chunk = chunks[ki];
+        int iters = 0;
+        // one untimed run (graph capture, caches), one timed run
+        care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw, sw_bytes, s, &iters);
+        cudaEventRecord(e0, cs);
+        care_status r = care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw,
+                                           sw_bytes, s, &iters);
+        cudaEventRecord(e1, cs);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r == CARE_OK && ms < best) {
+          best = ms;
+          bestopt = o;
+        }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best >= 1e300) {
     set_tuned_ctas_per_sm(prev_ctas);
+    set_tuned_spmm_vpt(prev_vpt);
     return CARE_INNER_FAILED;
   }
+  opts->krylov = bestopt.krylov;
   opts->precond = bestopt.precond;
   opts->krylov_chunk = bestopt.krylov_chunk;
   opts->tri_sweeps = bestopt.tri_sweeps;
-  set_tuned_ctas_per_sm(best_ctas);
   if (best_ms) *best_ms = best;
+  return CARE_OK;
+}
+
+int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm) {
+  if (spmm_vpt) *spmm_vpt = tuned_spmm_vpt();
+  if (ctas_per_sm) *ctas_per_sm = tuned_ctas_per_sm();
+  return 0;
+}
+
+care_status care_set_launch_shape(int spmm_vpt, int ctas_per_sm) {
+  if ((spmm_vpt != 1 && spmm_vpt != 2 && spmm_vpt != 4) || ctas_per_sm < 1 || ctas_per_sm > 8)
+    return CARE_ERR_INVALID_ARG;
+  set_tuned_spmm_vpt(spmm_vpt);
+  set_tuned_ctas_per_sm(ctas_per_sm);
   return CARE_OK;
 }
 
@@ -1241,6 +1315,126 @@ care_status care_solve_batched(int count, const care_csr* const* A, const double
   }
   cudaEventDestroy(start_ev);
   if (!setup_ok) return CARE_ERR_CUDA;
+  if (info)
+    for (int i = 0; i < count; ++i) info[i] = infos[i];
+  for (int i = 0; i < count; ++i)
+    if (status[i] != CARE_OK) return status[i];
+  return CARE_OK;
+}
+
+// ---- batched serving mode: shifted solves of all instances in shared launches --
+static care_opts persistent_opts(const care_opts* opts) {
+  care_opts o;
+  if (opts) o = *opts;
+  else care_opts_default(&o);
+  o.krylov = CARE_KRYLOV_BICGSTAB;
+  o.precond = CARE_PRECOND_JACOBI;
+  return o;
+}
+
+care_status care_workspace_size_batched_persistent(int count, const care_csr* const* A, const int* m, const int* p,
+                                                   const int* r_cap, care_prec prec, const care_opts* opts,
+                                                   size_t* bytes) {
+  if (count < 0 || !bytes || (count > 0 && (!A || !m || !p || !r_cap))) return CARE_ERR_INVALID_ARG;
+  if (count > kBatchMaxReq) return CARE_ERR_INVALID_ARG;
+  const care_opts o = persistent_opts(opts);
+  size_t tot = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!A[i]) return CARE_ERR_INVALID_ARG;
+    const size_t b = solve_ws_bytes(A[i], m[i], p[i], r_cap[i], prec, &o);
+    if (b == 0) return CARE_ERR_INVALID_ARG;
+    tot += b;
+  }
+  size_t sb = 0;
+  const care_status st = run_guarded([&] {
+    sb = batch_scratch_bytes(std::max(count, 1));
+    return CARE_OK;
+  });
+  if (st != CARE_OK) return st;
+  *bytes = tot + ((sb + 4095) & ~size_t(4095));
+  return CARE_OK;
+}
+
+care_status care_solve_batched_persistent(int count, const care_csr* const* A, const double* const* B,
+                                          const int* ldb, const int* m, const double* const* C, const int* ldc,
+                                          const int* p, double tol, care_prec prec, const care_opts* opts,
+                                          double* const* Z, const int* ldz, const int* r_cap, void* work,
+                                          size_t work_bytes, care_stream_t s, care_info* info,
+                                          long long* batch_launches) {
+  if (count < 0 || count > kBatchMaxReq) return CARE_ERR_INVALID_ARG;
+  if (count == 0) return CARE_OK;
+  if (!A || !B || !ldb || !m || !C || !ldc || !p || !Z || !ldz || !r_cap || !work) return CARE_ERR_INVALID_ARG;
+  if (prec < CARE_PREC_FP64 || prec > CARE_PREC_MIXED_BF16) return CARE_ERR_INVALID_ARG;
+  size_t need = 0;
+  care_status st = care_workspace_size_batched_persistent(count, A, m, p, r_cap, prec, opts, &need);
+  if (st != CARE_OK) return st;
+  if (work_bytes < need) return CARE_ERR_WORKSPACE;
+  const care_opts o = persistent_opts(opts);
+  // per-instance slices of the workspace, then the launch scratch
+  std::vector<size_t> off(count + 1, 0);
+  for (int i = 0; i < count; ++i) off[i + 1] = off[i] + solve_ws_bytes(A[i], m[i], p[i], r_cap[i], prec, &o);
+  char* base = static_cast<char*>(work);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CARE_ERR_CUDA;
+  std::vector<care_status> status(count, CARE_OK);
+  std::vector<care_info> infos(count);
+  cudaEvent_t start_ev = nullptr;
+  if (cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming) != cudaSuccess) return CARE_ERR_CUDA;
+  if (cudaEventRecord(start_ev, (cudaStream_t)s) != cudaSuccess) {
+    cudaEventDestroy(start_ev);
+    return CARE_ERR_CUDA;
+  }
+  std::vector<cudaStream_t> streams(count, nullptr);
+  std::vector<cudaEvent_t> done(count, nullptr);
+  bool setup_ok = true;
+  for (int i = 0; i < count; ++i) {
+    setup_ok &= cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking) == cudaSuccess;
+    setup_ok &= cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) == cudaSuccess;
+    if (setup_ok) setup_ok &= cudaStreamWaitEvent(streams[i], start_ev, 0) == cudaSuccess;
+  }
+  long long launches = 0;
+  if (setup_ok) {
+    st = run_guarded([&] {
+      BatchBroker broker(count, prec == CARE_PREC_FP64 ? 8 : 4, base + off[count], work_bytes - off[count]);
+      const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+      std::vector<std::thread> pool;
+      for (int i = 0; i < count; ++i) {
+        pool.emplace_back([&, i] {
+          cudaSetDevice(dev);
+          omp_set_num_threads(std::max(1, hw / count));
+          status[i] = run_guarded([&] {
+            struct Done {
+              BatchBroker& b;
+              ~Done() { b.instance_done(); }
+            } guard{broker};
+            Ctx c;
+            begin(c, &o, streams[i], base + off[i], off[i + 1] - off[i]);
+            c.broker = &broker;
+            c.lowp = prec == CARE_PREC_MIXED_TF32 ? 1 : (prec == CARE_PREC_MIXED_BF16 ? 2 : 0);
+            if (prec == CARE_PREC_FP64)
+              return solve_impl<double>(c, A[i], B[i], ldb[i], m[i], C[i], ldc[i], p[i], tol, Z[i], ldz[i],
+                                        r_cap[i], &infos[i]);
+            return solve_impl<float>(c, A[i], B[i], ldb[i], m[i], C[i], ldc[i], p[i], tol, Z[i], ldz[i], r_cap[i],
+                                     &infos[i]);
+          });
+          infos[i].status = status[i];
+          cudaEventRecord(done[i], streams[i]);
+        });
+      }
+      for (auto& t : pool) t.join();
+      for (int i = 0; i < count; ++i) cudaStreamWaitEvent((cudaStream_t)s, done[i], 0);
+      launches = broker.launches();
+      return CARE_OK;
+    });
+  }
+  for (int i = 0; i < count; ++i) {
+    if (streams[i]) cudaStreamDestroy(streams[i]);
+    if (done[i]) cudaEventDestroy(done[i]);
+  }
+  cudaEventDestroy(start_ev);
+  if (!setup_ok) return CARE_ERR_CUDA;
+  if (st != CARE_OK) return st;
+  if (batch_launches) *batch_launches = launches;
   if (info)
     for (int i = 0; i < count; ++i) info[i] = infos[i];
   for (int i = 0; i < count; ++i)

@@ -146,6 +146,22 @@ constexpr int kMaxRealCols = 128;  // widest row-block handled by the fused kern
 // CTAs per SM of the row-block kernels (set by care_autotune; default 8)
 int tuned_ctas_per_sm();
 void set_tuned_ctas_per_sm(int v);
+// 16-byte vectors per thread of the SpMM (1, 2 or 4; set by care_autotune,
+// default 1): fewer threads per row, more independent gathers in flight each
+int tuned_spmm_vpt();
+void set_tuned_spmm_vpt(int v);
+// SpMM thread shape for a row of nvec vectors: tpr threads of nvpt vectors each
+inline void spmm_shape(int nvec, int vpt, int* tpr, int* nvpt) {
+  if (vpt < 1) vpt = 1;
+  int t = tpr_for((nvec + vpt - 1) / vpt);
+  int v = (nvec + t - 1) / t;
+  if (v > 4) {
+    t = 32;
+    v = (nvec + 31) / 32;
+  }
+  *tpr = t;
+  *nvpt = v < 1 ? 1 : v;
+}
 
 inline int grid_rows(long rows, int tpr, int ctas_per_sm = 0) {
   if (ctas_per_sm <= 0) ctas_per_sm = tuned_ctas_per_sm();

@@ -54,10 +54,16 @@ void scale_cols(long n, int cols, T* Y, int ldy, const double* d, cudaStream_t s
 // the eigenvectors of those for which want(w_i, max|w|) holds, written as rows of
 // V (device, length n each, in ascending eigenvalue order); returns their indices.
 // work: dev_symeig_work_elems(n) doubles of device scratch.
+// weighted = false: the vectors are orthonormal to working accuracy (clusters of
+// eigenvalues closer than 1e-6 ||T|| orthogonalised explicitly).  weighted = true:
+// for callers that only use the vectors weighted by their eigenvalues (V diag(f(w))
+// with |f(w)| <= |w|^(1/2)...|w|): clusters are also split where the gap exceeds 1e-3
+// of the eigenvalues' magnitude, which keeps the weighted loss of orthogonality
+// below about 1e3 eps ||S|| but not V's own orthogonality among tiny eigenvalues.
 size_t dev_symeig_work_elems(int n);
 std::vector<int> dev_symeig_select(int n, const double* S, int lds, std::vector<double>& w, double* V,
                                    const std::function<bool(double, double)>& want, double* work,
-                                   size_t work_elems, cudaStream_t s);
+                                   size_t work_elems, cudaStream_t s, bool weighted = false);
 
 // measured FP64 FMA throughput of the CUDA cores (TFLOP/s)
 double fp64_fma_peak_tflops(cudaStream_t s);

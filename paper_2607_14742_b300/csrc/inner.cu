@@ -17,6 +17,9 @@ void set_verbose(int v) { g_verbose = v; }
 static std::atomic<int> g_ctas_per_sm{8};
 int tuned_ctas_per_sm() { return g_ctas_per_sm.load(std::memory_order_relaxed); }
 void set_tuned_ctas_per_sm(int v) { g_ctas_per_sm.store(v < 1 ? 1 : (v > 8 ? 8 : v)); }
+static std::atomic<int> g_spmm_vpt{1};
+int tuned_spmm_vpt() { return g_spmm_vpt.load(std::memory_order_relaxed); }
+void set_tuned_spmm_vpt(int v) { g_spmm_vpt.store(v >= 4 ? 4 : (v >= 2 ? 2 : 1)); }
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -271,6 +274,7 @@ void Inner<T>::alloc(Ctx& c, int n_, int m_, int bcap_, int adicap_, int hcap_) 
                           : 0;
   const bool ilu = c.o.precond == CARE_PRECOND_ILU0 || c.o.precond == CARE_PRECOND_ILU0_EXACT;
   kw = krylov_alloc<T>(c.ar, n, jacobi, ilu ? (long)c.op_nnz : -1L, restart);
+  if (c.o.krylov == CARE_KRYLOV_DENSE_LU) dw = dlu_alloc<T>(c.ar, n);
   kw.ilu_sweeps = c.o.ilu_sweeps;
   kw.tri_sweeps = c.o.tri_sweeps;
   ldm = pad_ld<T>(std::max(m, 1));
@@ -390,6 +394,34 @@ static std::vector<Shift> proj_shifts(Ctx& c, Inner<T>& in, bool hasK, const T* 
   return out;
 }
 
+// One chunk of a shifted solve through the batch broker (batched serving mode).
+template <class T>
+static KrylovResult batched_solve(Ctx& c, Inner<T>& in, const OpT<T>& op, Shift p, bool cplx, int c0, int w) {
+  BatchReq<T> q;
+  q.n = op.n;
+  q.cols = w;
+  q.cplx = cplx ? 1 : 0;
+  q.rp = op.rp;
+  q.ci = op.ci;
+  q.av = op.val;
+  q.rs = op.rowsum;
+  q.diag = op.diag;
+  q.sre = p.re;
+  q.sim = p.im;
+  q.rhs = in.RHS + c0;
+  q.ld_rhs = in.ldr;
+  q.sol = in.SOL + c0;
+  q.ld_sol = in.ldr;
+  const KrylovWork<T>& k = in.kw;
+  q.X = k.X; q.R = k.R; q.Rh = k.Rh; q.P = k.P; q.V = k.V; q.S = k.S; q.Tt = k.Tt; q.Ph = k.Ph; q.Sh = k.Sh;
+  CARE_REQUIRE(k.Ph && k.Sh && k.Dinv, CARE_ERR_INVALID_ARG, "batched solve: Jacobi blocks missing");
+  q.Dinv = k.Dinv;
+  const double tol = krylov_tol<T>(c);
+  q.tol2 = tol * tol;
+  q.maxit = krylov_maxit<T>(c);
+  return c.broker->solve<T>(q, c.s);
+}
+
 // SMW shifted solve (Section 4):  V = M_p^{-1} W + Y (I - B^T Y)^{-1} B^T M_p^{-1} W,
 // Y = M_p^{-1} K, M_p = (A + p I)^T.  W: first b columns of in.W (real).
 // On return V occupies the first b (complex: 2b real) columns of in.SOL.
@@ -409,7 +441,9 @@ static void smw_solve(Ctx& c, Inner<T>& in, Shift p, int b, bool hasK) {
     if (m) copy2d<T, T>(n, m, in.K, in.ldm, 1, in.RHS + b, in.ldr, 1, 1.0, c.s);
   }
   const OpT<T> op = op_of<T>(c);
-  const int chunk = std::min(kMaxRealCols, std::max(2, (c.o.krylov_chunk > 0 ? c.o.krylov_chunk : 64) * (cplx ? 2 : 1)));
+  const bool dense = c.o.krylov == CARE_KRYLOV_DENSE_LU;  // one factorisation serves every column
+  const int chunk =
+      dense ? rc : std::min(kMaxRealCols, std::max(2, (c.o.krylov_chunk > 0 ? c.o.krylov_chunk : 64) * (cplx ? 2 : 1)));
   for (int c0 = 0; c0 < rc; c0 += chunk) {
     const int w = std::min(chunk, rc - c0);
     if (!c.ke0) {
@@ -418,7 +452,9 @@ static void smw_solve(Ctx& c, Inner<T>& in, Shift p, int b, bool hasK) {
     }
     CARE_CUDA(cudaEventRecord(c.ke0, c.s));
     KrylovResult kr =
-        c.o.krylov == CARE_KRYLOV_GMRES
+        c.broker ? batched_solve<T>(c, in, op, p, cplx, c0, w)
+        : dense ? dense_lu_solve<T>(c.op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr, w, in.dw, c.s)
+        : c.o.krylov == CARE_KRYLOV_GMRES
             ? krylov_gmres<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr, w,
                               krylov_tol<T>(c), krylov_maxit<T>(c), c.o.precond, in.kw, c.s)
             : krylov_bicgstab<T>(op, cd{p.re, p.im}, cplx, in.RHS + c0, in.ldr, in.SOL + c0, in.ldr, w,
@@ -545,9 +581,10 @@ static bool compress_joint(Ctx& c, Inner<T>& in, int& np, int& nm) {
   double* Vd = ds.get((size_t)q * q);
   const double rel = sizeof(T) == 4 ? 1e-8 : 1e-15;
   std::vector<double> lam;
+  // the compressed factors carry each vector weighted by |lambda|^(1/2): weighted clustering
   std::vector<int> sel = dev_symeig_select(
       q, Pd, q, lam, Vd, [rel](double l, double lmx) { return std::fabs(l) >= rel * lmx && l != 0.0; }, ework, ew,
-      c.s);
+      c.s, true);
   c.host_syncs += 3;
   std::vector<int> pos(q, -1);
   for (int t = 0; t < (int)sel.size(); ++t) pos[sel[t]] = t;

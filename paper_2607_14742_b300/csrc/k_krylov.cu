@@ -350,11 +350,12 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
   }
 }
 
+// Every SpMM launch (standalone and inside the Krylov iterations) takes the thread
+// shape of the tuned vectors-per-thread count, with its own grid.
 template <class T, int NDOT, bool CPLX>
 static void launch_spmm(const SpmmArgs<T>& a, cudaStream_t s) {
-  const int nv = a.nvec;
-  int tpr = tpr_for(nv);
-  const int nvpt = (nv + 31) / 32;
+  int tpr = 1, nvpt = 1;
+  spmm_shape(a.nvec, tuned_spmm_vpt(), &tpr, &nvpt);
   const int grid = grid_rows(a.n, tpr);
 #define CARE_SPMM_CASE(TP, NV)                                                          \
   if (tpr == TP && nvpt == NV) {                                                        \
@@ -364,6 +365,9 @@ static void launch_spmm(const SpmmArgs<T>& a, cudaStream_t s) {
   }
   CARE_SPMM_CASE(1, 1) CARE_SPMM_CASE(2, 1) CARE_SPMM_CASE(4, 1) CARE_SPMM_CASE(8, 1)
   CARE_SPMM_CASE(16, 1) CARE_SPMM_CASE(32, 1) CARE_SPMM_CASE(32, 2)
+  CARE_SPMM_CASE(1, 2) CARE_SPMM_CASE(2, 2) CARE_SPMM_CASE(4, 2) CARE_SPMM_CASE(8, 2) CARE_SPMM_CASE(16, 2)
+  CARE_SPMM_CASE(1, 3) CARE_SPMM_CASE(2, 3) CARE_SPMM_CASE(4, 3) CARE_SPMM_CASE(8, 3)
+  CARE_SPMM_CASE(1, 4) CARE_SPMM_CASE(2, 4) CARE_SPMM_CASE(4, 4) CARE_SPMM_CASE(8, 4)
 #undef CARE_SPMM_CASE
   CARE_THROW(CARE_ERR_INVALID_ARG, "spmm: block too wide");
 }
@@ -969,7 +973,9 @@ __device__ __forceinline__ bool ilu_wait(const int* flags, int k, int* err) {
       }
     }
   }
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();  // the other lanes' reads of the awaited row come after lane 0's acquire
+  return ok != 0;
 }
 
 template <class T, bool CPLX>
@@ -990,7 +996,10 @@ __global__ void k_ilu_exact(int n, const int* __restrict__ rp, const int* __rest
     row = __shfl_sync(0xffffffffu, row, 0);
     if (row >= n) break;
     const int b = rp[row], e_end = rp[row + 1], dp = dpos[row];
-    bool alive = *(volatile int*)err == 0;
+    // entry e of the row belongs to lane (e - b) % 32 for the whole row: it is read
+    // and written by that lane only, so no value of this row passes between lanes
+    // through memory (the multiplier is broadcast by shuffle)
+    bool alive = __shfl_sync(0xffffffffu, *(volatile int*)err == 0 ? 1 : 0, 0) != 0;
     for (int e = b; e < dp && alive; ++e) {
       const int k = ci[e];
       if (!ilu_wait(flags, k, err)) {
@@ -998,10 +1007,17 @@ __global__ void k_ilu_exact(int n, const int* __restrict__ rp, const int* __rest
         break;
       }
       // l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for the pattern entries j > k of row i
-      const cd lik = cdivz(fld_cg<T, CPLX>(F, e), fld_cg<T, CPLX>(F, dpos[k]));
-      if (lane == 0) fstore<T, CPLX>(F, e, lik);
+      const int owner = (e - b) & 31;
+      cd lik{0.0, 0.0};
+      if (lane == owner) {
+        lik = cdivz(fld_cg<T, CPLX>(F, e), fld_cg<T, CPLX>(F, dpos[k]));
+        fstore<T, CPLX>(F, e, lik);
+      }
+      lik.re = __shfl_sync(0xffffffffu, lik.re, owner);
+      lik.im = __shfl_sync(0xffffffffu, lik.im, owner);
       const int kb = dpos[k] + 1, ke = rp[k + 1];
-      for (int e2 = e + 1 + lane; e2 < e_end; e2 += 32) {
+      for (int e2 = b + lane; e2 < e_end; e2 += 32) {
+        if (e2 <= e) continue;
         const int j = ci[e2];
         int lo = kb, hi = ke - 1, pos = -1;
         while (lo <= hi) {
@@ -1018,7 +1034,6 @@ __global__ void k_ilu_exact(int n, const int* __restrict__ rp, const int* __rest
           fstore<T, CPLX>(F, e2, a);
         }
       }
-      __syncwarp();
     }
     __threadfence();
     __syncwarp();
@@ -1049,7 +1064,7 @@ __global__ void k_tri_exact(long n, const int* __restrict__ rp, const int* __res
       const int v = lane + 32 * k2;
       if (v < nvec) vload(r + (size_t)row * ld + v * VEC, acc[k2]);
     }
-    bool alive = *(volatile int*)err == 0;
+    bool alive = __shfl_sync(0xffffffffu, *(volatile int*)err == 0 ? 1 : 0, 0) != 0;
     for (int e = e0; e < e1 && alive; ++e) {
       const int k = ci[e];
       if (!ilu_wait(flags, k, err)) {
@@ -1200,14 +1215,12 @@ static void bicg_iteration(const KArgs<T>& a, SpmmArgs<T>& sp, int grid, cudaStr
   CARE_LAUNCH();
   if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.P, a.Ph, grid, s);
   sp.X = PREC ? a.Ph : a.P; sp.Y = a.V; sp.w0 = a.Rh; sp.w1 = nullptr; sp.mode = FIN_ALPHA;
-  k_spmm<T, TPR, NVPT, CPLX, 1><<<grid, kBlock, 0, s>>>(sp);
-  CARE_LAUNCH();
+  launch_spmm<T, 1, CPLX>(sp, s);
   k_bicg_s<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
   CARE_LAUNCH();
   if constexpr (PREC == 2) ilu_apply<T, TPR, NVPT, CPLX>(a, a.S, a.Sh, grid, s);
   sp.X = PREC ? a.Sh : a.S; sp.Y = a.Tt; sp.w0 = a.S; sp.w1 = nullptr; sp.mode = FIN_OMEGA;
-  k_spmm<T, TPR, NVPT, CPLX, 2><<<grid, kBlock, 0, s>>>(sp);
-  CARE_LAUNCH();
+  launch_spmm<T, 2, CPLX>(sp, s);
   k_bicg_xr<T, TPR, NVPT, CPLX, PREC><<<grid, kBlock, 0, s>>>(a);
   CARE_LAUNCH();
 }
@@ -1449,13 +1462,13 @@ done:
     const double blk = (double)op.n * a.ld * sv;
     const double amat = (double)op.nnz * (sv + 4) + 4.0 * (op.n + 1) + (op.rowsum ? sv * op.n : 0.0);
     const double trisw = 0.5 * op.nnz * (sf + 4) + 8.0 * op.n;
-    const int T_ = a.tri_sweeps;
+    const int T_ = a.exact ? 1 : a.tri_sweeps;  // exact triangular solves: one pass each
     double per = 2 * amat;
     if (pmode == 0) per += 21 * blk;
     else if (pmode == 1) per += 25 * blk + 2 * sf * op.n;
     else per += (24 + 12.0 * T_) * blk + 4.0 * T_ * trisw;
     double setup = 6 * blk;
-    if (pmode == 2) setup += (1 + w.ilu_sweeps) * ((double)op.nnz * (2 * sf + 4) + 8.0 * op.n);
+    if (pmode == 2) setup += (1 + (a.exact ? 1 : w.ilu_sweeps)) * ((double)op.nnz * (2 * sf + 4) + 8.0 * op.n);
     r.bytes = setup + per * r.iters;
   }
   {
@@ -1761,8 +1774,7 @@ static KrylovResult run_gmres(const OpT<T>& op, cd sigma, const KArgs<T>& a, int
   sp.nvec = a.nvec; sp.sre = sigma.re; sp.sim = sigma.im;
   auto matvec = [&](const T* x, T* y) {
     sp.X = x; sp.Y = y;
-    k_spmm<T, TPR, NVPT, CPLX, 0><<<grid, kBlock, 0, s>>>(sp);
-    CARE_LAUNCH();
+    launch_spmm<T, 0, CPLX>(sp, s);
   };
   // x = 0, r = b (padded block copy of the right-hand side)
   CARE_CUDA(cudaMemsetAsync(X, 0, sizeof(T) * blk, s));

@@ -13,9 +13,11 @@
 //     to an absolute accuracy of a few units of roundoff of ||T||.
 //  3. Eigenvectors of T by inverse iteration with a partially pivoted LU of
 //     T - lambda I (Golub & Van Loan, Sec. 8.4.3 / 7.6.1), one CTA per cluster:
-//     eigenvalues closer than 1e-6 ||T||_1 form a cluster whose vectors are
-//     orthogonalised against each other after every solve (as LAPACK's dstein
-//     does with its wider 1e-3 window).
+//     eigenvalues closer than 1e-6 ||T||_1 (and, for callers that weight the
+//     vectors by their eigenvalues, closer than 1e-3 of their magnitude) form a
+//     cluster whose vectors are orthogonalised against each other after every
+//     solve (as LAPACK's dstein does with its absolute 1e-3 window), by classical
+//     Gram-Schmidt twice.
 //  4. Back-transformation x <- H_0 ... H_{n-3} x, one CTA per group of vectors
 //     held in shared memory.
 // Results are deterministic (fixed reduction orders, no atomics).
@@ -154,6 +156,8 @@ __global__ void k_stebz(int n, const double* __restrict__ d, const double* __res
   w[i] = 0.5 * (lo + hi);
 }
 
+constexpr int STEIN_CHUNK = 1024;
+
 // Inverse iteration for the selected eigenvalues, one CTA per cluster
 // [cstart[c], cstart[c+1]) of the selected list lam[]; vector j -> X[j * n ..).
 // Thread 0 factors T - lambda I (partially pivoted LU) and runs the triangular
@@ -170,6 +174,8 @@ __global__ void __launch_bounds__(128) k_stein(int n, const double* __restrict__
   const int c = blockIdx.x;
   if (c >= nclus) return;
   __shared__ double sh[4];
+  __shared__ double tdot[STEIN_CHUNK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double eps = 2.220446049250313e-16;
   const double eps3 = eps * onenrm;
   double* dl = scratch + (long)c * 5 * n;
@@ -252,14 +258,26 @@ __global__ void __launch_bounds__(128) k_stein(int n, const double* __restrict__
         }
       }
       __syncthreads();
-      // orthogonalise against the earlier vectors of the cluster (twice)
+      // orthogonalise against the earlier vectors of the cluster: classical
+      // Gram-Schmidt, twice, in chunks of STEIN_CHUNK vectors (all dots of a chunk,
+      // one warp per vector, then one subtraction sweep: two barriers per chunk)
       for (int pass = 0; pass < 2; ++pass)
-        for (int q = cstart[c]; q < j; ++q) {
-          const double* xq = X + (long)q * n;
-          double t = 0.0;
-          for (int i = threadIdx.x; i < n; i += blockDim.x) t += xq[i] * b[i];
-          t = csum(t);
-          for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] -= t * xq[i];
+        for (int q0 = cstart[c]; q0 < j; q0 += STEIN_CHUNK) {
+          const int nq = min(STEIN_CHUNK, j - q0);
+          for (int q = warp; q < nq; q += 4) {
+            const double* xq = X + (long)(q0 + q) * n;
+            double t = 0.0;
+            for (int i = lane; i < n; i += 32) t += xq[i] * b[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) tdot[q] = t;
+          }
+          __syncthreads();
+          for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double bi = b[i];
+            for (int q = 0; q < nq; ++q) bi -= tdot[q] * X[(long)(q0 + q) * n + i];
+            b[i] = bi;
+          }
           __syncthreads();
         }
       double t = 0.0;
@@ -365,7 +383,7 @@ size_t dev_symeig_work_elems(int n) {
 // of V = eigenvector of w[sel[i]], length n), returning the selected indices.
 std::vector<int> dev_symeig_select(int n, const double* S, int lds, std::vector<double>& w, double* V,
                                    const std::function<bool(double, double)>& want, double* work,
-                                   size_t work_elems, cudaStream_t s) {
+                                   size_t work_elems, cudaStream_t s, bool weighted) {
   std::vector<int> sel;
   w.assign(n, 0.0);
   if (n == 0) return sel;
@@ -440,14 +458,24 @@ std::vector<int> dev_symeig_select(int n, const double* S, int lds, std::vector<
     if (want(w[i], wmax)) sel.push_back(i);
   const int k = (int)sel.size();
   if (k == 0) return sel;
-  // clusters of the selected eigenvalues: consecutive gaps below 1e-6 ||T||_1 (inverse
-  // iteration leaves vectors of eigenvalues that far apart orthogonal to about
-  // eps ||T|| / gap <= 2e-10; closer ones are orthogonalised explicitly)
+  // clusters of the selected eigenvalues.  Inverse iteration leaves the vectors of
+  // eigenvalues a gap g apart orthogonal to about eps ||T|| / g, so a new cluster
+  // starts where the gap exceeds 1e-6 ||T||_1 (vectors of closer eigenvalues are
+  // orthogonalised explicitly).  For weighted use (products that weight each vector
+  // by its eigenvalue, V diag(lambda) V^T or V diag(sqrt|lambda|)) what matters is
+  // |lambda| eps ||T|| / g, and a cluster also ends where the gap exceeds
+  // 1e-3 max(|lambda_q|, |lambda_q-1|): that keeps the weighted loss of
+  // orthogonality below about 1e3 eps ||T|| and splits the dense run of small
+  // eigenvalues (hundreds within 1e-6 ||T|| of zero in the truncations) that would
+  // otherwise be one cluster orthogonalised vector by vector in a single CTA.
   std::vector<double> lam(k);
   std::vector<int> cst;
   for (int q = 0; q < k; ++q) {
     lam[q] = w[sel[q]];
-    if (q == 0 || lam[q] - lam[q - 1] > 1e-6 * tnorm) cst.push_back(q);
+    const double gap = q > 0 ? lam[q] - lam[q - 1] : 0.0;
+    if (q == 0 || gap > 1e-6 * tnorm ||
+        (weighted && gap > 1e-3 * std::max(std::fabs(lam[q]), std::fabs(lam[q - 1]))))
+      cst.push_back(q);
   }
   cst.push_back(k);
   const int ncl = (int)cst.size() - 1;

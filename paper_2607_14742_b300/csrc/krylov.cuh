@@ -88,6 +88,24 @@ template <class T>
 KrylovResult krylov_gmres(const OpT<T>& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol, int ld_sol,
                           int cols, double tol, int maxit, int precond, KrylovWork<T>& w, cudaStream_t s);
 
+// Dense-direct shifted solve (Section 4's dense direct solvers): M_p formed densely
+// from the operator, LU with partial pivoting, all `cols` real columns at once
+// (complex interleaved when cplx).  iters = 1; unconverged = cols if a pivot was
+// exactly zero.  Synchronises s.
+template <class T>
+struct DluWork {
+  T* M = nullptr;     // n x n (complex: 2 n^2) column-major factors
+  int* ipiv = nullptr;
+  T* cbuf = nullptr;  // two copies of the next pivot column
+  int* info = nullptr;
+  int n = 0;
+};
+template <class T>
+DluWork<T> dlu_alloc(Arena& ar, int n);
+template <class T>
+KrylovResult dense_lu_solve(const care_op& op, cd sigma, bool cplx, const T* rhs, int ld_rhs, T* sol, int ld_sol,
+                            int cols, const DluWork<T>& w, cudaStream_t s);
+
 // The ILU(0) factor of M_p (fixed-point sweeps, or exact) copied into F (values on
 // the pattern of A^T; complex interleaved when cplx).  Synchronises s.
 template <class T>

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <vector>
 
+#include "batch.cuh"
 #include "dense.cuh"
 #include "krylov.cuh"
 #include "tc.cuh"
@@ -59,6 +60,9 @@ struct Ctx {
   double kry_ms = 0.0, kry_gbyte = 0.0;
   cudaEvent_t ke0 = nullptr, ke1 = nullptr;
   long long host_syncs = 0;  // stream synchronisations of the host control
+  // batched serving mode: the shifted solves go to this broker (one persistent
+  // launch over the pending solves of all instances) instead of the block Krylov
+  BatchBroker* broker = nullptr;
   bool counting() const { return ar.counting(); }
   Ctx() = default;
   Ctx(const Ctx&) = delete;
@@ -189,6 +193,7 @@ template <class T>
 struct Inner {
   int n = 0, m = 0, bcap = 0, adicap = 0, hcap = 0;
   KrylovWork<T> kw;
+  DluWork<T> dw;  // dense-direct shifted solves (CARE_KRYLOV_DENSE_LU)
   T *B = nullptr, *K = nullptr, *Knew = nullptr, *Kd = nullptr;  // n x m (ldm)
   T *W = nullptr, *W0 = nullptr;                                 // n x bcap (ldw)
   T *RHS = nullptr, *SOL = nullptr;                              // n x 2(bcap+m) (ldr)

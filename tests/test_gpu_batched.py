@@ -40,3 +40,40 @@ def test_batched_uneven_sizes_order_independent(pb):
     Z4, _, _ = pb.care_solve_batched(dev, tol=1e-10, prec="mixed", r_cap=128, workers=4)
     for a, b in zip(Z1, Z4):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batched_persistent_vs_oracle(pb, prec):
+    """Serving mode (care_solve_batched_persistent): the shifted solves of all instances
+    run in shared persistent launches.  Every instance reaches the residual tolerance
+    and the dense Newton / Bartels-Stewart solution of the oracle to 1e-8, and the
+    launches are fewer than the shifted solves the instances issue on their own."""
+    probs = ci.config_batched(count=6, side_lo=12, side_hi=28, mp_hi=3)
+    dev = [(pb.CSR.from_arrays(p.n, p.A.rowptr, p.A.colind, p.A.val), p.B, p.C) for p in probs]
+    stats = {}
+    Zb, infos, st = pb.care_solve_batched(dev, tol=1e-10, prec=prec, r_cap=128, persistent=True, stats=stats)
+    assert st == 0
+    solves = 0
+    for (A, B, C), p, Z, inf in zip(dev, probs, Zb, infos):
+        assert inf["status"] == "CARE_OK" and inf["res_rel_CtC"] <= 1e-10, (p.name, inf)
+        X = od.newton_care(p.A.to_dense(), p.B, p.C)["X"]
+        Zh = Z.cpu().numpy()
+        assert np.linalg.norm(Zh @ Zh.T - X) <= 1e-8 * np.linalg.norm(X), p.name
+        solves += inf["iter0"][1] + inf["iter"][1]  # LR-ADI steps: one SMW solve each
+    assert 0 < stats["batch_launches"] < solves, (stats, solves)
+
+
+def test_batched_persistent_uneven_many(pb):
+    """A scaled-down serving sweep: 16 instances, grid sides 8..40, m, p in 1..8 (the
+    uneven-size, uneven-width mix of the serving workload), mixed precision: every
+    instance converges and agrees with its own single FP64 solve to 1e-8."""
+    probs = ci.config_batched(count=16, side_lo=8, side_hi=40, mp_hi=8)
+    dev = [(pb.CSR.from_arrays(p.n, p.A.rowptr, p.A.colind, p.A.val), p.B, p.C) for p in probs]
+    Zb, infos, st = pb.care_solve_batched(dev, tol=1e-10, prec="mixed", r_cap=192, persistent=True)
+    assert st == 0
+    for (A, B, C), p, Z, inf in zip(dev, probs, Zb, infos):
+        assert inf["status"] == "CARE_OK", (p.name, inf)
+        Zi, _ = pb.care_solve(A, B, C, tol=1e-10, prec="fp64", r_cap=192)
+        Zh, Zih = Z.cpu().numpy(), Zi.cpu().numpy()
+        Xi = Zih @ Zih.T
+        assert np.linalg.norm(Zh @ Zh.T - Xi) <= 1e-8 * np.linalg.norm(Xi), p.name

@@ -32,7 +32,7 @@ def _problem(case):
     rng = np.random.default_rng(11)  # unstructured: random pattern plus the diagonal
     n = 1500
     R = sp.random(n, n, density=0.003, random_state=12, format="csr")
-    return sp.csr_matrix(R - (4.0 + rng.random(n)) * sp.eye(n))
+    return sp.csr_matrix(R - sp.diags(4.0 + rng.random(n)))
 
 
 def _op(pb, A):

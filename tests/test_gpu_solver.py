@@ -1,5 +1,8 @@
 """GPU parity of the solver entry points (lyap_lradi, care_residual_factor,
 care_solve) against the CPU FP64 oracle, through the C ABI."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -116,6 +119,43 @@ def test_care_solve_dense_conditioning(pb, k, compress):
     # the error against the oracle is the one the final residual implies (first-order
     # estimate est, from the oracle's dense Lyapunov solve), and <= 1e-8 once that is small
     assert err <= max(1e-8, 1.5 * est), (info, err, est)
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.mark.parametrize("k", range(7))
+def test_care_solve_conditioning_sweep_dense_direct(pb, k):
+    """The Lyapunov-conditioning threshold (Theorem 1; Table 1's experiment, Section
+    5.1) on the n = 200 dense family, kappa_2(A) = 10^k, with dense-direct shifted
+    solves as Section 5.1 uses, against the oracle's outcome at the same k
+    (tests/golden/dense200_sweep.json, written by make_dense200_sweep.py): where the
+    oracle's FP32-inner refinement converges (k <= 3) the mixed GPU path reaches
+    relative residual 1e-10 and ||Z Z^T - X*||_F / ||X*||_F <= 1e-8; at k = 4 the
+    FP32-inner path stalls while FP64 inner solves still reach the oracle's FP64
+    level; beyond (k >= 5) neither precision converges, as in the oracle."""
+    with open(os.path.join(GOLDEN, "dense200_sweep.json")) as f:
+        g = json.load(f)
+    o32, o64 = g[f"{k}/fp32"], g[f"{k}/fp64"]
+    prob = ci.config_dense_conditioning(k)
+    A = prob.A.to_dense()
+    X = od.newton_care(A, prob.B, prob.C)["X"]
+    o = pb.default_options(krylov=pb.KRYLOV_DENSE_LU)
+    Z, info = pb.care_solve(dcsr(pb, prob), prob.B, prob.C, tol=1e-12, prec="mixed", r_cap=600, opts=o,
+                            allow=(5, 6, 7, 8))
+    Z = Z.cpu().numpy()
+    err = np.linalg.norm(Z @ Z.T - X) / np.linalg.norm(X)
+    rel = info["res_rel_CtC"]
+    if o32["status"] == "ok":
+        assert rel <= 1e-10 and err <= 1e-8, (info, err, o32)
+    else:
+        assert info["status"] != "CARE_OK" and rel > 1e-9, (info, err, o32)
+    if k == 4:
+        Z64, i64 = pb.care_solve(dcsr(pb, prob), prob.B, prob.C, tol=1e-12, prec="fp64", r_cap=600, opts=o,
+                                 allow=(5, 6, 7, 8))
+        assert o64["rel_res"] < 1e-9 and i64["res_rel_CtC"] <= 10 * o64["rel_res"], (i64, o64)
+    if k >= 5:
+        assert o64["status"] != "ok" and o32["status"] != "ok"
 
 
 def test_care_solve_eigen_aligned_closed_form(pb):
