@@ -237,7 +237,7 @@ def main():
     del dA0
 
     def opts(prec):
-        return pb.default_options(krylov_chunk=tuned.krylov_chunk, tri_sweeps=tuned.tri_sweeps,
+        return pb.default_options(krylov=tuned.krylov, krylov_chunk=tuned.krylov_chunk, tri_sweeps=tuned.tri_sweeps,
                                   precond=tuned.precond)
 
     def step(prec):
@@ -324,7 +324,9 @@ def main():
                      "alg2": info["ms_phase"][3]},
         "host_syncs": info["host_syncs"],
         "fp64_path": fp64,
-        "autotune": {"krylov_chunk": tuned.krylov_chunk, "tri_sweeps": tuned.tri_sweeps, "precond": tuned.precond,
+        "autotune": {"krylov": tuned.krylov, "krylov_chunk": tuned.krylov_chunk, "tri_sweeps": tuned.tri_sweeps,
+                     "precond": tuned.precond, "spmm_vectors_per_thread": pb.launch_shape()[0],
+                     "ctas_per_sm": pb.launch_shape()[1], "spmm_row_blocks": pb.launch_shape()[2],
                      "best_ms": tune_ms, "seconds": t_tune},
         "e2e": {"value": te, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -285,10 +285,12 @@ care_status care_shifted_solve(const care_op* op, const double* B, int ldb, cons
 
 /* Autotuner for the shifted solves (no paper counterpart), in two stages on the
  * operator at a mid-spectrum shift p = -0.05 max|a_ii|:
- *  1. SpMM thread shape: 16-byte vectors per thread in {1, 2, 4} (fewer threads
+ *  1. SpMM launch shape: 16-byte vectors per thread in {1, 2, 4} (fewer threads
  *     per row, more gathers in flight per thread) x {4, 8} CTAs per SM for the
- *     row-block kernels, each timed on a b-column block in the working precision
- *     (median of 5 launches); the fastest is applied process-wide.
+ *     row-block kernels x row order (grid-stride, or contiguous row blocks per
+ *     CTA so that a stencil's neighbour rows come from the same SM's cache),
+ *     each timed on a b-column block in the working precision (median of 5
+ *     launches); the fastest is applied process-wide.
  *  2. Shifted solves (SMW + block Krylov) of a b-column right-hand side
  *     (deterministic pseudo-random entries) with that shape over krylov in
  *     {BiCGStab, GMRES}, precond in {ILU0 with tri_sweeps 1, 2, 3, ILU0_EXACT,
@@ -301,10 +303,11 @@ care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_p
 care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_opts* opts, void* work,
                           size_t work_bytes, care_stream_t s, double* best_ms);
 /* The process-wide launch shape (autotuner stage 1): SpMM vectors per thread
- * (1, 2 or 4) and CTAs per SM (1..8) of the row-block kernels.  set returns
+ * (1, 2 or 4), CTAs per SM (1..8) of the row-block kernels, SpMM row order
+ * (0 grid-stride, 1 contiguous blocks per CTA).  set returns
  * CARE_ERR_INVALID_ARG for other values; get always succeeds (returns 0). */
-int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm);
-care_status care_set_launch_shape(int spmm_vpt, int ctas_per_sm);
+int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm, int* spmm_blocked);
+care_status care_set_launch_shape(int spmm_vpt, int ctas_per_sm, int spmm_blocked);
 
 /* ---- solver entry points ------------------------------------------------ */
 

@@ -126,8 +126,8 @@ def lib() -> ct.CDLL:
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_fp64_peak": (i, [P(d), vp]),
         "care_symeig_work_size": (sz, [i]),
-        "care_get_launch_shape": (i, [P(i), P(i)]),
-        "care_set_launch_shape": (i, [i, i]),
+        "care_get_launch_shape": (i, [P(i), P(i), P(i)]),
+        "care_set_launch_shape": (i, [i, i, i]),
         "care_ilu0_work_size": (sz, [P(op_t), i]),
         "care_ilu0": (i, [P(op_t), i, i, d, d, vp, vp, sz, vp]),
         "care_symeig": (i, [i, vp, i, vp, vp, d, d, P(i), vp, sz, vp]),
@@ -472,14 +472,15 @@ TC_MODES = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3}
 
 
 def launch_shape():
-    """(SpMM vectors per thread, CTAs per SM) of the row-block kernels."""
-    v, c = ct.c_int(0), ct.c_int(0)
-    lib().care_get_launch_shape(ct.byref(v), ct.byref(c))
-    return v.value, c.value
+    """(SpMM vectors per thread, CTAs per SM, SpMM contiguous row blocks) of the row-block kernels."""
+    v, c, b = ct.c_int(0), ct.c_int(0), ct.c_int(0)
+    lib().care_get_launch_shape(ct.byref(v), ct.byref(c), ct.byref(b))
+    return v.value, c.value, b.value
 
 
-def set_launch_shape(spmm_vpt: int, ctas_per_sm: int):
-    _check(lib().care_set_launch_shape(int(spmm_vpt), int(ctas_per_sm)), "care_set_launch_shape")
+def set_launch_shape(spmm_vpt: int, ctas_per_sm: int, spmm_blocked: int = 0):
+    _check(lib().care_set_launch_shape(int(spmm_vpt), int(ctas_per_sm), int(spmm_blocked)),
+           "care_set_launch_shape")
 
 
 def ilu0(op: Operator, shift, exact=True, dtype=torch.float64):

@@ -367,8 +367,7 @@ static Alg1Out alg1(Ctx& c, const Prob& P, Ref& R, int rq, const std::vector<dou
     const double e = eta_rel * lmx;
     return e > 0 ? (l >= e || l <= -e) : l != 0.0;
   };
-  // C+- only enter as factors weighted by |lambda|^(1/2): weighted clustering
-  std::vector<int> sel = dev_symeig_select(rt, H, rt, lam, Vd, kept_r, ework, ew, c.s, true);
+  std::vector<int> sel = dev_symeig_select(rt, H, rt, lam, Vd, kept_r, ework, ew, c.s);
   c.ms_host += now_ms() - th;
   c.host_syncs += 3;
   double ss = 0.0, lmax = 0.0;
@@ -1079,19 +1078,21 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int prev_ctas = tuned_ctas_per_sm(), prev_vpt = tuned_spmm_vpt();
+  const int prev_ctas = tuned_ctas_per_sm(), prev_vpt = tuned_spmm_vpt(), prev_blk = tuned_spmm_blocked();
   // stage 1: SpMM thread shape (vectors per thread) and CTAs per SM, timed on the
   // operator at the solve's width and working precision (median of 5 launches)
-  int best_vpt = prev_vpt, best_ctas = prev_ctas;
+  int best_vpt = prev_vpt, best_ctas = prev_ctas, best_blk = prev_blk;
   {
     const bool f64 = prec == CARE_PREC_FP64;
     const int ld = f64 ? (int)pad_ld<double>(b) : (int)pad_ld<float>(b);
     double bst = 1e300;
     const int vpts[3] = {1, 2, 4}, ctas[2] = {4, 8};
+    for (int bl = 0; bl < 2; ++bl)
     for (int ci = 0; ci < 2; ++ci)
       for (int vi = 0; vi < 3; ++vi) {
         set_tuned_ctas_per_sm(ctas[ci]);
         set_tuned_spmm_vpt(vpts[vi]);
+        set_tuned_spmm_blocked(bl);
         std::vector<float> ms;
         bool ok = true;
         for (int r = 0; r < 7 && ok; ++r) {
@@ -1116,10 +1117,12 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
           bst = med;
           best_vpt = vpts[vi];
           best_ctas = ctas[ci];
+          best_blk = bl;
         }
       }
     set_tuned_ctas_per_sm(best_ctas);
     set_tuned_spmm_vpt(best_vpt);
+    set_tuned_spmm_blocked(best_blk);
   }
   // stage 2: shifted-solve configurations with that shape
   double best = 1e300;
@@ -1158,6 +1161,7 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   if (best >= 1e300) {
     set_tuned_ctas_per_sm(prev_ctas);
     set_tuned_spmm_vpt(prev_vpt);
+    set_tuned_spmm_blocked(prev_blk);
     return CARE_INNER_FAILED;
   }
   opts->krylov = bestopt.krylov;
@@ -1168,17 +1172,20 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   return CARE_OK;
 }
 
-int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm) {
+int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm, int* spmm_blocked) {
   if (spmm_vpt) *spmm_vpt = tuned_spmm_vpt();
   if (ctas_per_sm) *ctas_per_sm = tuned_ctas_per_sm();
+  if (spmm_blocked) *spmm_blocked = tuned_spmm_blocked();
   return 0;
 }
 
-care_status care_set_launch_shape(int spmm_vpt, int ctas_per_sm) {
-  if ((spmm_vpt != 1 && spmm_vpt != 2 && spmm_vpt != 4) || ctas_per_sm < 1 || ctas_per_sm > 8)
+care_status care_set_launch_shape(int spmm_vpt, int ctas_per_sm, int spmm_blocked) {
+  if ((spmm_vpt != 1 && spmm_vpt != 2 && spmm_vpt != 4) || ctas_per_sm < 1 || ctas_per_sm > 8 ||
+      (spmm_blocked != 0 && spmm_blocked != 1))
     return CARE_ERR_INVALID_ARG;
   set_tuned_spmm_vpt(spmm_vpt);
   set_tuned_ctas_per_sm(ctas_per_sm);
+  set_tuned_spmm_blocked(spmm_blocked);
   return CARE_OK;
 }
 

@@ -150,6 +150,9 @@ void set_tuned_ctas_per_sm(int v);
 // default 1): fewer threads per row, more independent gathers in flight each
 int tuned_spmm_vpt();
 void set_tuned_spmm_vpt(int v);
+// SpMM row order: 1 = contiguous row blocks per CTA, 0 = grid-stride (set by care_autotune)
+int tuned_spmm_blocked();
+void set_tuned_spmm_blocked(int v);
 // SpMM thread shape for a row of nvec vectors: tpr threads of nvpt vectors each
 inline void spmm_shape(int nvec, int vpt, int* tpr, int* nvpt) {
   if (vpt < 1) vpt = 1;

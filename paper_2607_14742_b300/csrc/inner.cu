@@ -20,6 +20,9 @@ void set_tuned_ctas_per_sm(int v) { g_ctas_per_sm.store(v < 1 ? 1 : (v > 8 ? 8 :
 static std::atomic<int> g_spmm_vpt{1};
 int tuned_spmm_vpt() { return g_spmm_vpt.load(std::memory_order_relaxed); }
 void set_tuned_spmm_vpt(int v) { g_spmm_vpt.store(v >= 4 ? 4 : (v >= 2 ? 2 : 1)); }
+static std::atomic<int> g_spmm_blocked{0};
+int tuned_spmm_blocked() { return g_spmm_blocked.load(std::memory_order_relaxed); }
+void set_tuned_spmm_blocked(int v) { g_spmm_blocked.store(v ? 1 : 0); }
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -581,10 +584,12 @@ static bool compress_joint(Ctx& c, Inner<T>& in, int& np, int& nm) {
   double* Vd = ds.get((size_t)q * q);
   const double rel = sizeof(T) == 4 ? 1e-8 : 1e-15;
   std::vector<double> lam;
-  // the compressed factors carry each vector weighted by |lambda|^(1/2): weighted clustering
+  // The compressed FP32 factors carry each vector weighted by |lambda|^(1/2) and are only
+  // FP32-accurate: weighted clustering, which splits the long run of small kept
+  // eigenvalues into separate clusters.  FP64 factors keep the strict clustering.
   std::vector<int> sel = dev_symeig_select(
       q, Pd, q, lam, Vd, [rel](double l, double lmx) { return std::fabs(l) >= rel * lmx && l != 0.0; }, ework, ew,
-      c.s, true);
+      c.s, sizeof(T) == 4);
   c.host_syncs += 3;
   std::vector<int> pos(q, -1);
   for (int t = 0; t < (int)sel.size(); ++t) pos[sel[t]] = t;

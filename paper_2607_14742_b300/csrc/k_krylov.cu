@@ -251,6 +251,10 @@ struct SpmmArgs {
   KState* st;
   KHeader* hdr;
   double tol2;
+  // rows per CTA when > 0: CTA b takes the contiguous rows [b chunk, (b+1) chunk)
+  // (its warps interleaved inside), so the neighbours a stencil row gathers were
+  // mostly loaded by the same SM moments before; 0: rows grid-stride over warps
+  long chunk;
 };
 
 template <class T, int TPR, int NVPT, bool CPLX, int NDOT>
@@ -258,6 +262,14 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
   constexpr int VEC = 16 / sizeof(T), NS = NVPT * VEC;
   constexpr int ND = NDOT > 0 ? NDOT : 1;
   RowIter<TPR> it;
+  long row_end = a.n;
+  if (a.chunk > 0) {
+    constexpr int RPW = 32 / TPR;
+    const long r0 = (long)blockIdx.x * a.chunk;
+    it.row = r0 + (long)(threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / TPR;
+    it.stride = (long)(blockDim.x >> 5) * RPW;
+    row_end = r0 + a.chunk < a.n ? r0 + a.chunk : a.n;
+  }
   T acc[ND][NS];
 #pragma unroll
   for (int q = 0; q < ND; ++q)
@@ -265,7 +277,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
     for (int e = 0; e < NS; ++e) acc[q][e] = T(0);
   const T sim = (T)a.sim;
   const bool diff = a.rs != nullptr;
-  for (long row = it.row; row < a.n; row += it.stride) {
+  for (long row = it.row; row < row_end; row += it.stride) {
     const int s = __ldg(a.rp + row), e = __ldg(a.rp + row + 1);
     T y[NVPT][VEC], xi[NVPT][VEC];
 #pragma unroll
@@ -357,9 +369,15 @@ static void launch_spmm(const SpmmArgs<T>& a, cudaStream_t s) {
   int tpr = 1, nvpt = 1;
   spmm_shape(a.nvec, tuned_spmm_vpt(), &tpr, &nvpt);
   const int grid = grid_rows(a.n, tpr);
+  SpmmArgs<T> b = a;
+  b.chunk = 0;
+  if (tuned_spmm_blocked()) {
+    const long step = (long)(kBlock / 32) * (32 / tpr);  // rows per pass of a CTA
+    b.chunk = ((a.n + grid - 1) / grid + step - 1) / step * step;
+  }
 #define CARE_SPMM_CASE(TP, NV)                                                          \
   if (tpr == TP && nvpt == NV) {                                                        \
-    k_spmm<T, TP, NV, CPLX, NDOT><<<grid, kBlock, 0, s>>>(a);                           \
+    k_spmm<T, TP, NV, CPLX, NDOT><<<grid, kBlock, 0, s>>>(b);                           \
     CARE_LAUNCH();                                                                      \
     return;                                                                             \
   }
