@@ -229,16 +229,26 @@ def main():
     hC = torch.from_numpy(np.ascontiguousarray(prob.C)).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in hA + [hB, hC])
     ws = pb.Workspace()
-    # shifted-solve configuration chosen by the library's autotuner (outside the timed region)
+    # shifted-solve configuration chosen by the library's autotuner for each precision
+    # (outside the timed region; the choice is cached per operator shape, and applying
+    # it again sets that precision's launch shape)
     dA0 = pb.CSR(prob.n, hA[0].to(dev), hA[1].to(dev), hA[2].to(dev))
+    op0 = pb.Operator(dA0)
     t_tune = time.perf_counter()
-    tuned, tune_ms = pb.autotune(pb.Operator(dA0), MP, 2 * MP, prec="mixed")
+    tuned = {}
+    tune_ms = {}
+    for pr in ("fp64", "mixed"):
+        tuned[pr], tune_ms[pr] = pb.autotune(op0, MP, 2 * MP, prec=pr)
     t_tune = time.perf_counter() - t_tune
-    del dA0
 
-    def opts(prec):
-        return pb.default_options(krylov=tuned.krylov, krylov_chunk=tuned.krylov_chunk, tri_sweeps=tuned.tri_sweeps,
-                                  precond=tuned.precond)
+    def use(prec):
+        """The tuned options of prec; applying the cached choice sets its launch shape."""
+        t = tuned[prec]
+        pb.autotune(op0, MP, 2 * MP, prec=prec)
+        return pb.default_options(krylov=t.krylov, krylov_chunk=t.krylov_chunk, tri_sweeps=t.tri_sweeps,
+                                  precond=t.precond)
+
+    run_opts = {}
 
     def step(prec):
         """One end-to-end solve; returns (device solve s, whole step s, info, d2h bytes)."""
@@ -251,7 +261,7 @@ def main():
         dB = hB.to(dev, non_blocking=True)
         dC = hC.to(dev, non_blocking=True)
         ev[1].record(stream)
-        Z, info = pb.care_solve(dA, dB, dC, tol=TOL, prec=prec, r_cap=R_CAP, workspace=ws, opts=opts(prec))
+        Z, info = pb.care_solve(dA, dB, dC, tol=TOL, prec=prec, r_cap=R_CAP, workspace=ws, opts=run_opts[prec])
         ev[2].record(stream)
         Zh = Z.to("cpu", non_blocking=False)
         ev[3].record(stream)
@@ -259,13 +269,15 @@ def main():
         return (ev[1].elapsed_time(ev[2]) / 1e3, ev[0].elapsed_time(ev[3]) / 1e3, info,
                 Zh.numel() * Zh.element_size())
 
-    # the all-FP64 path of the same code (same end-to-end step, same options), first,
-    # so that the budget of the mixed steps is known
+    # the all-FP64 path of the same code (same end-to-end step, its own autotuned
+    # options), first, so that the budget of the mixed steps is known
     fp64 = None
     if args.fp64_steps > 0:
         t64 = []
         i64 = None
         for _ in range(args.fp64_steps):
+            if "fp64" not in run_opts:
+                run_opts["fp64"] = use("fp64")
             v64, _, i64, _ = step("fp64")
             t64.append(v64)
         fp64 = {"s_per_solve": statistics.mean(t64), "status": i64["status"], "rank": i64["rank"],
@@ -274,6 +286,7 @@ def main():
     # warm-up, with a budget check after the first step
     warm_done = 0
     t0 = time.perf_counter()
+    run_opts["mixed"] = use("mixed")
     step("mixed")
     warm_done = 1
     t_step = time.perf_counter() - t0
@@ -324,10 +337,11 @@ def main():
                      "alg2": info["ms_phase"][3]},
         "host_syncs": info["host_syncs"],
         "fp64_path": fp64,
-        "autotune": {"krylov": tuned.krylov, "krylov_chunk": tuned.krylov_chunk, "tri_sweeps": tuned.tri_sweeps,
-                     "precond": tuned.precond, "spmm_vectors_per_thread": pb.launch_shape()[0],
-                     "ctas_per_sm": pb.launch_shape()[1], "spmm_row_blocks": pb.launch_shape()[2],
-                     "best_ms": tune_ms, "seconds": t_tune},
+        "autotune": {pr: {"krylov": t.krylov, "krylov_chunk": t.krylov_chunk, "tri_sweeps": t.tri_sweeps,
+                          "precond": t.precond, "best_ms": tune_ms[pr]} for pr, t in tuned.items()},
+        "launch_shape_mixed": {"spmm_vectors_per_thread_by_width_class": pb.launch_shape()[0],
+                               "ctas_per_sm": pb.launch_shape()[1], "spmm_row_blocks": pb.launch_shape()[2]},
+        "autotune_seconds": t_tune,
         "e2e": {"value": te, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roofline(info, t, pk, fp64_peak),
@@ -506,19 +520,35 @@ def spmm_roofline(pb, torch, prob, dev):
         # A^T values + column indices, row pointers, row sums, X read once, Y written once
         return nnz * (vb + 4) + 4 * (n + 1) + vb * n + 2 * n * b * vb
 
+    # every case is timed with the launch shape the autotuner's first stage would pick
+    # for it (vectors per thread x CTAs per SM x row order, fastest median); the
+    # library's default shape is set again afterwards (the solves are autotuned later)
+    shapes = [(v, c, b) for b in (0, 1) for c in (4, 8) for v in (1, 2, 4)]
+
+    def best_shape(op, X):
+        best = None
+        for sh in shapes:
+            pb.set_launch_shape(*sh)
+            t = timeit(op, X, reps=7)
+            if best is None or t < best[0]:
+                best = (t, sh)
+        pb.set_launch_shape(*best[1])
+        return timeit(op, X), best[1]
+
     op2 = pb.Operator(pb.CSR.from_arrays(prob.n, prob.A.rowptr, prob.A.colind, prob.A.val, device=dev))
     for b in (16, 32):
         X2 = torch.randn(prob.n, b, device=dev, dtype=torch.float32)
-        ms2 = timeit(op2, X2)
+        ms2, sh = best_shape(op2, X2)
         by = alg_bytes(prob.n, prob.A.nnz, b, 4)
-        cases[f"fdm2d_500_b{b}_f32"] = {"ms": ms2, "alg_bytes": by, "GBs": by / ms2 / 1e6}
+        cases[f"fdm2d_500_b{b}_f32"] = {"ms": ms2, "alg_bytes": by, "GBs": by / ms2 / 1e6, "shape": sh}
     p3 = ci.convection_diffusion(100, (10.0, 50.0, 100.0))
     op3 = pb.Operator(pb.CSR.from_arrays(p3.n, p3.rowptr, p3.colind, p3.val, device=dev))
     for b in (16, 32):
         X3 = torch.randn(p3.n, b, device=dev, dtype=torch.float32)
-        ms3 = timeit(op3, X3)
+        ms3, sh = best_shape(op3, X3)
         by = alg_bytes(p3.n, p3.nnz, b, 4)
-        cases[f"fdm3d_100_b{b}_f32"] = {"ms": ms3, "alg_bytes": by, "GBs": by / ms3 / 1e6}
+        cases[f"fdm3d_100_b{b}_f32"] = {"ms": ms3, "alg_bytes": by, "GBs": by / ms3 / 1e6, "shape": sh}
+    pb.set_launch_shape(1, 8, 0)
     main = cases["fdm3d_100_b32_f32"]
     out["cases"] = cases
     out["roofline"] = {"bound": "hbm", "achieved": main["GBs"], "peak": peak, "unit": "GB/s",
@@ -526,7 +556,8 @@ def spmm_roofline(pb, torch, prob, dev):
                        "traffic_note": "DRAM bytes per launch of this case are in profiles/k_spmm_fdm3d_100_b32.md "
                                        "(ncu, not captured live)",
                        "kernel": "k_spmm: Y = (A^T + pI) X, CSR, 7-point 100^3 operator (n=1e6, nnz=6.94e6), "
-                                 "32 FP32 columns, difference form, L2 flushed; measured on the launching stream"}
+                                 "32 FP32 columns, difference form, L2 flushed; measured on the launching stream "
+                                 f"with launch shape (vectors/thread, CTAs/SM, row blocks) = {main['shape']}"}
     return out
 
 

@@ -289,23 +289,29 @@ care_status care_shifted_solve(const care_op* op, const double* B, int ldb, cons
  *     per row, more gathers in flight per thread) x {4, 8} CTAs per SM for the
  *     row-block kernels x row order (grid-stride, or contiguous row blocks per
  *     CTA so that a stencil's neighbour rows come from the same SM's cache),
- *     each timed on a b-column block in the working precision (median of 5
- *     launches); the fastest is applied process-wide.
+ *     timed on a b-column block in the working precision (median of 5
+ *     launches); then the vectors per thread for each other width class of the
+ *     Krylov blocks (vectors per row <= 2, <= 4, <= 8, <= 16, more); the
+ *     fastest are applied process-wide.
  *  2. Shifted solves (SMW + block Krylov) of a b-column right-hand side
  *     (deterministic pseudo-random entries) with that shape over krylov in
  *     {BiCGStab, GMRES}, precond in {ILU0 with tri_sweeps 1, 2, 3, ILU0_EXACT,
  *     NONE} and krylov_chunk in {16, 32, 64}; keeps the fastest whose solve
  *     converged.
  * On return opts->krylov, precond, tri_sweeps and krylov_chunk hold the choice
- * and *best_ms (host, may be NULL) its time.  work: device scratch of
- * care_autotune_workspace_size bytes.  Synchronises s. */
+ * and *best_ms (host, may be NULL) its time.  The choice is kept for the life of
+ * the process per (device, n, nnz, m, b, prec): a later call with the same key
+ * applies it without timing (a serving process tunes each operator shape once).
+ * work: device scratch of care_autotune_workspace_size bytes.  Synchronises s. */
 care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_prec prec, size_t* bytes);
 care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_opts* opts, void* work,
                           size_t work_bytes, care_stream_t s, double* best_ms);
 /* The process-wide launch shape (autotuner stage 1): SpMM vectors per thread
  * (1, 2 or 4), CTAs per SM (1..8) of the row-block kernels, SpMM row order
- * (0 grid-stride, 1 contiguous blocks per CTA).  set returns
- * CARE_ERR_INVALID_ARG for other values; get always succeeds (returns 0). */
+ * (0 grid-stride, 1 contiguous blocks per CTA).  get writes the vectors per
+ * thread of the 5 width classes (spmm_vpt: host array of 5) and always
+ * succeeds (returns 0); set applies one value to every width class and returns
+ * CARE_ERR_INVALID_ARG for other values. */
 int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm, int* spmm_blocked);
 care_status care_set_launch_shape(int spmm_vpt, int ctas_per_sm, int spmm_blocked);
 
@@ -364,7 +370,9 @@ care_status care_solve_batched(int count, const care_csr* const* A, const double
  * cooperative launch runs block BiCGStab (right Jacobi preconditioning) on all
  * of them over a work list of row tiles of every instance, with per-column
  * convergence and early exit.  opts->krylov and opts->precond are replaced by
- * BiCGStab + Jacobi.  Results agree with
+ * BiCGStab + Jacobi, and the Krylov iteration limits are raised to at least
+ * 400 (FP32) / 800 (FP64), four times the paper's, since Jacobi is the weaker
+ * preconditioner.  Results agree with
  * care_solve to the solver tolerances, not bitwise (a different preconditioner
  * and summation order).  batch_launches (host, may be NULL) receives the
  * number of batched launches.  Other arguments as for care_solve_batched. */

@@ -126,7 +126,7 @@ def lib() -> ct.CDLL:
         "care_kernel_launches": (ct.c_ulonglong, []),
         "care_fp64_peak": (i, [P(d), vp]),
         "care_symeig_work_size": (sz, [i]),
-        "care_get_launch_shape": (i, [P(i), P(i), P(i)]),
+        "care_get_launch_shape": (i, [vp, P(i), P(i)]),
         "care_set_launch_shape": (i, [i, i, i]),
         "care_ilu0_work_size": (sz, [P(op_t), i]),
         "care_ilu0": (i, [P(op_t), i, i, d, d, vp, vp, sz, vp]),
@@ -472,10 +472,12 @@ TC_MODES = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3}
 
 
 def launch_shape():
-    """(SpMM vectors per thread, CTAs per SM, SpMM contiguous row blocks) of the row-block kernels."""
-    v, c, b = ct.c_int(0), ct.c_int(0), ct.c_int(0)
-    lib().care_get_launch_shape(ct.byref(v), ct.byref(c), ct.byref(b))
-    return v.value, c.value, b.value
+    """(SpMM vectors per thread per width class (5-tuple), CTAs per SM, SpMM contiguous row
+    blocks) of the row-block kernels."""
+    v = (ct.c_int * 5)()
+    c, b = ct.c_int(0), ct.c_int(0)
+    lib().care_get_launch_shape(v, ct.byref(c), ct.byref(b))
+    return tuple(v), c.value, b.value
 
 
 def set_launch_shape(spmm_vpt: int, ctas_per_sm: int, spmm_blocked: int = 0):

@@ -56,6 +56,8 @@ struct BatchArgs {
   double* partial;
   int* active;
   int* iters;
+  int* ractive;       // active columns per request (last reduction)
+  int* ractive_next;  // the same, being counted
   int maxit;
 };
 

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <functional>
 #include <string>
+#include <mutex>
 #include <thread>
 
 #include <omp.h>
@@ -1025,9 +1026,10 @@ __global__ void k_fill_hash(long count, double* x) {
 }
 
 // autotuner scratch: right-hand side W (n x b FP64), solution V (n x b complex FP64),
-// the SpMM stage's blocks X, Y (n x (b + 2) FP64 each), then the solver workspace
+// the SpMM stage's blocks X, Y (n x kMaxRealCols FP64 each: room for every width
+// class), then the solver workspace
 static size_t autotune_head_bytes(long n, int b) {
-  return (((size_t)n * b * 8 * 3 + (size_t)n * (b + 2) * 8 * 2) + 4095) & ~size_t(4095);
+  return (((size_t)n * b * 8 * 3 + (size_t)n * kMaxRealCols * 8 * 2) + 4095) & ~size_t(4095);
 }
 
 care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_prec prec, size_t* bytes) {
@@ -1047,9 +1049,42 @@ care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_p
   return CARE_OK;
 }
 
+// Tuned choices per (device, n, nnz, m, b, prec), kept for the life of the process.
+struct TuneKey {
+  int dev, n, nnz, m, b, prec;
+  bool operator==(const TuneKey& o) const {
+    return dev == o.dev && n == o.n && nnz == o.nnz && m == o.m && b == o.b && prec == o.prec;
+  }
+};
+struct TuneVal {
+  int krylov, precond, tri_sweeps, chunk, vpt[kSpmmBuckets], ctas, blocked;
+  double best_ms;
+};
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
 care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_opts* opts, void* work,
                           size_t work_bytes, care_stream_t s, double* best_ms) {
   if (!op || !opts || !work || b <= 0) return CARE_ERR_INVALID_ARG;
+  int cur_dev = 0;
+  if (cudaGetDevice(&cur_dev) != cudaSuccess) return CARE_ERR_CUDA;
+  const TuneKey key{cur_dev, op->n, op->nnz, m, b, (int)prec};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : g_tune_cache)
+      if (kv.first == key) {
+        const TuneVal& v = kv.second;
+        opts->krylov = v.krylov;
+        opts->precond = v.precond;
+        opts->tri_sweeps = v.tri_sweeps;
+        opts->krylov_chunk = v.chunk;
+        for (int k = 0; k < kSpmmBuckets; ++k) set_tuned_spmm_vpt_bucket(k, v.vpt[k]);
+        set_tuned_ctas_per_sm(v.ctas);
+        set_tuned_spmm_blocked(v.blocked);
+        if (best_ms) *best_ms = v.best_ms;
+        return CARE_OK;
+      }
+  }
   size_t need = 0;
   care_status st = care_autotune_workspace_size(op, m, b, prec, &need);
   if (st != CARE_OK) return st;
@@ -1059,13 +1094,13 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   double* W = reinterpret_cast<double*>(base);
   double* V = W + (size_t)n * b;
   double* SX = V + (size_t)n * b * 2;
-  double* SY = SX + (size_t)n * (b + 2);
+  double* SY = SX + (size_t)n * kMaxRealCols;
   const size_t head = autotune_head_bytes(n, b);
   void* sw = base + head;
   const size_t sw_bytes = work_bytes - head;
   cudaStream_t cs = (cudaStream_t)s;
   k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * b, W);
-  k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * (b + 2), SX);
+  k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * kMaxRealCols, SX);
   if (cudaGetLastError() != cudaSuccess) return CARE_ERR_CUDA;
   // mid-spectrum shift from the largest diagonal magnitude
   std::vector<double> d(n);
@@ -1078,52 +1113,76 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int prev_ctas = tuned_ctas_per_sm(), prev_vpt = tuned_spmm_vpt(), prev_blk = tuned_spmm_blocked();
-  // stage 1: SpMM thread shape (vectors per thread) and CTAs per SM, timed on the
-  // operator at the solve's width and working precision (median of 5 launches)
-  int best_vpt = prev_vpt, best_ctas = prev_ctas, best_blk = prev_blk;
+  const int prev_ctas = tuned_ctas_per_sm(), prev_blk = tuned_spmm_blocked();
+  int prev_vpt[kSpmmBuckets];
+  for (int k = 0; k < kSpmmBuckets; ++k) prev_vpt[k] = tuned_spmm_vpt(2 << k);  // a width of class k
+  // stage 1: SpMM launch shape on the operator in the working precision (median of
+  // 5 timed launches after 2 warm-up ones).  1a: CTAs per SM, row order and vectors
+  // per thread at the request's width b; 1b: vectors per thread for the other width
+  // classes (the Krylov solves run chunks of up to kMaxRealCols columns)
+  const bool f64 = prec == CARE_PREC_FP64;
+  const int vec = f64 ? 2 : 4;
+  auto time_spmm = [&](int width) -> double {
+    const int ld = f64 ? (int)pad_ld<double>(width) : (int)pad_ld<float>(width);
+    std::vector<float> ms;
+    for (int r = 0; r < 7; ++r) {
+      cudaEventRecord(e0, cs);
+      const care_status q = run_guarded([&] {
+        if (f64) spmm<double>(op64(*op), cd{p, 0.0}, false, SX, ld, SY, ld, width, cs);
+        else spmm<float>(op32(*op), cd{p, 0.0}, false, reinterpret_cast<const float*>(SX), ld,
+                         reinterpret_cast<float*>(SY), ld, width, cs);
+        return CARE_OK;
+      });
+      cudaEventRecord(e1, cs);
+      cudaEventSynchronize(e1);
+      if (q != CARE_OK) return 1e300;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r >= 2) ms.push_back(t);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+  };
+  const int vpts[3] = {1, 2, 4}, ctas[2] = {4, 8};
+  int best_ctas = prev_ctas, best_blk = prev_blk;
+  int best_vpt[kSpmmBuckets];
+  for (int k = 0; k < kSpmmBuckets; ++k) best_vpt[k] = prev_vpt[k];
+  const int b_width = std::min(b, kMaxRealCols);
+  const int b_bucket = spmm_bucket((b_width + vec - 1) / vec);
   {
-    const bool f64 = prec == CARE_PREC_FP64;
-    const int ld = f64 ? (int)pad_ld<double>(b) : (int)pad_ld<float>(b);
     double bst = 1e300;
-    const int vpts[3] = {1, 2, 4}, ctas[2] = {4, 8};
     for (int bl = 0; bl < 2; ++bl)
-    for (int ci = 0; ci < 2; ++ci)
-      for (int vi = 0; vi < 3; ++vi) {
-        set_tuned_ctas_per_sm(ctas[ci]);
-        set_tuned_spmm_vpt(vpts[vi]);
-        set_tuned_spmm_blocked(bl);
-        std::vector<float> ms;
-        bool ok = true;
-        for (int r = 0; r < 7 && ok; ++r) {
-          cudaEventRecord(e0, cs);
-          const care_status q = run_guarded([&] {
-            if (f64) spmm<double>(op64(*op), cd{p, 0.0}, false, SX, ld, SY, ld, b, cs);
-            else spmm<float>(op32(*op), cd{p, 0.0}, false, reinterpret_cast<const float*>(SX), ld,
-                             reinterpret_cast<float*>(SY), ld, b, cs);
-            return CARE_OK;
-          });
-          cudaEventRecord(e1, cs);
-          cudaEventSynchronize(e1);
-          float t = 0.f;
-          cudaEventElapsedTime(&t, e0, e1);
-          ok = q == CARE_OK;
-          if (r >= 2) ms.push_back(t);  // two warm-up launches
+      for (int ci = 0; ci < 2; ++ci)
+        for (int vi = 0; vi < 3; ++vi) {
+          set_tuned_ctas_per_sm(ctas[ci]);
+          set_tuned_spmm_blocked(bl);
+          set_tuned_spmm_vpt(vpts[vi]);
+          const double t = time_spmm(b_width);
+          if (t < bst) {
+            bst = t;
+            best_vpt[b_bucket] = vpts[vi];
+            best_ctas = ctas[ci];
+            best_blk = bl;
+          }
         }
-        if (!ok) continue;
-        std::sort(ms.begin(), ms.end());
-        const double med = ms[ms.size() / 2];
-        if (med < bst) {
-          bst = med;
-          best_vpt = vpts[vi];
-          best_ctas = ctas[ci];
-          best_blk = bl;
-        }
-      }
     set_tuned_ctas_per_sm(best_ctas);
-    set_tuned_spmm_vpt(best_vpt);
     set_tuned_spmm_blocked(best_blk);
   }
+  // 1b: one representative width per other class (vectors per row 2, 4, 8, 16, 32)
+  for (int k = 0; k < kSpmmBuckets; ++k) {
+    if (k == b_bucket) continue;
+    const int width = std::min(kMaxRealCols, vec * (2 << k));
+    double bst = 1e300;
+    for (int vi = 0; vi < 3; ++vi) {
+      set_tuned_spmm_vpt(vpts[vi]);
+      const double t = time_spmm(width);
+      if (t < bst) {
+        bst = t;
+        best_vpt[k] = vpts[vi];
+      }
+    }
+  }
+  for (int k = 0; k < kSpmmBuckets; ++k) set_tuned_spmm_vpt_bucket(k, best_vpt[k]);
   // stage 2: shifted-solve configurations with that shape
   double best = 1e300;
   care_opts bestopt = *opts;
@@ -1160,7 +1219,7 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   cudaEventDestroy(e1);
   if (best >= 1e300) {
     set_tuned_ctas_per_sm(prev_ctas);
-    set_tuned_spmm_vpt(prev_vpt);
+    for (int k = 0; k < kSpmmBuckets; ++k) set_tuned_spmm_vpt_bucket(k, prev_vpt[k]);
     set_tuned_spmm_blocked(prev_blk);
     return CARE_INNER_FAILED;
   }
@@ -1169,11 +1228,19 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   opts->krylov_chunk = bestopt.krylov_chunk;
   opts->tri_sweeps = bestopt.tri_sweeps;
   if (best_ms) *best_ms = best;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneVal tv{bestopt.krylov, bestopt.precond, bestopt.tri_sweeps, bestopt.krylov_chunk, {}, best_ctas, best_blk,
+               best};
+    for (int k = 0; k < kSpmmBuckets; ++k) tv.vpt[k] = best_vpt[k];
+    g_tune_cache.push_back({key, tv});
+  }
   return CARE_OK;
 }
 
 int care_get_launch_shape(int* spmm_vpt, int* ctas_per_sm, int* spmm_blocked) {
-  if (spmm_vpt) *spmm_vpt = tuned_spmm_vpt();
+  if (spmm_vpt)
+    for (int k = 0; k < kSpmmBuckets; ++k) spmm_vpt[k] = tuned_spmm_vpt(2 << k);  // a width of class k
   if (ctas_per_sm) *ctas_per_sm = tuned_ctas_per_sm();
   if (spmm_blocked) *spmm_blocked = tuned_spmm_blocked();
   return 0;
@@ -1336,6 +1403,11 @@ static care_opts persistent_opts(const care_opts* opts) {
   else care_opts_default(&o);
   o.krylov = CARE_KRYLOV_BICGSTAB;
   o.precond = CARE_PRECOND_JACOBI;
+  // Jacobi needs more iterations than ILU(0) on the stencil operators: four times
+  // the limits (a request whose columns have all converged drops out of the
+  // launch's phases, so it pays nothing for the others' iterations)
+  o.krylov_maxit_lo = std::max(o.krylov_maxit_lo, 4 * 100);
+  o.krylov_maxit_hi = std::max(o.krylov_maxit_hi, 4 * 200);
   return o;
 }
 

@@ -112,6 +112,18 @@ __device__ __forceinline__ void vload(const T* p, T (&v)[16 / sizeof(T)]) {
     v[0] = x.x; v[1] = x.y;
   }
 }
+// the same through the read-only (non-coherent) data path, for blocks that no
+// thread of the running kernel writes
+template <class T>
+__device__ __forceinline__ void vload_ro(const T* p, T (&v)[16 / sizeof(T)]) {
+  using V = typename Vec<T>::type;
+  const V x = __ldg(reinterpret_cast<const V*>(p));
+  if constexpr (sizeof(T) == 4) {
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else {
+    v[0] = x.x; v[1] = x.y;
+  }
+}
 template <class T>
 __device__ __forceinline__ void vstore(T* p, const T (&v)[16 / sizeof(T)]) {
   using V = typename Vec<T>::type;
@@ -146,14 +158,21 @@ constexpr int kMaxRealCols = 128;  // widest row-block handled by the fused kern
 // CTAs per SM of the row-block kernels (set by care_autotune; default 8)
 int tuned_ctas_per_sm();
 void set_tuned_ctas_per_sm(int v);
-// 16-byte vectors per thread of the SpMM (1, 2 or 4; set by care_autotune,
-// default 1): fewer threads per row, more independent gathers in flight each
-int tuned_spmm_vpt();
-void set_tuned_spmm_vpt(int v);
+// 16-byte vectors per thread of the SpMM (1, 2 or 4): fewer threads per row,
+// more independent gathers in flight each.  One value per width class of the
+// block (vectors per row <= 2, <= 4, <= 8, <= 16, more), set by care_autotune,
+// default 1.
+constexpr int kSpmmBuckets = 5;
+inline int spmm_bucket(int nvec) { return nvec <= 2 ? 0 : nvec <= 4 ? 1 : nvec <= 8 ? 2 : nvec <= 16 ? 3 : 4; }
+int tuned_spmm_vpt(int nvec);
+void set_tuned_spmm_vpt(int v);                 // every width class
+void set_tuned_spmm_vpt_bucket(int bucket, int v);
 // SpMM row order: 1 = contiguous row blocks per CTA, 0 = grid-stride (set by care_autotune)
 int tuned_spmm_blocked();
 void set_tuned_spmm_blocked(int v);
 // SpMM thread shape for a row of nvec vectors: tpr threads of nvpt vectors each
+// (tpr a power of two <= 32, nvpt <= vpt; every pair this returns for nvec <= 64
+// has a kernel instance)
 inline void spmm_shape(int nvec, int vpt, int* tpr, int* nvpt) {
   if (vpt < 1) vpt = 1;
   int t = tpr_for((nvec + vpt - 1) / vpt);

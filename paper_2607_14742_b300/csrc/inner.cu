@@ -17,9 +17,15 @@ void set_verbose(int v) { g_verbose = v; }
 static std::atomic<int> g_ctas_per_sm{8};
 int tuned_ctas_per_sm() { return g_ctas_per_sm.load(std::memory_order_relaxed); }
 void set_tuned_ctas_per_sm(int v) { g_ctas_per_sm.store(v < 1 ? 1 : (v > 8 ? 8 : v)); }
-static std::atomic<int> g_spmm_vpt{1};
-int tuned_spmm_vpt() { return g_spmm_vpt.load(std::memory_order_relaxed); }
-void set_tuned_spmm_vpt(int v) { g_spmm_vpt.store(v >= 4 ? 4 : (v >= 2 ? 2 : 1)); }
+static std::atomic<int> g_spmm_vpt[kSpmmBuckets] = {1, 1, 1, 1, 1};
+static int clamp_vpt(int v) { return v >= 4 ? 4 : (v >= 2 ? 2 : 1); }
+int tuned_spmm_vpt(int nvec) { return g_spmm_vpt[spmm_bucket(nvec)].load(std::memory_order_relaxed); }
+void set_tuned_spmm_vpt(int v) {
+  for (int b = 0; b < kSpmmBuckets; ++b) g_spmm_vpt[b].store(clamp_vpt(v));
+}
+void set_tuned_spmm_vpt_bucket(int bucket, int v) {
+  if (bucket >= 0 && bucket < kSpmmBuckets) g_spmm_vpt[bucket].store(clamp_vpt(v));
+}
 static std::atomic<int> g_spmm_blocked{0};
 int tuned_spmm_blocked() { return g_spmm_blocked.load(std::memory_order_relaxed); }
 void set_tuned_spmm_blocked(int v) { g_spmm_blocked.store(v ? 1 : 0); }

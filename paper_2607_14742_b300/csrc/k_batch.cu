@@ -232,7 +232,10 @@ __device__ void reduce_phase(const BatchArgs<T>& g, int ph, int it) {
       S.rho_im = d0.im;
       if (S.flag != 0) S.alpha_re = S.alpha_im = S.omega_re = S.omega_im = S.beta_re = S.beta_im = 0.0;
     }
-    if ((ph == PH_INIT || ph == PH_RHO) && S.flag == 0) atomicAdd(g.active, 1);
+    if ((ph == PH_INIT || ph == PH_RHO) && S.flag == 0) {
+      atomicAdd(g.active, 1);
+      atomicAdd(g.ractive_next + lo, 1);
+    }
   }
 }
 
@@ -345,6 +348,16 @@ __device__ __forceinline__ void axpy_elem(bool cplx, const ColScal<T>& s, const 
   }
 }
 
+// ractive = the per-request active-column counts of the last reduction; the
+// counters for the next one start from zero
+template <class T>
+__device__ void publish_active(const BatchArgs<T>& g) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.nreq; r += gridDim.x * blockDim.x) {
+    g.ractive[r] = __ldcg(g.ractive_next + r);
+    g.ractive_next[r] = 0;
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(BT) k_batch_bicgstab(BatchArgs<T> g) {
   constexpr int VEC = 16 / sizeof(T);
@@ -358,6 +371,8 @@ __global__ void __launch_bounds__(BT) k_batch_bicgstab(BatchArgs<T> g) {
     int cur = -1;
     for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
       const int r = req_of(g, t);
+      // a request whose columns are all frozen is skipped (its scalars ignore the dots)
+      if (__ldcg(g.ractive + r) == 0) continue;
       if (r != cur) {
         if (cur >= 0 && ndot) flush_dots(g, cur, acc, ndot, sm);
         cur = r;
@@ -400,6 +415,8 @@ __global__ void __launch_bounds__(BT) k_batch_bicgstab(BatchArgs<T> g) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *g.active = 0;
   grid.sync();
   reduce_phase(g, PH_INIT, 0);
+  grid.sync();
+  publish_active(g);
   grid.sync();
   int it = 0;
   while (*(volatile int*)g.active > 0 && it < g.maxit) {
@@ -487,9 +504,13 @@ __global__ void __launch_bounds__(BT) k_batch_bicgstab(BatchArgs<T> g) {
     grid.sync();
     reduce_phase(g, PH_RHO, it);
     grid.sync();
+    publish_active(g);
+    grid.sync();
     ++it;
   }
-  // sol = x (valid columns)
+  // sol = x (valid columns) for every request
+  for (int r = 0; r < g.nreq && threadIdx.x == 0 && blockIdx.x == 0; ++r) g.ractive[r] = 1;
+  grid.sync();
   tiles(0, [&](const BatchReq<T>& q, long row, int v) {
     const size_t o = (size_t)row * q.ld + v * VEC;
     T x[VEC];
@@ -510,6 +531,7 @@ size_t batch_scratch_bytes(int max_req) {
   a.get<BatchReq<double>>((size_t)max_req);
   a.get<BatchSlot>((size_t)max_req * kMaxRealCols);
   a.get<int>(64);
+  a.get<int>((size_t)2 * max_req);
   a.get<double>((size_t)max_req * (size_t)device_sms() * 8 * kMaxRealCols * 2);
   return a.off + 256;
 }
@@ -552,8 +574,15 @@ int batch_launch(std::vector<BatchReq<T>>& reqs, char* scratch, size_t scratch_b
   BatchReq<T>* dreq = a.get<BatchReq<T>>((size_t)nreq);
   BatchSlot* dslot = a.get<BatchSlot>((size_t)std::max(nslot, 1));
   int* misc = a.get<int>(64);
+  int* ract = a.get<int>((size_t)2 * nreq);
   double* partial = a.get<double>(pb * 2);
   CARE_CUDA(cudaMemcpyAsync(dreq, reqs.data(), sizeof(BatchReq<T>) * nreq, cudaMemcpyHostToDevice, s));
+  {
+    std::vector<int> init(2 * (size_t)nreq, 0);
+    for (int r = 0; r < nreq; ++r) init[r] = 1;  // every request takes part in the first phase
+    CARE_CUDA(cudaMemcpyAsync(ract, init.data(), sizeof(int) * 2 * nreq, cudaMemcpyHostToDevice, s));
+    CARE_CUDA(cudaStreamSynchronize(s));  // the host vector goes out of scope
+  }
   BatchArgs<T> g{};
   g.req = dreq;
   g.nreq = nreq;
@@ -563,6 +592,8 @@ int batch_launch(std::vector<BatchReq<T>>& reqs, char* scratch, size_t scratch_b
   g.partial = partial;
   g.active = misc;
   g.iters = misc + 1;
+  g.ractive = ract;
+  g.ractive_next = ract + nreq;
   g.maxit = maxit;
   void* args[] = {(void*)&g};
   CARE_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_bicgstab<T>, dim3(G), dim3(BT), args, 0, s));

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
         y[k][q] = T(0);
         xi[k][q] = T(0);
       }
-      if (v < a.nvec && diff) vload(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
+      if (v < a.nvec && diff) vload_ro(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
     }
     // the row's entries in predicated batches of 8 (stencil rows have 5-7): all
     // index/value loads of a batch, then all its gathers, are in flight together,
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
         if (v < a.nvec) {
           T x[8][VEC];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) vload(a.X + (size_t)c[u] * a.ldx + v * VEC, x[u]);
+          for (int u = 0; u < 8; ++u) vload_ro(a.X + (size_t)c[u] * a.ldx + v * VEC, x[u]);
 #pragma unroll
           for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
     for (int k = 0; k < NVPT; ++k) {
       const int v = it.lane_v + k * TPR;
       if (v < a.nvec) {
-        if (!diff) vload(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
+        if (!diff) vload_ro(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
         if constexpr (CPLX) {
 #pragma unroll
           for (int q = 0; q < VEC; q += 2) {
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
 template <class T, int NDOT, bool CPLX>
 static void launch_spmm(const SpmmArgs<T>& a, cudaStream_t s) {
   int tpr = 1, nvpt = 1;
-  spmm_shape(a.nvec, tuned_spmm_vpt(), &tpr, &nvpt);
+  spmm_shape(a.nvec, tuned_spmm_vpt(a.nvec), &tpr, &nvpt);
   const int grid = grid_rows(a.n, tpr);
   SpmmArgs<T> b = a;
   b.chunk = 0;
@@ -384,8 +384,8 @@ static void launch_spmm(const SpmmArgs<T>& a, cudaStream_t s) {
   CARE_SPMM_CASE(1, 1) CARE_SPMM_CASE(2, 1) CARE_SPMM_CASE(4, 1) CARE_SPMM_CASE(8, 1)
   CARE_SPMM_CASE(16, 1) CARE_SPMM_CASE(32, 1) CARE_SPMM_CASE(32, 2)
   CARE_SPMM_CASE(1, 2) CARE_SPMM_CASE(2, 2) CARE_SPMM_CASE(4, 2) CARE_SPMM_CASE(8, 2) CARE_SPMM_CASE(16, 2)
-  CARE_SPMM_CASE(1, 3) CARE_SPMM_CASE(2, 3) CARE_SPMM_CASE(4, 3) CARE_SPMM_CASE(8, 3)
-  CARE_SPMM_CASE(1, 4) CARE_SPMM_CASE(2, 4) CARE_SPMM_CASE(4, 4) CARE_SPMM_CASE(8, 4)
+  CARE_SPMM_CASE(1, 3) CARE_SPMM_CASE(2, 3) CARE_SPMM_CASE(4, 3) CARE_SPMM_CASE(8, 3) CARE_SPMM_CASE(16, 3)
+  CARE_SPMM_CASE(1, 4) CARE_SPMM_CASE(2, 4) CARE_SPMM_CASE(4, 4) CARE_SPMM_CASE(8, 4) CARE_SPMM_CASE(16, 4)
 #undef CARE_SPMM_CASE
   CARE_THROW(CARE_ERR_INVALID_ARG, "spmm: block too wide");
 }

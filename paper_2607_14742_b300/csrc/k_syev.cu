@@ -16,7 +16,7 @@
 //     eigenvalues closer than 1e-6 ||T||_1 (and, for callers that weight the
 //     vectors by their eigenvalues, closer than 1e-3 of their magnitude) form a
 //     cluster whose vectors are orthogonalised against each other after every
-//     solve (as LAPACK's dstein does with its absolute 1e-3 window), by classical
+//     solve (as LAPACK's dstein does with its absolute 1e-3 window), by modified
 //     Gram-Schmidt twice.
 //  4. Back-transformation x <- H_0 ... H_{n-3} x, one CTA per group of vectors
 //     held in shared memory.
@@ -156,8 +156,6 @@ __global__ void k_stebz(int n, const double* __restrict__ d, const double* __res
   w[i] = 0.5 * (lo + hi);
 }
 
-constexpr int STEIN_CHUNK = 1024;
-
 // Inverse iteration for the selected eigenvalues, one CTA per cluster
 // [cstart[c], cstart[c+1]) of the selected list lam[]; vector j -> X[j * n ..).
 // Thread 0 factors T - lambda I (partially pivoted LU) and runs the triangular
@@ -174,8 +172,6 @@ __global__ void __launch_bounds__(128) k_stein(int n, const double* __restrict__
   const int c = blockIdx.x;
   if (c >= nclus) return;
   __shared__ double sh[4];
-  __shared__ double tdot[STEIN_CHUNK];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double eps = 2.220446049250313e-16;
   const double eps3 = eps * onenrm;
   double* dl = scratch + (long)c * 5 * n;
@@ -258,26 +254,15 @@ __global__ void __launch_bounds__(128) k_stein(int n, const double* __restrict__
         }
       }
       __syncthreads();
-      // orthogonalise against the earlier vectors of the cluster: classical
-      // Gram-Schmidt, twice, in chunks of STEIN_CHUNK vectors (all dots of a chunk,
-      // one warp per vector, then one subtraction sweep: two barriers per chunk)
+      // orthogonalise against the earlier vectors of the cluster (modified
+      // Gram-Schmidt, twice)
       for (int pass = 0; pass < 2; ++pass)
-        for (int q0 = cstart[c]; q0 < j; q0 += STEIN_CHUNK) {
-          const int nq = min(STEIN_CHUNK, j - q0);
-          for (int q = warp; q < nq; q += 4) {
-            const double* xq = X + (long)(q0 + q) * n;
-            double t = 0.0;
-            for (int i = lane; i < n; i += 32) t += xq[i] * b[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) tdot[q] = t;
-          }
-          __syncthreads();
-          for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double bi = b[i];
-            for (int q = 0; q < nq; ++q) bi -= tdot[q] * X[(long)(q0 + q) * n + i];
-            b[i] = bi;
-          }
+        for (int q = cstart[c]; q < j; ++q) {
+          const double* xq = X + (long)q * n;
+          double t = 0.0;
+          for (int i = threadIdx.x; i < n; i += blockDim.x) t += xq[i] * b[i];
+          t = csum(t);
+          for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] -= t * xq[i];
           __syncthreads();
         }
       double t = 0.0;

@@ -69,11 +69,14 @@ def test_batched_persistent_uneven_many(pb):
     instance converges and agrees with its own single FP64 solve to 1e-8."""
     probs = ci.config_batched(count=16, side_lo=8, side_hi=40, mp_hi=8)
     dev = [(pb.CSR.from_arrays(p.n, p.A.rowptr, p.A.colind, p.A.val), p.B, p.C) for p in probs]
-    Zb, infos, st = pb.care_solve_batched(dev, tol=1e-10, prec="mixed", r_cap=400, persistent=True, allow=(5, 6))
+    o = pb.default_options(adi_cap=512)  # small instances: a smaller ADI buffer keeps the workspace small
+    Zb, infos, st = pb.care_solve_batched(dev, tol=1e-10, prec="mixed", r_cap=400, persistent=True, allow=(5, 6),
+                                          opts=o)
     summary = [(p.name, p.B.shape[1], p.C.shape[0], inf["status"], inf["res_rel_CtC"], inf["iter"])
                for p, inf in zip(probs, infos)]
+    bad = [t for t in summary if not t[4] <= 1e-10]
+    assert not bad, bad
     for (A, B, C), p, Z, inf in zip(dev, probs, Zb, infos):
-        assert inf["res_rel_CtC"] <= 1e-10, summary
         Zi, _ = pb.care_solve(A, B, C, tol=1e-10, prec="fp64", r_cap=400)
         Zh, Zih = Z.cpu().numpy(), Zi.cpu().numpy()
         Xi = Zih @ Zih.T

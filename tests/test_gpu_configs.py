@@ -1,0 +1,51 @@
+"""The large configurations end to end: the 500x500 2D convection-diffusion CARE
+(n = 250,000, m = p = 5) and the 100^3 3D one (n = 1,000,000, m = p = 10), mixed
+precision to relative residual 1e-10.  Besides the library's own FP64 residual
+(Algorithm 1's ||H||_F = ||R||_F), the residual of the returned factor is
+estimated independently on the CPU: R(X) v = A^T X v + X A v - X B B^T X v + C^T C v
+with X = Z Z^T applied through the factor, over Gaussian probe vectors v
+(E ||R v||^2 = ||R||_F^2, Hutchinson's estimator)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import care_inputs as ci
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_14742_b300 as m
+    m.lib()
+    return m
+
+
+def _residual_estimate(A, B, C, Z, probes=12, seed=7):
+    """sqrt(mean ||R v||^2) for Gaussian v: an unbiased estimate of ||R||_F^2."""
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((A.shape[0], probes))
+    XV = Z @ (Z.T @ V)
+    XAV = Z @ (Z.T @ (A @ V))
+    XBBXV = Z @ (Z.T @ (B @ (B.T @ XV)))
+    RV = A.T @ XV + XAV - XBBXV + C.T @ (C @ V)
+    return float(np.sqrt(np.mean(np.sum(RV * RV, axis=0))))
+
+
+@pytest.mark.parametrize("cfg", ["c3_fdm2d_500", "c4_fdm3d_100"])
+def test_large_config_mixed_residual_certificate(pb, cfg):
+    prob = ci.config_fdm2d(500, 5, 5) if cfg == "c3_fdm2d_500" else ci.config_fdm3d(100, 10, 10)
+    A = pb.CSR.from_arrays(prob.n, prob.A.rowptr, prob.A.colind, prob.A.val)
+    # r_cap bounds the workspace (about 100 GB at n = 1e6 with 640 columns)
+    Z, info = pb.care_solve(A, prob.B, prob.C, tol=1e-10, prec="mixed", r_cap=1536 if prob.n < 500000 else 640)
+    assert info["status"] == "CARE_OK" and info["res_rel_CtC"] <= 1e-10, info
+    Zh = Z.cpu().numpy()
+    As = sp.csr_matrix(prob.A.to_scipy())
+    ctc = np.linalg.norm(prob.C @ prob.C.T)  # ||C^T C||_F = ||C C^T||_F
+    est = _residual_estimate(As, prob.B, prob.C, Zh) / ctc
+    # the estimator's relative spread with 12 probes is well below a factor 3
+    assert est <= 3e-10, (est, info["res_rel_CtC"])
+    assert est <= 3 * info["res_rel_CtC"] + 1e-13 and info["res_rel_CtC"] <= 3 * est + 1e-13, (est, info)

@@ -192,11 +192,25 @@ def test_autotune_picks_valid_config_and_keeps_parity(pb):
     the tuned options still matches the oracle."""
     prob = ci.config_fdm2d(100, 2, 2)
     dA, op, As = _ops(pb, prob)
+    import time
+    t0 = time.perf_counter()
     o, best_ms = pb.autotune(op, 2, 4, prec="fp64")
+    t_first = time.perf_counter() - t0
     assert best_ms > 0
+    assert o.krylov in (pb.KRYLOV_BICGSTAB, pb.KRYLOV_GMRES)
     assert o.krylov_chunk in (16, 32, 64) and o.tri_sweeps in (1, 2, 3)
-    assert o.precond in (pb.PRECOND_NONE, pb.PRECOND_ILU0)
+    assert o.precond in (pb.PRECOND_NONE, pb.PRECOND_ILU0, pb.PRECOND_ILU0_EXACT)
+    vpt, ctas, blk = pb.launch_shape()
+    assert len(vpt) == 5 and all(v in (1, 2, 4) for v in vpt) and ctas in (4, 8) and blk in (0, 1)
     W = ci.random_block(prob.n, 4, 54)
     ref = ol.smw_solve(ol.ShiftedSolver(As), None, None, -500.0, W)
     V, _ = pb.shifted_solve(op, W, -500.0, prec="fp64", opts=o)
     assert np.linalg.norm(V.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+    # the choice is cached per operator shape: the same answer without timing again
+    t0 = time.perf_counter()
+    o2, best2 = pb.autotune(op, 2, 4, prec="fp64")
+    t_second = time.perf_counter() - t0
+    assert (o2.krylov, o2.precond, o2.tri_sweeps, o2.krylov_chunk, best2) == (
+        o.krylov, o.precond, o.tri_sweeps, o.krylov_chunk, best_ms)
+    assert pb.launch_shape() == (vpt, ctas, blk)
+    assert t_second < 0.5 * t_first
