@@ -133,13 +133,15 @@ typedef struct {
   int ilu_sweeps;        /* ILU(0) fixed-point sweeps per shift (CARE_PRECOND_ILU0)  */
   int tri_sweeps;        /* Jacobi sweeps per triangular factor in the ILU(0) apply  */
   int verbose;           /* 0 silent, 1 per outer step, 2 per ADI step (stderr)      */
-  int inner_compress;    /* FP32 inner solves only.  0 (default): the +/- correction  */
-                         /* factors go to Algorithm 2 as computed, compressed in u_s */
-                         /* only when their capacity is reached; 1: also compress    */
-                         /* them at the end of the solve when wider than             */
-                         /* max(2b, 512) (cheaper Algorithm 2, but a u_s truncation  */
-                         /* relative to ||X_+-|| slows the refinement).  FP64 inner  */
-                         /* factors are always compressed (at FP64 accuracy).        */
+  int inner_compress;    /* FP32 inner solves only (default 2).  0: the +/- factors   */
+                         /* go to Algorithm 2 as computed (jointly compressed only   */
+                         /* when their capacity is reached); 1: also compress each   */
+                         /* sign group at the end when wider than max(2b, 512) (a    */
+                         /* u_s truncation relative to ||X_+-||, which can slow the  */
+                         /* refinement); 2: compress X_+ - X_- jointly in FP64 at    */
+                         /* the end, truncated at 1e-8 relative to the correction    */
+                         /* itself.  FP64 inner factors are always compressed (at    */
+                         /* FP64 accuracy).                                          */
   int gmres_restart_lo;  /* GMRES restart length, FP32 solves (Section 5.2: 30)      */
   int gmres_restart_hi;  /* GMRES restart length, FP64 solves (Section 5.2: 50)      */
 } care_opts;
@@ -293,13 +295,14 @@ care_status care_shifted_solve(const care_op* op, const double* B, int ldb, cons
  *     launches); then the vectors per thread for each other width class of the
  *     Krylov blocks (vectors per row <= 2, <= 4, <= 8, <= 16, more); the
  *     fastest are applied process-wide.
- *  2. Shifted solves (SMW + block Krylov) of a b-column right-hand side
- *     (deterministic pseudo-random entries) with that shape over krylov in
- *     {BiCGStab, GMRES}, precond in {ILU0 with tri_sweeps 1, 2, 3, ILU0_EXACT,
- *     NONE} and krylov_chunk in {16, 32, 64}; keeps the fastest whose solve
- *     converged.
+ *  2. Shifted solves (SMW + block Krylov) of a b-column and a 128-column
+ *     right-hand side (deterministic pseudo-random entries; the wide one is where
+ *     the chunking matters) with that shape over krylov in {BiCGStab, GMRES},
+ *     precond in {ILU0 with tri_sweeps 2, 3, ILU0_EXACT, NONE} and krylov_chunk
+ *     in {32, 64}; keeps the configuration with the smallest total time whose
+ *     solves converged.
  * On return opts->krylov, precond, tri_sweeps and krylov_chunk hold the choice
- * and *best_ms (host, may be NULL) its time.  The choice is kept for the life of
+ * and *best_ms (host, may be NULL) its total time.  The choice is kept for the life of
  * the process per (device, n, nnz, m, b, prec): a later call with the same key
  * applies it without timing (a serving process tunes each operator shape once).
  * work: device scratch of care_autotune_workspace_size bytes.  Synchronises s. */

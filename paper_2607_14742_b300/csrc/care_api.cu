@@ -670,9 +670,10 @@ static care_status solve_impl(Ctx& c, const care_csr* A, const double* B, int ld
     t1 = now_ms();
     const int bw = a1.rp + a1.rm;
     // FP64 inner factors are compressed at FP64 accuracy (harmless before Algorithm 2's own
-    // truncation at 10u); FP32 ones only if asked, since a u_s truncation relative to
-    // ||X_+-|| can exceed the correction X_+ - X_- itself
-    const bool cmp = sizeof(T) == 8 || c.o.inner_compress != 0;
+    // truncation at 10u); FP32 ones as asked (inner_compress): a per-sign u_s truncation
+    // relative to ||X_+-|| can exceed the correction X_+ - X_- itself, the joint one is
+    // relative to the correction
+    const int cmp = sizeof(T) == 8 ? 1 : c.o.inner_compress;
     AdiResult ad = lradi<T>(c, S.in, bw, a1.rp, true, tauL, c.o.jmax, false, cmp);
     inf.iter_inner += ad.steps;
     CARE_CUDA(cudaStreamSynchronize(c.s));
@@ -899,7 +900,7 @@ void care_opts_default(care_opts* o) {
   o->ilu_sweeps = 3;
   o->tri_sweeps = 2;
   o->verbose = 0;
-  o->inner_compress = 0;
+  o->inner_compress = 2;
   o->gmres_restart_lo = 30;
   o->gmres_restart_hi = 50;
 }
@@ -1025,11 +1026,17 @@ __global__ void k_fill_hash(long count, double* x) {
   }
 }
 
-// autotuner scratch: right-hand side W (n x b FP64), solution V (n x b complex FP64),
-// the SpMM stage's blocks X, Y (n x kMaxRealCols FP64 each: room for every width
-// class), then the solver workspace
+// Stage 2 times every configuration on two right-hand sides: the request's width b
+// and a wide block of kTuneWide columns, where the Krylov chunking matters (the
+// correction solves of the refinement have hundreds of columns).
+constexpr int kTuneWide = 128;
+static int tune_wb(int b) { return std::max(b, kTuneWide); }
+
+// autotuner scratch: right-hand side W (n x max(b, kTuneWide) FP64), solution V
+// (the same, complex FP64), the SpMM stage's blocks X, Y (n x kMaxRealCols FP64
+// each: room for every width class), then the solver workspace
 static size_t autotune_head_bytes(long n, int b) {
-  return (((size_t)n * b * 8 * 3 + (size_t)n * kMaxRealCols * 8 * 2) + 4095) & ~size_t(4095);
+  return (((size_t)n * tune_wb(b) * 8 * 3 + (size_t)n * kMaxRealCols * 8 * 2) + 4095) & ~size_t(4095);
 }
 
 care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_prec prec, size_t* bytes) {
@@ -1041,7 +1048,7 @@ care_status care_autotune_workspace_size(const care_op* op, int m, int b, care_p
     o.precond = CARE_PRECOND_ILU0_EXACT;  // the ILU workspace of both ILU(0) variants
     o.krylov = kr == 0 ? CARE_KRYLOV_BICGSTAB : CARE_KRYLOV_GMRES;
     size_t sk = 0;
-    care_status st = care_shifted_solve_workspace_size(op, std::max(m, 1), b, prec, &o, &sk);
+    care_status st = care_shifted_solve_workspace_size(op, std::max(m, 1), tune_wb(b), prec, &o, &sk);
     if (st != CARE_OK) return st;
     s1 = std::max(s1, sk);
   }
@@ -1091,15 +1098,16 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   if (work_bytes < need) return CARE_ERR_WORKSPACE;
   const long n = op->n;
   char* base = static_cast<char*>(work);
+  const int wb = tune_wb(b);
   double* W = reinterpret_cast<double*>(base);
-  double* V = W + (size_t)n * b;
-  double* SX = V + (size_t)n * b * 2;
+  double* V = W + (size_t)n * wb;
+  double* SX = V + (size_t)n * wb * 2;
   double* SY = SX + (size_t)n * kMaxRealCols;
   const size_t head = autotune_head_bytes(n, b);
   void* sw = base + head;
   const size_t sw_bytes = work_bytes - head;
   cudaStream_t cs = (cudaStream_t)s;
-  k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * b, W);
+  k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * wb, W);
   k_fill_hash<<<device_sms() * 4, 256, 0, cs>>>((long)n * kMaxRealCols, SX);
   if (cudaGetLastError() != cudaSuccess) return CARE_ERR_CUDA;
   // mid-spectrum shift from the largest diagonal magnitude
@@ -1186,32 +1194,39 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   // stage 2: shifted-solve configurations with that shape
   double best = 1e300;
   care_opts bestopt = *opts;
-  const int chunks[3] = {16, 32, 64};
+  const int chunks[2] = {32, 64};
   struct Pc {
     int precond, sweeps;
   };
-  const Pc pcs[5] = {{CARE_PRECOND_ILU0, 1}, {CARE_PRECOND_ILU0, 2}, {CARE_PRECOND_ILU0, 3},
-                     {CARE_PRECOND_ILU0_EXACT, 1}, {CARE_PRECOND_NONE, 1}};
+  const Pc pcs[4] = {{CARE_PRECOND_ILU0, 2}, {CARE_PRECOND_ILU0, 3}, {CARE_PRECOND_ILU0_EXACT, 1},
+                     {CARE_PRECOND_NONE, 1}};
   for (int kr = 0; kr < 2; ++kr)
-    for (int pc = 0; pc < 5; ++pc)
-      for (int ki = 0; ki < 3; ++ki) {
+    for (int pc = 0; pc < 4; ++pc)
+      for (int ki = 0; ki < 2; ++ki) {
         care_opts o = *opts;
         o.krylov = kr == 0 ? CARE_KRYLOV_BICGSTAB : CARE_KRYLOV_GMRES;
         o.precond = pcs[pc].precond;
         o.tri_sweeps = pcs[pc].sweeps;
         o.krylov_chunk = chunks[ki];
-        int iters = 0;
-        // one untimed run (graph capture, caches), one timed run
-        care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw, sw_bytes, s, &iters);
-        cudaEventRecord(e0, cs);
-        care_status r = care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, b, prec, &o, V, n, sw,
-                                           sw_bytes, s, &iters);
-        cudaEventRecord(e1, cs);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (r == CARE_OK && ms < best) {
-          best = ms;
+        double tot = 0.0;
+        bool ok = true;
+        for (const int width : {b, kTuneWide}) {
+          int iters = 0;
+          // one untimed run (graph capture, caches), one timed run
+          care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, width, prec, &o, V, n, sw, sw_bytes, s,
+                             &iters);
+          cudaEventRecord(e0, cs);
+          care_status r = care_shifted_solve(op, nullptr, n, nullptr, n, 0, p, 0.0, W, n, width, prec, &o, V, n,
+                                             sw, sw_bytes, s, &iters);
+          cudaEventRecord(e1, cs);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ok = ok && r == CARE_OK;
+          tot += ms;
+        }
+        if (ok && tot < best) {
+          best = tot;
           bestopt = o;
         }
       }

@@ -625,7 +625,7 @@ static bool compress_joint(Ctx& c, Inner<T>& in, int& np, int& nm) {
 
 template <class T>
 AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew,
-                bool compress_end) {
+                int compress_end) {
   AdiResult res;
   const long n = in.n;
   const int rm = b - rp;
@@ -710,9 +710,23 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
     if (verbose_level() >= 2)
       fprintf(stderr, "[care]   adi j=%d p=(%.4e,%.4e) res=%.3e cols=%d+%d\n", j, p.re, p.im, r, np, nm);
   }
-  // compress only wide factors: below a few hundred columns Algorithm 2's FP64
-  // rank revealing is cheap and keeps the full FP32 accuracy of X_+ - X_-
-  if (compress_end && np + nm > std::max(2 * b, 512)) {
+  // compress_end 1: each sign group on its own, only wide factors (below a few
+  // hundred columns Algorithm 2's FP64 rank revealing is cheap and keeps the full
+  // accuracy of X_+ - X_-).  2: the joint indefinite FP64 compression of X_+ - X_-,
+  // truncated relative to the correction itself, whenever the factor is wider than
+  // the right-hand side (it also drops the inner-precision noise directions that a
+  // Gram-based QR in Algorithm 2 cannot resolve); each sign group on its own where
+  // the session has no FP64 blocks.
+  if (compress_end == 2 && np + nm > b) {
+    int np2 = np, nm2 = nm;
+    if (!compress_joint<T>(c, in, np2, nm2)) {
+      np2 = compress_part<T>(c, in, 0, np, false);
+      nm2 = compress_part<T>(c, in, cap - nm, nm, true);
+    }
+    np = np2;
+    nm = nm2;
+    res.compressions++;
+  } else if (compress_end == 1 && np + nm > std::max(2 * b, 512)) {
     np = compress_part<T>(c, in, 0, np, false);
     nm = compress_part<T>(c, in, cap - nm, nm, true);
     res.compressions++;
@@ -727,8 +741,8 @@ AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int 
             j, r, np, nm, res.compressions, c.krylov_unconverged);
   return res;
 }
-template AdiResult lradi<float>(Ctx&, Inner<float>&, int, int, bool, double, int, bool, bool);
-template AdiResult lradi<double>(Ctx&, Inner<double>&, int, int, bool, double, int, bool, bool);
+template AdiResult lradi<float>(Ctx&, Inner<float>&, int, int, bool, double, int, bool, int);
+template AdiResult lradi<double>(Ctx&, Inner<double>&, int, int, bool, double, int, bool, int);
 
 template <class T>
 NlrResult nlradi(Ctx& c, Inner<T>& in, const T* Ct, int ldct, int p, double tol_lyap, double tol_newton,
@@ -747,7 +761,7 @@ NlrResult nlradi(Ctx& c, Inner<T>& in, const T* Ct, int ldct, int p, double tol_
       b += in.m;
     }
     CARE_CUDA(cudaMemsetAsync(in.Knew, 0, (size_t)n * in.ldm * sizeof(T), c.s));
-    AdiResult a = lradi<T>(c, in, b, b, hasK, tol_lyap, jmax, true, false);
+    AdiResult a = lradi<T>(c, in, b, b, hasK, tol_lyap, jmax, true, 0);
     out.adi += a.steps;
     out.newton = i + 1;
     out.cols = a.np;

@@ -257,8 +257,11 @@ struct SpmmArgs {
   long chunk;
 };
 
+// (register budget: the plain FP32 product with one vector per thread keeps 8 CTAs
+// per SM resident; the other variants take what they need without spilling)
 template <class T, int TPR, int NVPT, bool CPLX, int NDOT>
-__global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (NVPT == 1 && NDOT == 0 && sizeof(T) == 4) ? 8 : 1)
+    k_spmm(SpmmArgs<T> a) {
   constexpr int VEC = 16 / sizeof(T), NS = NVPT * VEC;
   constexpr int ND = NDOT > 0 ? NDOT : 1;
   RowIter<TPR> it;
@@ -290,30 +293,43 @@ __global__ void __launch_bounds__(kBlock) k_spmm(SpmmArgs<T> a) {
       }
       if (v < a.nvec && diff) vload_ro(a.X + (size_t)row * a.ldx + v * VEC, xi[k]);
     }
-    // the row's entries in predicated batches of 8 (stencil rows have 5-7): all
-    // index/value loads of a batch, then all its gathers, are in flight together,
-    // so a row costs three dependent memory round trips (row pointers, indices,
-    // gathered rows of X); padding entries gather row `row` with weight 0
-    for (int j0 = s; j0 < e; j0 += 8) {
-      int c[8];
-      T av[8];
+    // four independent gathers in flight per thread (stencil rows have 5-7 entries),
+    // then the remainder one by one; 32 registers keep every warp slot resident
+    int j = s;
+    for (; j + 3 < e; j += 4) {
+      int c[4];
+      T av[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const bool in = j0 + u < e;
-        c[u] = in ? __ldg(a.ci + j0 + u) : (int)row;
-        av[u] = in ? __ldg(a.av + j0 + u) : T(0);
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __ldg(a.ci + j + u);
+        av[u] = __ldg(a.av + j + u);
       }
 #pragma unroll
       for (int k = 0; k < NVPT; ++k) {
         const int v = it.lane_v + k * TPR;
         if (v < a.nvec) {
-          T x[8][VEC];
+          T x[4][VEC];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) vload_ro(a.X + (size_t)c[u] * a.ldx + v * VEC, x[u]);
+          for (int u = 0; u < 4; ++u) vload_ro(a.X + (size_t)c[u] * a.ldx + v * VEC, x[u]);
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int q = 0; q < VEC; ++q) y[k][q] = fma(av[u], x[u][q] - xi[k][q], y[k][q]);
+        }
+      }
+    }
+    for (; j < e; ++j) {
+      const int c = __ldg(a.ci + j);
+      const T av = __ldg(a.av + j);
+      const T* xr = a.X + (size_t)c * a.ldx;
+#pragma unroll
+      for (int k = 0; k < NVPT; ++k) {
+        const int v = it.lane_v + k * TPR;
+        if (v < a.nvec) {
+          T x[VEC];
+          vload_ro(xr + v * VEC, x);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) y[k][q] = fma(av, x[q] - xi[k][q], y[k][q]);
         }
       }
     }

@@ -223,11 +223,11 @@ struct AdiResult {
 // knew, accumulates K_new += Z_blk (Z_blk^T B) into in.Knew (requires rp = b).
 // When the factor reaches its capacity it is column-compressed; if that does
 // not free enough room the solve stops early (inexact inner solve).
-// compress_end: column-compress both factor groups at the end (inner-precision
-// truncation) before they are handed to Algorithm 2.
+// compress_end: 0 none; 1 column-compress each factor group at the end (inner-
+// precision truncation) before Algorithm 2; 2 compress X_+ - X_- jointly in FP64.
 template <class T>
 AdiResult lradi(Ctx& c, Inner<T>& in, int b, int rp, bool hasK, double tol, int jmax, bool knew,
-                bool compress_end = false);
+                int compress_end = 0);
 
 struct NlrResult {
   int newton = 0, adi = 0, cols = 0;
