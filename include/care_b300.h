@@ -289,8 +289,8 @@ care_status care_shifted_solve(const care_op* op, const double* B, int ldb, cons
  * operator at a mid-spectrum shift p = -0.05 max|a_ii|:
  *  1. SpMM launch shape: 16-byte vectors per thread in {1, 2, 4} (fewer threads
  *     per row, more gathers in flight per thread) x {4, 8} CTAs per SM for the
- *     row-block kernels x row order (grid-stride, or contiguous row blocks per
- *     CTA so that a stencil's neighbour rows come from the same SM's cache),
+ *     row-block kernels, with grid-stride rows (contiguous row blocks per CTA,
+ *     settable with care_set_launch_shape, lost on every operator measured),
  *     timed on a b-column block in the working precision (median of 5
  *     launches); then the vectors per thread for each other width class of the
  *     Krylov blocks (vectors per row <= 2, <= 4, <= 8, <= 16, more); the

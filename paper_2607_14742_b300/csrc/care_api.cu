@@ -1159,7 +1159,9 @@ care_status care_autotune(const care_op* op, int m, int b, care_prec prec, care_
   const int b_bucket = spmm_bucket((b_width + vec - 1) / vec);
   {
     double bst = 1e300;
-    for (int bl = 0; bl < 2; ++bl)
+    // contiguous row blocks (bl = 1) lost to grid-stride rows on every stencil operator
+    // measured, and inside the fused Krylov kernels; the tuner keeps grid-stride rows
+    for (int bl = 0; bl < 1; ++bl)
       for (int ci = 0; ci < 2; ++ci)
         for (int vi = 0; vi < 3; ++vi) {
           set_tuned_ctas_per_sm(ctas[ci]);
