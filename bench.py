@@ -503,20 +503,20 @@ def batched_cases(pb, torch, dev, count, side_hi):
         return time.perf_counter() - t0, r
 
     stats = {}
-    t, (Z, infos, st) = timed(lambda: pb.care_solve_batched(dA, tol=1e-10, prec="mixed", r_cap=256, opts=o,
-                                                            persistent=True, stats=stats, allow=(5, 6)))
+    t, (Z, infos, st) = timed(lambda: pb.care_solve_batched(dA, tol=1e-10, prec="mixed", r_cap=512, opts=o,
+                                                            persistent=True, stats=stats, allow=(4, 5, 6)))
     out["persistent"] = {"s": t, "cares_per_s": count / t, "batch_launches": stats.get("batch_launches"),
                          "ok": sum(i["status"] == "CARE_OK" for i in infos),
                          "worst_res": max(i["res_rel_CtC"] for i in infos)}
-    t, (Z, infos, st) = timed(lambda: pb.care_solve_batched(dA, tol=1e-10, prec="mixed", r_cap=256, opts=o,
-                                                            workers=8, allow=(5, 6)))
+    t, (Z, infos, st) = timed(lambda: pb.care_solve_batched(dA, tol=1e-10, prec="mixed", r_cap=512, opts=o,
+                                                            workers=8, allow=(4, 5, 6)))
     out["host_workers_8"] = {"s": t, "cares_per_s": count / t, "ok": sum(i["status"] == "CARE_OK" for i in infos),
                              "worst_res": max(i["res_rel_CtC"] for i in infos)}
 
     def loop(prec, items):
         res = []
         for A, B, C in items:
-            res.append(pb.care_solve(A, B, C, tol=1e-10, prec=prec, r_cap=256, opts=o, allow=(5, 6))[1])
+            res.append(pb.care_solve(A, B, C, tol=1e-10, prec=prec, r_cap=512, opts=o, allow=(4, 5, 6))[1])
         return res
     t, infos = timed(lambda: loop("mixed", dA))
     out["single_mixed_loop"] = {"s": t, "cares_per_s": count / t, "ok": sum(i["status"] == "CARE_OK" for i in infos)}
