@@ -332,9 +332,7 @@ def main():
     t = statistics.mean(vals)
     te = statistics.mean(e2es)
     if world > 1:
-        tt = torch.tensor([t, te], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t, te = float(tt[0].item()), float(tt[1].item())
+        t, te = max_over_ranks([t, te], dev)
     info = infos[-1]
     if fp64 is not None:
         fp64["speedup_mixed_vs_fp64"] = fp64["s_per_solve"] / t
@@ -480,6 +478,18 @@ def summarize_launches(path):
         print(f"| `{k}` | {c} | {t / 1e3:.1f} | {100 * t / total:.1f}% |")
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of `values` over the ranks of the default process group
+    (every rank gets the result): the job's time is its slowest replica's.  The
+    single-CARE path does not shard, so N GPUs run N independent replicas and this
+    is the only collective of the bench."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def batched_cases(pb, torch, dev, count, side_hi):
     """Serving sweep: `count` independent 2D convection-diffusion CAREs, grid sides
     U{64..side_hi}, m, p U{1..8}, mixed precision to 1e-10, solved (a) by the serving
@@ -502,16 +512,21 @@ def batched_cases(pb, torch, dev, count, side_hi):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, r
 
+    def progress(key):  # each variant as it completes (stderr), so a cut run keeps them
+        print(json.dumps({key: out[key]}), file=sys.stderr, flush=True)
+
     stats = {}
     t, (Z, infos, st) = timed(lambda: pb.care_solve_batched(dA, tol=1e-10, prec="mixed", r_cap=512, opts=o,
                                                             persistent=True, stats=stats, allow=(4, 5, 6)))
     out["persistent"] = {"s": t, "cares_per_s": count / t, "batch_launches": stats.get("batch_launches"),
                          "ok": sum(i["status"] == "CARE_OK" for i in infos),
                          "worst_res": max(i["res_rel_CtC"] for i in infos)}
+    progress("persistent")
     t, (Z, infos, st) = timed(lambda: pb.care_solve_batched(dA, tol=1e-10, prec="mixed", r_cap=512, opts=o,
                                                             workers=8, allow=(4, 5, 6)))
     out["host_workers_8"] = {"s": t, "cares_per_s": count / t, "ok": sum(i["status"] == "CARE_OK" for i in infos),
                              "worst_res": max(i["res_rel_CtC"] for i in infos)}
+    progress("host_workers_8")
 
     def loop(prec, items):
         res = []
@@ -520,6 +535,7 @@ def batched_cases(pb, torch, dev, count, side_hi):
         return res
     t, infos = timed(lambda: loop("mixed", dA))
     out["single_mixed_loop"] = {"s": t, "cares_per_s": count / t, "ok": sum(i["status"] == "CARE_OK" for i in infos)}
+    progress("single_mixed_loop")
     sample = dA[:8]
     t0 = time.perf_counter()
     infos = loop("fp64", sample)
