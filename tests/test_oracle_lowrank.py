@@ -297,3 +297,18 @@ def test_res_paper_hand_computed():
              2 * 3 * 2 + 3 * 4 + r3]    # ||Z||_F^2 instead of ||Z^T Z||_F
     for w in wrong:
         assert abs(den / w - 1.0) > 0.05
+
+
+@pytest.mark.parametrize("k,inner", [(0, "fp64"), (1, "fp32"), (3, "fp32"), (4, "fp32")])
+def test_dense200_sweep_golden_is_the_oracles(k, inner):
+    """The stored conditioning-sweep outcomes (tests/golden/dense200_sweep.json, which the
+    GPU sweep test compares against) are what the oracle computes: status, rank and the
+    relative residual (to 1e-6 relative: LAPACK's threading may move the last bits) for the cases that
+    finish in seconds, including the first one past the FP32 threshold (k = 4)."""
+    g = json.load(open(os.path.join(GOLD, "dense200_sweep.json")))[f"{k}/{inner}"]
+    p = ci.config_dense_conditioning(k)
+    tol = 1e-5 if inner == "fp32" else 1e-12
+    Z, info = ol.framework1(p.A.to_dense(), p.B, p.C, tau_R=1e-12, dense=True, inner=inner, tol_lyap=tol,
+                            tol_newton=tol)
+    assert info["status"] == g["status"] and info["rank"] == g["rank"], (info["status"], info["rank"], g)
+    assert abs(info["rel_res"] - g["rel_res"]) <= 1e-6 * g["rel_res"], (info["rel_res"], g)
