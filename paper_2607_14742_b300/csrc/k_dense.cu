@@ -387,7 +387,7 @@ template void scale_cols<double>(long, int, double*, int, const double*, cudaStr
 
 // ------------------------------------------------- allocation-free Gram ----
 // Scratch for care_gram_noalloc: a fixed file-scope device array, so the entry
-// point never allocates.  The driver reserves it when it loads this module on a
+// point never allocates.  The CUDA driver reserves it when it loads this module on a
 // device (with lazy loading: at the first call into the library there), and
 // that device holds it until the process exits.  Host code must not pass the symbol itself to a kernel
 // (in host code it names a host-side stand-in); its device address is looked
