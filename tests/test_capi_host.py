@@ -245,11 +245,38 @@ def test_entry_points_reject_invalid_arguments_before_any_device_work():
                                                                      ct.byref(sz)),
         "batched count<0": L.care_solve_batched(-1, None, None, None, None, None, None, None, 1e-10, 1,
                                                 ct.byref(o), None, None, None, 1, None, 0, None, None),
+        "batched persistent count>256": L.care_solve_batched_persistent(
+            257, None, None, None, None, None, None, None, 1e-10, 1, ct.byref(o), None, None, None, None, 0, None,
+            None, None),
+        "batched persistent null arrays": L.care_solve_batched_persistent(
+            2, None, None, None, None, None, None, None, 1e-10, 1, ct.byref(o), None, None, None, dummy, 1024, None,
+            None, None),
+        "persistent workspace count>256": L.care_workspace_size_batched_persistent(257, None, None, None, None, 1,
+                                                                                   ct.byref(o), ct.byref(sz)),
+        "ilu0 null op": L.care_ilu0(None, 0, 1, -1.0, 0.0, dummy, dummy, 1024, None),
+        "ilu0 dtype": L.care_ilu0(ct.byref(op0), 2, 1, -1.0, 0.0, dummy, dummy, 1024, None),
+        "launch shape vpt 3": L.care_set_launch_shape(3, 8, 0),
+        "launch shape ctas 9": L.care_set_launch_shape(1, 9, 0),
+        "launch shape row order 2": L.care_set_launch_shape(1, 8, 2),
         "host symeig n<0": L.care_host_symeig(-1, None, None, None),
         "host gemm sym m!=n": L.care_host_gemm_nt(3, 2, 1, dummy, 1, dummy, 1, None, dummy, 2, 1),
     }
     bad = {k: v for k, v in cases.items() if v != INVALID}
     assert not bad, bad
+
+
+def test_launch_shape_round_trip():
+    """The process-wide launch shape (host state only): set applies one vectors-per-
+    thread value to every width class, get reads the table back; the library's
+    defaults are set again afterwards."""
+    try:
+        pb.set_launch_shape(2, 4, 1)
+        assert pb.launch_shape() == ((2, 2, 2, 2, 2), 4, 1)
+        pb.set_launch_shape(4, 8, 0)
+        assert pb.launch_shape() == ((4, 4, 4, 4, 4), 8, 0)
+    finally:
+        pb.set_launch_shape(1, 8, 0)
+    assert pb.launch_shape() == ((1, 1, 1, 1, 1), 8, 0)
 
 
 def test_workspace_size_grows_with_problem():
