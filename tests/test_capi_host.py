@@ -29,9 +29,17 @@ def test_library_loads_and_exports_every_declared_symbol():
 
 
 def test_status_strings_and_defaults():
-    assert pb.status_string(0) == "CARE_OK"
-    assert pb.status_string(6) == "CARE_STAGNATED"
+    names = ["CARE_OK", "CARE_ERR_INVALID_ARG", "CARE_ERR_CUDA", "CARE_ERR_WORKSPACE", "CARE_ERR_RANK_CAPACITY",
+             "CARE_NOT_CONVERGED", "CARE_STAGNATED", "CARE_INNER_FAILED", "CARE_UNSTABLE", "CARE_NONFINITE",
+             "CARE_ERR_SMALL_DENSE", "CARE_TIMEOUT"]
+    for code, name in enumerate(names):
+        assert pb.status_string(code) == name
     o = pb.default_options()
+    # the library's own defaults beyond the paper's: GMRES restarts (Section 5.2), the joint
+    # FP64 compression of the FP32 correction factors, BiCGStab + sweep ILU(0)
+    assert (o.gmres_restart_lo, o.gmres_restart_hi) == (30, 50)
+    assert o.inner_compress == 2
+    assert (o.krylov, o.precond) == (pb.KRYLOV_BICGSTAB, pb.PRECOND_ILU0)
     # Section 5 parameter list
     assert (o.kmax, o.jmax) == (20, 50)
     assert o.eta_r_rel == 1e-4 and o.eta_s_mult == 10.0
